@@ -1,0 +1,52 @@
+"""QAOA layers of the TFIM on the three-level chain (oracle; test infrastructure only).
+
+Sec. IV, Eqs. tfim_hamiltonian, tfim_model, HZ_block_representation, HZ_representation.
+Readings (the paper's signs disagree between Eq. tfim_model and Eq. HZ_block):
+  * S^z, S^x are Pauli matrices on the qubit levels and zero on |r>.
+  * Layer k applies every ZZ block exp(-i J alpha_k S^z S^z) (with the bias
+    exp(-i b J alpha_k S^z) on each site), then exp(-i beta_k S^x) on every site;
+    layers run k = 1..p.  The ZZ and X rotations carry the same sign; the noiseless
+    statevector then reproduces Table II (pinned in tests).
+  * Blocks run left->right in odd layers and right->left in even layers (snake); the
+    single-site gates of a site are folded, exactly, into the last block that touches
+    it in that layer (no later block in the layer acts on that site).
+"""
+from __future__ import annotations
+
+from typing import List, Tuple
+
+import numpy as np
+
+from . import ops
+
+
+def site_gate(alpha: float, beta: float, J: float, bz: float) -> np.ndarray:
+    """exp(-i beta S^x) exp(-i b J alpha S^z) on one atom."""
+    return ops.expm_h(beta, ops.X_Q) @ ops.expm_h(bz * J * alpha, ops.Z_Q)
+
+
+def layer_ops(c, k: int) -> List[Tuple[int, list]]:
+    """Ordered two-site ops [(left site i, Kraus set on (i, i+1))] of layer k (0-based)."""
+    n = c.n_sites
+    a, b = c.alpha[k], c.beta[k]
+    v = site_gate(a, b, c.J, c.bz)
+    common = dict(angle_zz=c.J * a, gamma_diss=c.gamma_diss, gamma_deph=c.gamma_deph,
+                  xtalk_phase=c.xtalk_phase, delta_pp=c.delta_pp, b0=c.b0, b1=c.b1, bd=c.bd)
+    both = ops.g0_block_channel(**common, post_left=v, post_right=v)
+    if k % 2 == 0:                                   # left -> right
+        mid = ops.g0_block_channel(**common, post_left=v)
+        return [(i, both if i == n - 2 else mid) for i in range(n - 1)]
+    mid = ops.g0_block_channel(**common, post_right=v)
+    return [(i, both if i == 0 else mid) for i in range(n - 2, -1, -1)]
+
+
+def circuit_ops(c) -> List[Tuple[int, list]]:
+    out = []
+    for k in range(c.p):
+        out.extend(layer_ops(c, k))
+    return out
+
+
+def plus_state() -> np.ndarray:
+    """|+_X> on the qubit levels (Sec. IV initial state)."""
+    return np.array([1.0, 1.0, 0.0], dtype=complex) / np.sqrt(2.0)
