@@ -1,0 +1,189 @@
+/*
+ * mpdo.h -- C ABI of the GB300 noisy neutral-atom MPDO library (libmpdo.so).
+ *
+ * Method: arXiv:2309.08572 ("Simulating Large One-Dimensional Neutral Atom Quantum
+ * Systems").  The state is a matrix product density operator (Sec. III.C, Fig. 3a):
+ * rho = sum_k X_k X_k^+, stored as site tensors A_n[l][s][k][r] (left bond l, atom
+ * level s in {0:|0>, 1:|1>, 2:|r>}, inner/Kraus index k, right bond r; r fastest).
+ * A two-site channel is applied by contracting the two site tensors with the channel
+ * and splitting back by a truncated SVD (Sec. III.A, Fig. 2c, Fig. 6a); the inner
+ * index of the new orthogonality centre is truncated with the purity-preserving
+ * scheme (Sec. III.D, Eqs. xiformula and ppt, App. B).  Energies, success probability
+ * and samples come from transfer-matrix contractions (Sec. IV, Eq. tfim_hamiltonian,
+ * qubit trace in Sec. IV.A).
+ *
+ * Conventions for every entry point:
+ *  - Returns MPDO_OK (0) or a negative MPDO_ERR_* code; no C++ exception crosses the ABI.
+ *  - Host pointers passed in are borrowed for the duration of the call only.
+ *  - "host" arrays are ordinary CPU memory; "device" arrays live in GPU memory.
+ *  - complex numbers are (re, im) pairs of doubles, interleaved, row-major.
+ *  - All work is enqueued on the handle's CUDA stream; calls that return host
+ *    results synchronise that stream before returning.
+ *  - mpdo_last_error(h) describes the last failure on handle h (valid until the next
+ *    call on h); mpdo_last_error(NULL) describes the last handle-less failure.
+ */
+#ifndef MPDO_H
+#define MPDO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MPDO_OK = 0,
+  MPDO_ERR_ARG = -1,      /* invalid argument (sizes, sites, null pointers, layout)   */
+  MPDO_ERR_OOM = -2,      /* device allocation failed                                  */
+  MPDO_ERR_CUDA = -3,     /* a CUDA call failed (message in mpdo_last_error)           */
+  MPDO_ERR_NUMERIC = -4,  /* NaN/Inf in inputs or state, zero state, non-PSD Gram     */
+  MPDO_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up                        */
+  MPDO_ERR_STATE = -6     /* op does not touch the orthogonality centre, etc.          */
+};
+
+/* Arithmetic of the hot path.
+ *  MPDO_FP64 : complex128 state, FP64 GEMMs and FP64 Jacobi eigensolves.
+ *  MPDO_C64  : complex64 state, FP32 GEMMs (FP32 accumulation), FP32 Jacobi;
+ *              cutoff, PPT and trace renormalisation in FP64 scalars.
+ *  MPDO_TF32X3, MPDO_BF16X3 : as MPDO_C64 with the large contractions on the
+ *              tensor cores in split precision (3 products per real product). */
+typedef enum { MPDO_FP64 = 0, MPDO_C64 = 1, MPDO_TF32X3 = 2, MPDO_BF16X3 = 3 } mpdo_prec;
+
+typedef struct mpdo_ctx* mpdo_t;   /* opaque; the library owns all its device memory */
+
+typedef struct {
+  int n_sites;          /* N >= 2                                                       */
+  int d;                /* local dimension; must be 3 (|0>,|1>,|r>)                    */
+  int chi_max;          /* bond dimension cap chi (1..1024)                             */
+  int k_max;            /* inner (Kraus) dimension cap K (1..1024)                      */
+  int m_max;            /* largest Kraus count of any two-site op that will be applied */
+  mpdo_prec prec;
+  double sv_cutoff;     /* bond values with s <= sv_cutoff*s_max are dropped (<=0: default) */
+  double kraus_cutoff;  /* inner values with sqrt(w) <= kraus_cutoff*sqrt(w_max) dropped   */
+  int use_ppt;          /* 1: purity-preserving inner truncation; 0: plain + trace renorm  */
+  void* cuda_stream;    /* cudaStream_t to use; NULL = the legacy default stream           */
+} mpdo_config;
+
+/* One op of a layer.  kind 2: two-site channel on (site, site+1) with n_kraus Kraus
+ * operators E_m, each 9x9 on the index s_site*3 + s_{site+1}; kind 1: one-site unitary
+ * (n_kraus must be 1) on `site`, 3x3.  ops points to n_kraus*(d^k)^2 complex numbers
+ * (host, complex128 interleaved, row-major per operator). */
+typedef struct {
+  int kind;
+  int site;
+  int n_kraus;
+  const double* ops;
+} mpdo_op;
+
+typedef struct {
+  int n_ops;
+  const mpdo_op* ops;   /* applied in array order */
+} mpdo_layer;
+
+/* Per-call truncation statistics (accumulated over the call's updates). */
+typedef struct {
+  double disc_bond_w;     /* sum over updates of discarded bond weight / total         */
+  double disc_kraus_w;    /* sum over updates of discarded inner weight / total        */
+  double ppt_theta_min;   /* smallest PPT cone angle used (rad)                          */
+  int ppt_infeasible;     /* updates where PPT had no solution and used theta = 0       */
+  int ppt_clamped;        /* negative PPT values clamped to zero                         */
+  int chi_used_max;       /* largest bond dimension kept                                 */
+  int k_used_max;         /* largest inner dimension kept                                */
+  int n_updates;          /* two-site updates performed                                  */
+} mpdo_trunc_stats;
+
+/* Create a handle.  init_site_vec: host, d complex numbers (interleaved) giving the
+ * product state (x)_n |v>, or NULL for |+_X> = (|0>+|1>)/sqrt(2) (Sec. IV initial state).
+ * The orthogonality centre starts at site 0.  *out is set only on success. */
+int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out);
+
+/* Reset the state of an existing handle to the product state (no reallocation). */
+int mpdo_reset(mpdo_t h, const double* init_site_vec);
+
+/* Apply the ops of `layer` in order (Sec. III.A two-site update; Sec. IV layers).
+ * Each two-site op must be on a bond that contains the current orthogonality centre;
+ * the centre moves to the other site of the bond, whose inner index receives the
+ * op's Kraus index and is then truncated (PPT when enabled).  stats may be NULL. */
+int mpdo_apply_layer(mpdo_t h, const mpdo_layer* layer, mpdo_trunc_stats* stats);
+
+/* Device-resident layer: upload once, apply many times (inputs resident in HBM). */
+typedef struct mpdo_dlayer_s* mpdo_dlayer;
+int mpdo_layer_upload(mpdo_t h, const mpdo_layer* layer, mpdo_dlayer* out);
+int mpdo_apply_dlayer(mpdo_t h, mpdo_dlayer dl, mpdo_trunc_stats* stats);
+int mpdo_layer_free(mpdo_t h, mpdo_dlayer dl);
+
+/* Re-truncate the whole chain to (chi_max, k_max): identity two-site updates swept from
+ * the centre to the right end and back to site 0, so every bond and inner index is
+ * truncated with the centre on it.  The centre ends at site 0. */
+int mpdo_truncate(mpdo_t h, int chi_max, int k_max, int use_ppt, mpdo_trunc_stats* stats);
+
+/* TFIM energies (Eq. tfim_hamiltonian, S = Pauli on the qubit levels, 0 on |r>):
+ * H = -J sum Z_i Z_{i+1} - h sum X_i - b J sum Z_i.
+ *   e_raw        = tr(H rho)/tr(rho)
+ *   e_success    = tr(Pi_q H Pi_q rho)/success_prob,  Pi_q = (x)(|0><0|+|1><1|)
+ *   success_prob = tr(Pi_q rho) (qubit trace, Sec. IV.A), trace = tr(rho)
+ * Output pointers are host doubles; any of them may be NULL. */
+int mpdo_expect_energy(mpdo_t h, double J, double hx, double b, double* e_raw,
+                       double* e_success, double* success_prob, double* trace);
+
+/* Draw n_samples configurations x in {0,1,2}^N from <x|rho|x>/tr(rho) by sequential
+ * conditional sampling with Philox4x32-10 uniforms (counter (site, sample, 0, 0), key
+ * = seed).  bits: host uint8 [n_samples][N]; probs: host double [n_samples] receives
+ * <x|rho|x>.  Either output may be NULL. */
+int mpdo_sample_probs(mpdo_t h, int n_samples, uint64_t seed, uint8_t* bits, double* probs);
+
+/* Current bond dimensions (host int[N-1]), inner dimensions (host int[N]) and centre. */
+int mpdo_get_dims(mpdo_t h, int* bond_dims, int* kraus_dims, int* centre);
+
+/* Copy site tensor n to the host as complex128 [Dl][d][K][Dr] (capacity in complex
+ * numbers given by cap; the dims are written to dims[4]). */
+int mpdo_get_site(mpdo_t h, int n, double* out, size_t cap, int* dims);
+
+int mpdo_destroy(mpdo_t h);
+const char* mpdo_last_error(mpdo_t h);
+
+/* Channel builder (host, FP64, off the hot path).  Builds the Kraus set of one noisy
+ * ZZ block on a bond in the gate-level model: crosstalk phase exp(-i phi n_r n_r)
+ * (Sec. III.B, active pair), the ideal block CNOT (I (x) exp(-i a Z)) CNOT with
+ * CNOT = (I (x) Had) CZ (I (x) Had) (Eq. HZ_block_representation), post-promotion
+ * exp(-i dPP (|1><r| + h.c.)) on both atoms (Sec. IV.A), one unit of Rydberg decay
+ * (branching b0, b1, bd; Sec. II jump operators) and dephasing (linear rate) on both
+ * atoms, then the one-site unitaries post_left / post_right (3x3 complex128, may be
+ * NULL).  The Kraus set is the Choi eigendecomposition, eigenvalues below
+ * eta*lambda_max dropped.  out: host complex128 [cap][9][9]; *n_kraus receives M.
+ * Returns MPDO_ERR_ARG if cap < M. */
+int mpdo_build_block_channel(double angle_zz, double gamma_diss, double gamma_deph,
+                             double xtalk_phase, double delta_pp, double b0, double b1,
+                             double bd, const double* post_left, const double* post_right,
+                             double eta, double* out, int cap, int* n_kraus);
+
+/* QAOA layer builder: the ordered two-site ops of layer k (0-based) of the TFIM QAOA
+ * (Sec. IV, Eqs. tfim_model, HZ_block_representation, HZ_representation): blocks with
+ * ZZ angle J*alpha, left->right for even k and right->left for odd k; the one-site gate
+ * exp(-i beta S^x) exp(-i b J alpha S^z) of each site folded into the last block that
+ * touches it.  Writes n_sites-1 ops: sites[i], kraus counts ms[i], and the Kraus data
+ * into out (host complex128, capacity cap complex numbers). */
+int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double beta, double J,
+                          double bz, double gamma_diss, double gamma_deph,
+                          double xtalk_phase, double delta_pp, double b0, double b1,
+                          double bd, double eta, int* sites, int* ms, double* out,
+                          size_t cap);
+
+/* Kernel-level entry points used by the unit tests (device pointers). */
+/* C[b] = op(A[b]) op(B[b]) for complex matrices; prec 0 = complex128, 1 = complex64.
+ * opa/opb: 0 = N, 1 = T, 2 = C (conjugate transpose).  A is m x k after op, etc.;
+ * leading dimensions in complex elements (row-major), batch strides in elements. */
+int mpdo_kernel_cgemm(int prec, int opa, int opb, int m, int n, int k, const void* a,
+                      long lda, long sa, const void* b, long ldb, long sb, void* c,
+                      long ldc, long sc, int batch, void* stream);
+/* Hermitian eigendecomposition of a (n x n, row-major complex, overwritten): eigenvalues
+ * descending into w (double, host-visible device array of n), eigenvectors as the
+ * columns of v (n x n row-major complex of the same precision).  Returns sweeps used
+ * in *sweeps (host). */
+int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPDO_H */

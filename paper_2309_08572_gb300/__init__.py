@@ -1,0 +1,300 @@
+"""Python binding of libmpdo (GB300 noisy neutral-atom MPDO simulator).
+
+Argument marshalling only: every step of the method runs in the CUDA library behind the
+C ABI declared in include/mpdo.h.  The library is loaded from this package directory
+(built in-tree by build.py); importing this module raises if it is missing, so no code
+path can fall back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpdo.so")
+
+MPDO_FP64, MPDO_C64, MPDO_TF32X3, MPDO_BF16X3 = 0, 1, 2, 3
+PREC = {"fp64": MPDO_FP64, "c64": MPDO_C64, "tf32x3": MPDO_TF32X3, "bf16x3": MPDO_BF16X3}
+ERRORS = {-1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_NUMERIC", -5: "ERR_TIMEOUT",
+          -6: "ERR_STATE"}
+
+
+class MpdoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("d", C.c_int), ("chi_max", C.c_int), ("k_max", C.c_int),
+                ("m_max", C.c_int), ("prec", C.c_int), ("sv_cutoff", C.c_double),
+                ("kraus_cutoff", C.c_double), ("use_ppt", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class Op(C.Structure):
+    _fields_ = [("kind", C.c_int), ("site", C.c_int), ("n_kraus", C.c_int),
+                ("ops", C.POINTER(C.c_double))]
+
+
+class Layer(C.Structure):
+    _fields_ = [("n_ops", C.c_int), ("ops", C.POINTER(Op))]
+
+
+class TruncStats(C.Structure):
+    _fields_ = [("disc_bond_w", C.c_double), ("disc_kraus_w", C.c_double),
+                ("ppt_theta_min", C.c_double), ("ppt_infeasible", C.c_int),
+                ("ppt_clamped", C.c_int), ("chi_used_max", C.c_int), ("k_used_max", C.c_int),
+                ("n_updates", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, VP, S = C.POINTER, C.c_int, C.c_double, C.c_void_p, C.c_size_t
+    sig = {
+        "mpdo_create": (I, [P(Config), P(D), P(VP)]),
+        "mpdo_reset": (I, [VP, P(D)]),
+        "mpdo_apply_layer": (I, [VP, P(Layer), P(TruncStats)]),
+        "mpdo_layer_upload": (I, [VP, P(Layer), P(VP)]),
+        "mpdo_apply_dlayer": (I, [VP, VP, P(TruncStats)]),
+        "mpdo_layer_free": (I, [VP, VP]),
+        "mpdo_truncate": (I, [VP, I, I, I, P(TruncStats)]),
+        "mpdo_expect_energy": (I, [VP, D, D, D, P(D), P(D), P(D), P(D)]),
+        "mpdo_sample_probs": (I, [VP, I, C.c_uint64, P(C.c_uint8), P(D)]),
+        "mpdo_get_dims": (I, [VP, P(I), P(I), P(I)]),
+        "mpdo_get_site": (I, [VP, I, P(D), S, P(I)]),
+        "mpdo_destroy": (I, [VP]),
+        "mpdo_last_error": (C.c_char_p, [VP]),
+        "mpdo_build_block_channel": (I, [D, D, D, D, D, D, D, D, P(D), P(D), D, P(D), I, P(I)]),
+        "mpdo_build_qaoa_layer": (I, [I, I, D, D, D, D, D, D, D, D, D, D, D, D, P(I), P(I),
+                                      P(D), S]),
+        "mpdo_kernel_cgemm": (I, [I, I, I, I, I, I, VP, C.c_long, C.c_long, VP, C.c_long,
+                                  C.c_long, VP, C.c_long, C.c_long, I, VP]),
+        "mpdo_kernel_heig": (I, [I, I, VP, VP, P(D), P(I), VP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+LIB = _load()
+
+
+def _check(rc: int, handle=None):
+    if rc != 0:
+        msg = LIB.mpdo_last_error(handle)
+        raise MpdoError(rc, msg.decode() if msg else "")
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return C.c_void_p(None)
+
+
+# ------------------------------------------------------------------ channels (host, a0)
+def build_block_channel(angle_zz: float, gamma_diss: float, gamma_deph: float,
+                        xtalk_phase: float = 0.0, delta_pp: float = 0.0, b0: float = 1 / 16,
+                        b1: float = 1 / 16, bd: float = 7 / 8, post_left=None, post_right=None,
+                        eta: float = 1e-15) -> np.ndarray:
+    """Kraus set (M, 9, 9) complex128 of one noisy ZZ block (library channel builder)."""
+    out = np.zeros((81, 81, 2))
+    m = C.c_int(0)
+    pl = None if post_left is None else np.ascontiguousarray(np.asarray(post_left, complex)).view(float)
+    pr = None if post_right is None else np.ascontiguousarray(np.asarray(post_right, complex)).view(float)
+    rc = LIB.mpdo_build_block_channel(angle_zz, gamma_diss, gamma_deph, xtalk_phase, delta_pp,
+                                      b0, b1, bd, None if pl is None else _dptr(pl),
+                                      None if pr is None else _dptr(pr), eta, _dptr(out), 81,
+                                      C.byref(m))
+    _check(rc)
+    return out[: m.value].view(complex).reshape(m.value, 9, 9)
+
+
+def build_qaoa_layer(n_sites: int, k: int, alpha: float, beta: float, J: float = 1.0,
+                     bz: float = 0.0, gamma_diss: float = 0.0, gamma_deph: float = 0.0,
+                     xtalk_phase: float = 0.0, delta_pp: float = 0.0, b0: float = 1 / 16,
+                     b1: float = 1 / 16, bd: float = 7 / 8, eta: float = 1e-15):
+    """Ordered two-site ops [(site, Kraus (M,9,9))] of QAOA layer k (library builder)."""
+    nops = n_sites - 1
+    sites = np.zeros(nops, dtype=np.int32)
+    ms = np.zeros(nops, dtype=np.int32)
+    cap = nops * 81 * 81
+    out = np.zeros((cap, 2))
+    rc = LIB.mpdo_build_qaoa_layer(n_sites, k, alpha, beta, J, bz, gamma_diss, gamma_deph,
+                                   xtalk_phase, delta_pp, b0, b1, bd, eta,
+                                   sites.ctypes.data_as(C.POINTER(C.c_int)),
+                                   ms.ctypes.data_as(C.POINTER(C.c_int)), _dptr(out), cap)
+    _check(rc)
+    flat = out.view(complex).reshape(-1)
+    ops, off = [], 0
+    for s, m in zip(sites, ms):
+        ops.append((int(s), flat[off: off + m * 81].reshape(m, 9, 9).copy()))
+        off += m * 81
+    return ops
+
+
+def circuit_layers(c) -> List[list]:
+    """Library-built op lists for every layer of a workload description (synth.Circuit)."""
+    return [build_qaoa_layer(c.n_sites, k, c.alpha[k], c.beta[k], c.J, c.bz, c.gamma_diss,
+                             c.gamma_deph, c.xtalk_phase, c.delta_pp, c.b0, c.b1, c.bd)
+            for k in range(c.p)]
+
+
+class _LayerArgs:
+    """Keeps the ctypes layer and its arrays alive for one call."""
+
+    def __init__(self, ops):
+        self.arrays = []
+        self.cops = (Op * max(1, len(ops)))()
+        for n, op in enumerate(ops):
+            if len(op) == 2:
+                site, k = op
+                kind = 2
+            else:
+                kind, site, k = op
+            arr = np.ascontiguousarray(np.asarray(k, dtype=complex))
+            if kind == 1:
+                arr = arr.reshape(1, 3, 3)
+            else:
+                arr = arr.reshape(-1, 9, 9)
+            flat = arr.reshape(-1).view(float)
+            self.arrays.append(flat)
+            self.cops[n] = Op(kind, int(site), arr.shape[0], _dptr(flat))
+        self.layer = Layer(len(ops), self.cops)
+
+
+class Mpdo:
+    """One MPDO on the GPU (handle of libmpdo)."""
+
+    def __init__(self, n_sites: int, chi_max: int, k_max: int, m_max: int = 25,
+                 prec: str = "fp64", sv_cutoff: float = 0.0, kraus_cutoff: float = 0.0,
+                 use_ppt: bool = True, init_vec: Optional[Sequence[complex]] = None,
+                 stream=None):
+        self.n = n_sites
+        cfg = Config(n_sites, 3, chi_max, k_max, m_max, PREC[prec], sv_cutoff, kraus_cutoff,
+                     int(use_ppt), _current_stream() if stream is None else C.c_void_p(stream))
+        self._h = C.c_void_p(None)
+        v = None if init_vec is None else np.ascontiguousarray(np.asarray(init_vec, complex)).view(float)
+        rc = LIB.mpdo_create(C.byref(cfg), None if v is None else _dptr(v), C.byref(self._h))
+        _check(rc)
+        self.prec = prec
+
+    def close(self):
+        if self._h:
+            LIB.mpdo_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, init_vec=None):
+        v = None if init_vec is None else np.ascontiguousarray(np.asarray(init_vec, complex)).view(float)
+        _check(LIB.mpdo_reset(self._h, None if v is None else _dptr(v)), self._h)
+
+    def apply_layer(self, ops) -> dict:
+        args = _LayerArgs(ops)
+        st = TruncStats()
+        _check(LIB.mpdo_apply_layer(self._h, C.byref(args.layer), C.byref(st)), self._h)
+        return st.as_dict()
+
+    def upload_layer(self, ops):
+        args = _LayerArgs(ops)
+        dl = C.c_void_p(None)
+        _check(LIB.mpdo_layer_upload(self._h, C.byref(args.layer), C.byref(dl)), self._h)
+        return dl
+
+    def apply_uploaded(self, dl) -> dict:
+        st = TruncStats()
+        _check(LIB.mpdo_apply_dlayer(self._h, dl, C.byref(st)), self._h)
+        return st.as_dict()
+
+    def free_uploaded(self, dl):
+        _check(LIB.mpdo_layer_free(self._h, dl), self._h)
+
+    def truncate(self, chi_max: int, k_max: int, use_ppt: bool = True) -> dict:
+        st = TruncStats()
+        _check(LIB.mpdo_truncate(self._h, chi_max, k_max, int(use_ppt), C.byref(st)), self._h)
+        return st.as_dict()
+
+    def expect_energy(self, J: float = 1.0, hx: float = 1.0, bz: float = 0.0) -> dict:
+        vals = [C.c_double() for _ in range(4)]
+        _check(LIB.mpdo_expect_energy(self._h, J, hx, bz, *[C.byref(v) for v in vals]),
+               self._h)
+        return dict(zip(("e_raw", "e_succ", "p_succ", "trace"), (v.value for v in vals)))
+
+    def sample_probs(self, n_samples: int, seed: int) -> Tuple[np.ndarray, np.ndarray]:
+        bits = np.zeros((n_samples, self.n), dtype=np.uint8)
+        probs = np.zeros(n_samples)
+        _check(LIB.mpdo_sample_probs(self._h, n_samples, seed,
+                                     bits.ctypes.data_as(C.POINTER(C.c_uint8)), _dptr(probs)),
+               self._h)
+        return bits, probs
+
+    def dims(self):
+        b = np.zeros(self.n - 1, dtype=np.int32)
+        k = np.zeros(self.n, dtype=np.int32)
+        c = C.c_int(0)
+        _check(LIB.mpdo_get_dims(self._h, b.ctypes.data_as(C.POINTER(C.c_int)),
+                                 k.ctypes.data_as(C.POINTER(C.c_int)), C.byref(c)), self._h)
+        return b, k, c.value
+
+    def site(self, n: int) -> np.ndarray:
+        b, k, _ = self.dims()
+        dl = 1 if n == 0 else int(b[n - 1])
+        dr = 1 if n == self.n - 1 else int(b[n])
+        cap = dl * 3 * int(k[n]) * dr
+        out = np.zeros(2 * cap)
+        dims = (C.c_int * 4)()
+        _check(LIB.mpdo_get_site(self._h, n, _dptr(out), cap, dims), self._h)
+        return out.view(complex).reshape(tuple(dims))
+
+    def to_dense(self) -> np.ndarray:
+        """rho as a d^N x d^N matrix (tiny chains only; host-side reassembly for tests)."""
+        x = np.ones((1, 1, 1, 1), dtype=complex)
+        for n in range(self.n):
+            a = self.site(n)
+            x = np.einsum("pqab,askr,btkc->psqtrc", x, a, a.conj(), optimize=True)
+            p, s, q, t, r, c = x.shape
+            x = x.reshape(p * s, q * t, r, c)
+        return x[:, :, 0, 0]
+
+
+# ------------------------------------------------------ kernel-level entry points (tests)
+def kernel_cgemm(prec: int, opa: int, opb: int, m: int, n: int, k: int, a, lda: int, sa: int,
+                 b, ldb: int, sb: int, c, ldc: int, sc: int, batch: int, stream=None):
+    """c = op(a) op(b) on device tensors (complex128 if prec == 0 else complex64)."""
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    _check(LIB.mpdo_kernel_cgemm(prec, opa, opb, m, n, k, C.c_void_p(a.data_ptr()), lda, sa,
+                                 C.c_void_p(b.data_ptr()), ldb, sb, C.c_void_p(c.data_ptr()),
+                                 ldc, sc, batch, st))
+
+
+def kernel_heig(prec: int, n: int, a, v, w, stream=None) -> int:
+    """Hermitian eigendecomposition of the device matrix a (n x n) -> w (desc), v."""
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    sweeps = C.c_int(0)
+    _check(LIB.mpdo_kernel_heig(prec, n, C.c_void_p(a.data_ptr()), C.c_void_p(v.data_ptr()),
+                                C.cast(C.c_void_p(w.data_ptr()), C.POINTER(C.c_double)),
+                                C.byref(sweeps), st))
+    return sweeps.value

@@ -1,0 +1,865 @@
+// C ABI of libmpdo: handle management, the two-site MPDO update driver, observables and
+// sampling.  The arithmetic of every step runs in the kernels of gemm.cu, jacobi.cu and
+// kernels.cu; this file only sequences them and moves a few scalars to the host.
+//
+// Update of a bond (i, i+1) with the orthogonality centre at i (Sec. III.A, Fig. 2c):
+// with M_i = A_i as [(l,k_i) x (s_i,b)] and N_j = A_{i+1} as [(b,s_j) x (k_j,r)],
+//   G_i = M_i^+ M_i,  G_j = N_j N_j^+                               (Gram matrices)
+//   G_i = V diag(sigma) V^+,  R = diag(sqrt sigma) V^+             (left factor)
+//   Phi[(S,s,b),(S',s',b')] = sum_{t,t'} C[(S,s,t),(S',s',t')] G_j[(b,t),(b',t')]
+//       with C = sum_{m,T} E_m[(S,T),(s,t)] conj(E_m[(S',T),(s',t')])
+//   H = (I (x) R) Phi (I (x) R)^+ = Z Z^+ for the reduced two-site tensor Z
+// The eigenpairs (lambda = s^2, u) of H give the truncated SVD of theta' = (M_i (x) I) Y:
+//   new A_i  = (M_i (x) I)(I (x) V sigma^-1/2) u        (left-orthonormal)
+//   new A_j  = renorm * ((I (x) V sigma^1/2) u)^+ Gamma (I (x) N_j), Gamma = the channel,
+// whose inner index (m, k_j) is then truncated by the eigenpairs of its Gram matrix and
+// the purity-preserving rescaling (Sec. III.D).  Right-to-left updates run on the
+// mirrored chain (site order and the l/r bond indices swapped, channel sites swapped).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mpdo.h"
+#include "common.cuh"
+#include "internal.h"
+#include "kernels.h"
+
+using namespace mpdo;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct DevOp {
+  int kind = 2;
+  int site = 0;
+  int m = 1;
+  void* e = nullptr;      // M x 81 (precision of the handle)
+  void* em = nullptr;     // mirrored (sites swapped)
+  void* ct = nullptr;     // 27 x 27
+  void* ctm = nullptr;    // mirrored
+  void* u = nullptr;      // kind 1: 3x3
+};
+
+}  // namespace
+
+struct mpdo_dlayer_s {
+  std::vector<DevOp> ops;
+  void* mem = nullptr;
+};
+
+struct mpdo_ctx {
+  mpdo_config cfg{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  int n = 0, chi = 0, kmax = 0, mmax = 1;
+  bool dbl = true;     // complex128 state and arithmetic
+  bool rev = false;    // chain stored mirrored
+  int centre = 0;      // user coordinates
+  double gtol = 0, htol = 0, kcut = 0;
+  int max_sweeps = 30;
+  std::vector<int> bond;  // storage coords, size n+1
+  std::vector<int> kd;    // storage coords, size n
+  size_t elt = 16;        // bytes per complex
+  size_t site_cap = 0;    // complex elements per site
+  void* sites[2] = {nullptr, nullptr};
+  int cur = 0;
+  // workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<void*> allocs;
+  void *wM, *wGi, *wGj, *wVg, *wR, *wVs, *wVr, *wPhi, *wX, *wH, *wU, *wVgen, *wW, *wTmp, *wQ,
+      *wWB, *wBp, *wWK, *wVk, *wVks, *wCn, *wRs, *wIrs, *eigmem;
+  double *wSig, *wLam, *wWv, *wF;
+  EigWork<double> eig64;
+  EigWork<float> eig32;
+  StepScalars* dsc = nullptr;
+  StepScalars* hsc = nullptr;  // pinned
+  DevStats* dstats = nullptr;
+  DevStats* hstats = nullptr;  // pinned
+  // staging for host layers
+  mpdo_dlayer_s staged;
+  size_t staged_cap = 0;
+  // lazily allocated observable buffers
+  void* obs = nullptr;
+  size_t obs_bytes = 0;
+
+  void* site(int buf, int s) const {
+    return static_cast<char*>(sites[buf]) + (size_t)s * site_cap * elt;
+  }
+};
+
+namespace {
+
+int fail(mpdo_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_err = msg;
+  return code;
+}
+int cuda_fail(mpdo_ctx* h, cudaError_t e, const char* where) {
+  return fail(h, MPDO_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(expr)                                          \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, #expr); \
+  } while (0)
+
+template <typename R>
+cx<R> one() { return mkc<R>(1, 0); }
+template <typename R>
+cx<R> zero() { return mkc<R>(0, 0); }
+
+template <typename R>
+EigWork<R>& eigw(mpdo_ctx* h);
+template <>
+EigWork<double>& eigw<double>(mpdo_ctx* h) { return h->eig64; }
+template <>
+EigWork<float>& eigw<float>(mpdo_ctx* h) { return h->eig32; }
+
+int alloc_dev(mpdo_ctx* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, MPDO_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  h->allocs.push_back(*p);
+  return MPDO_OK;
+}
+
+int read_scalars(mpdo_ctx* h) {
+  CK(cudaMemcpyAsync(h->hsc, h->dsc, sizeof(StepScalars), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (h->hsc->flags & 1) return fail(h, MPDO_ERR_NUMERIC, "zero or non-finite state in update");
+  return MPDO_OK;
+}
+
+// ------------------------------------------------------------------ the update
+template <typename R>
+int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int kmax,
+              int use_ppt) {
+  using T = cx<R>;
+  cudaStream_t st = h->st;
+  const int dl = h->bond[i], ki = h->kd[i], dm = h->bond[i + 1], kj = h->kd[i + 1],
+            dr = h->bond[i + 2];
+  const int M = op.m;
+  const int n3 = 3 * dm, n9 = 9 * dm;
+  T* ai = static_cast<T*>(h->site(h->cur, i));
+  T* aj = static_cast<T*>(h->site(h->cur, i + 1));
+  const T* E = static_cast<const T*>(mirrored ? op.em : op.e);
+  const T* Ct = static_cast<const T*>(mirrored ? op.ctm : op.ct);
+  T* wM = static_cast<T*>(h->wM);
+  T* wGi = static_cast<T*>(h->wGi);
+  T* wGj = static_cast<T*>(h->wGj);
+  T* wVg = static_cast<T*>(h->wVg);
+  T* wR = static_cast<T*>(h->wR);
+  T* wVs = static_cast<T*>(h->wVs);
+  T* wVr = static_cast<T*>(h->wVr);
+  T* wPhi = static_cast<T*>(h->wPhi);
+  T* wX = static_cast<T*>(h->wX);
+  T* wH = static_cast<T*>(h->wH);
+  T* wU = static_cast<T*>(h->wU);
+  T* wVgen = static_cast<T*>(h->wVgen);
+  T* wW = static_cast<T*>(h->wW);
+  T* wTmp = static_cast<T*>(h->wTmp);
+  T* wQ = static_cast<T*>(h->wQ);
+  T* wWB = static_cast<T*>(h->wWB);
+  T* wBp = static_cast<T*>(h->wBp);
+  T* wWK = static_cast<T*>(h->wWK);
+  T* wVk = static_cast<T*>(h->wVk);
+  T* wVks = static_cast<T*>(h->wVks);
+  T* wCn = static_cast<T*>(h->wCn);
+  R* wRs = static_cast<R*>(h->wRs);
+  R* wIrs = static_cast<R*>(h->wIrs);
+  const T c1 = one<R>(), c0 = zero<R>();
+
+  // a2: Gram matrices of the two site tensors
+  CK(swap12<T>(st, dl, 3, ki, dm, ai, wM));
+  CK(cgemm<R>(st, OP_C, OP_N, n3, n3, dl * ki, wM, n3, 0, wM, n3, 0, wGi, n3, 0, 1, c1, c0));
+  CK(cgemm<R>(st, OP_N, OP_C, n3, n3, kj * dr, aj, (long)kj * dr, 0, aj, (long)kj * dr, 0, wGj,
+              n3, 0, 1, c1, c0));
+  // a3: left factor from the eigendecomposition of G_i (numerical rank by gtol)
+  CK(heig<R>(st, n3, wGi, n3, wVg, n3, h->wSig, eigw<R>(h), h->max_sweeps));
+  CK(gram_mask<R>(st, n3, h->wSig, h->gtol, wRs, wIrs, h->dsc));
+  CK(gram_factor<R>(st, n3, wVg, wRs, wIrs, wR, wVs, wVr));
+  // a4/a5: Phi from the channel and G_j, then H = (I x R) Phi (I x R)^+
+  CK(build_phi<R>(st, dm, Ct, wGj, wPhi));
+  CK(cgemm<R>(st, OP_N, OP_N, n3, n9, n3, wR, n3, 0, wPhi, n9, (long)n3 * n9, wX, n9,
+              (long)n3 * n9, 3, c1, c0));
+  CK(cgemm<R>(st, OP_N, OP_C, n9, n3, n3, wX, n9, n3, wR, n3, 0, wH, n9, n3, 3, c1, c0));
+  // a6: bond eigenpairs and cut
+  CK(heig<R>(st, n9, wH, n9, wU, n9, h->wLam, eigw<R>(h), h->max_sweeps));
+  CK(bond_select(st, n9, h->wLam, h->htol, chi, h->dsc, h->dstats));
+  int rc = read_scalars(h);
+  if (rc) return rc;
+  const int keep = h->hsc->keep;
+  // a7: split.  Vgen = (I x V sigma^-1/2) U_keep, W = (I x V sigma^1/2) U_keep
+  CK(cgemm<R>(st, OP_N, OP_N, n3, keep, n3, wVs, n3, 0, wU, n9, (long)n3 * n9, wVgen, keep,
+              (long)n3 * keep, 3, c1, c0));
+  CK(cgemm<R>(st, OP_N, OP_N, n3, keep, n3, wVr, n3, 0, wU, n9, (long)n3 * n9, wW, keep,
+              (long)n3 * keep, 3, c1, c0));
+  CK(cgemm<R>(st, OP_N, OP_N, dl * ki, keep, n3, wM, n3, 0, wVgen, keep, (long)n3 * keep, wTmp,
+              3L * keep, keep, 3, c1, c0));
+  CK(swap12<T>(st, dl, ki, 3, keep, wTmp, ai));
+  CK(make_q<R>(st, dm, keep, M, wW, E, h->dsc, wQ));
+  CK(cgemm<R>(st, OP_N, OP_N, keep * 3 * M, kj * dr, n3, wQ, n3, 0, aj, (long)kj * dr, 0, wWB,
+              (long)kj * dr, 0, 1, c1, c0));
+  // a8: inner-index Gram of the new centre and its eigenpairs
+  const int KM = M * kj;
+  const long colsB = (long)keep * 3 * dr;
+  CK(swap12<T>(st, 1, (long)keep * 3, KM, dr, wWB, wBp));
+  CK(cgemm<R>(st, OP_N, OP_C, KM, KM, colsB, wBp, colsB, 0, wBp, colsB, 0, wWK, KM, 0, 1, c1,
+              c0));
+  CK(heig<R>(st, KM, wWK, KM, wVk, KM, h->wWv, eigw<R>(h), h->max_sweeps));
+  // a9: cut + PPT (FP64 scalars)
+  CK(kraus_select(st, KM, h->wWv, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
+  rc = read_scalars(h);
+  if (rc) return rc;
+  const int kk = h->hsc->kkeep;
+  // a10: apply the inner isometry with the PPT scales
+  CK(scale_vk<R>(st, KM, kk, wVk, KM, h->wF, wVks));
+  CK(cgemm<R>(st, OP_C, OP_N, kk, colsB, KM, wVks, kk, 0, wBp, colsB, 0, wCn, colsB, 0, 1, c1,
+              c0));
+  CK(swap12<T>(st, 1, kk, (long)keep * 3, dr, wCn, aj));
+  h->bond[i + 1] = keep;
+  h->kd[i + 1] = kk;
+  return MPDO_OK;
+}
+
+template <typename R>
+int reverse_chain(mpdo_ctx* h) {
+  using T = cx<R>;
+  int other = 1 - h->cur;
+  for (int s = 0; s < h->n; ++s) {
+    int t = h->n - 1 - s;
+    CK(reverse_site<T>(h->st, h->bond[s], 3, h->kd[s], h->bond[s + 1],
+                       static_cast<const T*>(h->site(h->cur, s)),
+                       static_cast<T*>(h->site(other, t))));
+  }
+  h->cur = other;
+  std::reverse(h->bond.begin(), h->bond.end());
+  std::reverse(h->kd.begin(), h->kd.end());
+  h->rev = !h->rev;
+  return MPDO_OK;
+}
+
+template <typename R>
+int apply_ops(mpdo_ctx* h, const std::vector<DevOp>& ops, int chi, int kmax, int use_ppt) {
+  for (const DevOp& op : ops) {
+    if (op.kind == 1) {
+      int s = h->rev ? h->n - 1 - op.site : op.site;
+      int rc = MPDO_OK;
+      CK(one_site<R>(h->st, h->bond[s], h->kd[s], h->bond[s + 1],
+                     static_cast<const cx<R>*>(op.u), static_cast<cx<R>*>(h->site(h->cur, s))));
+      (void)rc;
+      continue;
+    }
+    int i = op.site;
+    bool ltr;
+    if (h->centre == i) ltr = true;
+    else if (h->centre == i + 1) ltr = false;
+    else
+      return fail(h, MPDO_ERR_STATE, "two-site op on bond (" + std::to_string(i) + "," +
+                                         std::to_string(i + 1) + ") does not touch centre " +
+                                         std::to_string(h->centre));
+    // storage must run left->right along the update direction
+    if (ltr == h->rev) {
+      int rc = reverse_chain<R>(h);
+      if (rc) return rc;
+    }
+    int is = h->rev ? h->n - 2 - i : i;
+    int rc = update_lr<R>(h, is, op, h->rev, chi, kmax, use_ppt);
+    if (rc) return rc;
+    h->centre = ltr ? i + 1 : i;
+  }
+  return MPDO_OK;
+}
+
+// ----------------------------------------------------------- op preparation
+using zc = std::complex<double>;
+
+void channel_c(const zc* e, int m, zc* c) {
+  // C[(S,s,t),(S2,s2,t2)] = sum_{m,T} E_m[(S,T),(s,t)] conj(E_m[(S2,T),(s2,t2)])
+  for (int a = 0; a < 729; ++a) c[a] = 0;
+  for (int mm = 0; mm < m; ++mm) {
+    const zc* em = e + mm * 81;
+    for (int S = 0; S < 3; ++S)
+      for (int s = 0; s < 3; ++s)
+        for (int t = 0; t < 3; ++t)
+          for (int S2 = 0; S2 < 3; ++S2)
+            for (int s2 = 0; s2 < 3; ++s2)
+              for (int t2 = 0; t2 < 3; ++t2) {
+                zc acc = 0;
+                for (int T = 0; T < 3; ++T)
+                  acc += em[(S * 3 + T) * 9 + s * 3 + t] *
+                         std::conj(em[(S2 * 3 + T) * 9 + s2 * 3 + t2]);
+                c[(S * 9 + s * 3 + t) * 27 + S2 * 9 + s2 * 3 + t2] += acc;
+              }
+  }
+}
+
+void mirror_ops(const zc* e, int m, zc* out) {
+  for (int mm = 0; mm < m; ++mm)
+    for (int S = 0; S < 3; ++S)
+      for (int T = 0; T < 3; ++T)
+        for (int s = 0; s < 3; ++s)
+          for (int t = 0; t < 3; ++t)
+            out[mm * 81 + (T * 3 + S) * 9 + t * 3 + s] = e[mm * 81 + (S * 3 + T) * 9 + s * 3 + t];
+}
+
+// Build device copies of a host layer into `dl` (memory from one cudaMalloc).
+int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool staged) {
+  if (!layer || layer->n_ops < 0 || (layer->n_ops > 0 && !layer->ops))
+    return fail(h, MPDO_ERR_ARG, "null layer");
+  const int elt = (int)h->elt;
+  size_t total = 0;
+  for (int k = 0; k < layer->n_ops; ++k) {
+    const mpdo_op& op = layer->ops[k];
+    if (!op.ops) return fail(h, MPDO_ERR_ARG, "op " + std::to_string(k) + " has no data");
+    if (op.kind == 2) {
+      if (op.site < 0 || op.site > h->n - 2)
+        return fail(h, MPDO_ERR_ARG, "two-site op site out of range");
+      if (op.n_kraus < 1 || op.n_kraus > h->mmax)
+        return fail(h, MPDO_ERR_ARG, "n_kraus " + std::to_string(op.n_kraus) +
+                                         " outside 1..m_max=" + std::to_string(h->mmax));
+      if ((size_t)op.n_kraus * h->kmax > 1024)
+        return fail(h, MPDO_ERR_ARG, "n_kraus*k_max exceeds 1024");
+      total += (size_t)(2 * op.n_kraus * 81 + 2 * 729) * elt;
+    } else if (op.kind == 1) {
+      if (op.site < 0 || op.site > h->n - 1) return fail(h, MPDO_ERR_ARG, "one-site op site");
+      if (op.n_kraus != 1) return fail(h, MPDO_ERR_ARG, "one-site op needs n_kraus == 1");
+      total += 9 * elt;
+    } else {
+      return fail(h, MPDO_ERR_ARG, "op kind must be 1 or 2");
+    }
+    total = (total + 255) & ~(size_t)255;
+  }
+  // host staging buffer of the converted data
+  std::vector<unsigned char> host(total + 256);
+  dl->ops.clear();
+  size_t off = 0;
+  for (int k = 0; k < layer->n_ops; ++k) {
+    const mpdo_op& op = layer->ops[k];
+    DevOp d;
+    d.kind = op.kind;
+    d.site = op.site;
+    d.m = op.n_kraus;
+    const int nval = op.kind == 2 ? op.n_kraus * 81 : 9;
+    std::vector<zc> e(nval);
+    for (int a = 0; a < nval; ++a) {
+      double re = op.ops[2 * a], im = op.ops[2 * a + 1];
+      if (!std::isfinite(re) || !std::isfinite(im))
+        return fail(h, MPDO_ERR_NUMERIC, "non-finite value in op " + std::to_string(k));
+      e[a] = zc(re, im);
+    }
+    std::vector<std::pair<const zc*, int>> parts;
+    std::vector<zc> em, ct(729), ctm(729);
+    if (op.kind == 2) {
+      em.resize(nval);
+      mirror_ops(e.data(), op.n_kraus, em.data());
+      channel_c(e.data(), op.n_kraus, ct.data());
+      channel_c(em.data(), op.n_kraus, ctm.data());
+      parts = {{e.data(), nval}, {em.data(), nval}, {ct.data(), 729}, {ctm.data(), 729}};
+    } else {
+      // one-site ops must be unitary to keep the canonical gauge
+      double dev = 0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          zc acc = 0;
+          for (int c = 0; c < 3; ++c) acc += std::conj(e[c * 3 + a]) * e[c * 3 + b];
+          dev = std::max(dev, std::abs(acc - (a == b ? 1.0 : 0.0)));
+        }
+      if (dev > 1e-10) return fail(h, MPDO_ERR_ARG, "one-site op is not unitary");
+      parts = {{e.data(), nval}};
+    }
+    size_t starts[4];
+    for (size_t p = 0; p < parts.size(); ++p) {
+      starts[p] = off;
+      for (int a = 0; a < parts[p].second; ++a) {
+        zc v = parts[p].first[a];
+        if (h->dbl) {
+          double* dst = reinterpret_cast<double*>(host.data() + off) + 2 * a;
+          dst[0] = v.real(); dst[1] = v.imag();
+        } else {
+          float* dst = reinterpret_cast<float*>(host.data() + off) + 2 * a;
+          dst[0] = (float)v.real(); dst[1] = (float)v.imag();
+        }
+      }
+      off += (size_t)parts[p].second * elt;
+    }
+    off = (off + 255) & ~(size_t)255;
+    // pointers are filled after the device buffer exists (store offsets for now)
+    if (op.kind == 2) {
+      d.e = (void*)starts[0]; d.em = (void*)starts[1]; d.ct = (void*)starts[2]; d.ctm = (void*)starts[3];
+    } else {
+      d.u = (void*)starts[0];
+    }
+    dl->ops.push_back(d);
+  }
+  void* dev = nullptr;
+  if (staged) {
+    if (h->staged_cap < total) {
+      if (h->staged.mem) { cudaFree(h->staged.mem); h->staged.mem = nullptr; }
+      cudaError_t ce = cudaMalloc(&h->staged.mem, total + 256);
+      if (ce != cudaSuccess) { cudaGetLastError(); return fail(h, MPDO_ERR_OOM, "layer staging"); }
+      h->staged_cap = total;
+    }
+    dev = h->staged.mem;
+  } else {
+    cudaError_t ce = cudaMalloc(&dev, total + 256);
+    if (ce != cudaSuccess) { cudaGetLastError(); return fail(h, MPDO_ERR_OOM, "layer upload"); }
+    dl->mem = dev;
+  }
+  CK(cudaMemcpyAsync(dev, host.data(), total, cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));  // host buffer is freed on return
+  char* base = static_cast<char*>(dev);
+  for (DevOp& d : dl->ops) {
+    if (d.kind == 2) {
+      d.e = base + (size_t)d.e; d.em = base + (size_t)d.em;
+      d.ct = base + (size_t)d.ct; d.ctm = base + (size_t)d.ctm;
+    } else {
+      d.u = base + (size_t)d.u;
+    }
+  }
+  return MPDO_OK;
+}
+
+int reset_stats(mpdo_ctx* h) {
+  DevStats z{};
+  z.ppt_theta_min = 1e300;
+  *h->hstats = z;
+  CK(cudaMemcpyAsync(h->dstats, h->hstats, sizeof(DevStats), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemsetAsync(h->dsc, 0, sizeof(StepScalars), h->st));
+  return MPDO_OK;
+}
+
+int read_stats(mpdo_ctx* h, mpdo_trunc_stats* out) {
+  CK(cudaMemcpyAsync(h->hstats, h->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (out) {
+    const DevStats& s = *h->hstats;
+    out->disc_bond_w = s.disc_bond_w;
+    out->disc_kraus_w = s.disc_kraus_w;
+    out->ppt_theta_min = s.ppt_theta_min;
+    out->ppt_infeasible = s.ppt_infeasible;
+    out->ppt_clamped = s.ppt_clamped;
+    out->chi_used_max = s.chi_used_max;
+    out->k_used_max = s.k_used_max;
+    out->n_updates = s.n_updates;
+  }
+  return MPDO_OK;
+}
+
+int run_ops(mpdo_ctx* h, const std::vector<DevOp>& ops, mpdo_trunc_stats* stats, int chi,
+            int kmax, int use_ppt) {
+  int rc = reset_stats(h);
+  if (rc) return rc;
+  rc = h->dbl ? apply_ops<double>(h, ops, chi, kmax, use_ppt)
+              : apply_ops<float>(h, ops, chi, kmax, use_ppt);
+  if (rc) return rc;
+  return read_stats(h, stats);
+}
+
+int init_state(mpdo_ctx* h, const double* v) {
+  double pl[6] = {1.0 / std::sqrt(2.0), 0, 1.0 / std::sqrt(2.0), 0, 0, 0};
+  if (!v) v = pl;
+  for (int a = 0; a < 6; ++a)
+    if (!std::isfinite(v[a])) return fail(h, MPDO_ERR_NUMERIC, "non-finite initial vector");
+  std::fill(h->bond.begin(), h->bond.end(), 1);
+  std::fill(h->kd.begin(), h->kd.end(), 1);
+  h->cur = 0;
+  h->rev = false;
+  h->centre = 0;
+  if (h->dbl)
+    CK(product_state<double>(h->st, v, static_cast<double2*>(h->sites[0]), (long)h->site_cap, h->n));
+  else
+    CK(product_state<float>(h->st, v, static_cast<float2*>(h->sites[0]), (long)h->site_cap, h->n));
+  CK(cudaStreamSynchronize(h->st));
+  return MPDO_OK;
+}
+
+// ---------------------------------------------------------------- observables
+template <typename R>
+int energy(mpdo_ctx* h, double J, double hx, double bz, double out[6]) {
+  using T = cx<R>;
+  cudaStream_t st = h->st;
+  const long chi = h->chi, K = h->kmax;
+  const long env = chi * chi, fsz = chi * 3 * K * chi;
+  size_t need = (2 * 6 * env + 2 * 6 * fsz) * sizeof(T) + 512;
+  if (h->obs_bytes < need) {
+    if (h->obs) cudaFree(h->obs);
+    h->obs = nullptr;
+    cudaError_t ce = cudaMalloc(&h->obs, need);
+    if (ce != cudaSuccess) { cudaGetLastError(); h->obs_bytes = 0; return fail(h, MPDO_ERR_OOM, "energy buffers"); }
+    h->obs_bytes = need;
+  }
+  T* ebuf[2] = {static_cast<T*>(h->obs), static_cast<T*>(h->obs) + 6 * env};
+  T* F = ebuf[1] + 6 * env;
+  T* G = F + 6 * fsz;
+  // initial envs (1x1): E0 = 1, EZ = 0, E1 = 0 for both automata
+  T init[6] = {one<R>(), zero<R>(), zero<R>(), one<R>(), zero<R>(), zero<R>()};
+  for (int a = 0; a < 6; ++a)
+    CK(cudaMemcpyAsync(ebuf[0] + a * env, &init[a], sizeof(T), cudaMemcpyHostToDevice, st));
+  int cur = 0;
+  for (int s = 0; s < h->n; ++s) {
+    const int dl = h->bond[s], k = h->kd[s], dr = h->bond[s + 1];
+    const T* A = static_cast<const T*>(h->site(h->cur, s));
+    const long cols = 3L * k * dr;
+    // F[a] = E[a]^T A   (dl x cols)
+    CK(cgemm<R>(st, OP_T, OP_N, dl, (int)cols, dl, ebuf[cur], dl, env, A, cols, 0, F, cols, fsz,
+                6, one<R>(), zero<R>()));
+    CK(energy_mix<R>(st, dl, (int)(k * dr), F, fsz, G, fsz, J, hx, bz));
+    // E'[a] = G[a]^T conj(A2), both as (dl*3*k) x dr
+    CK(cgemm<R>(st, OP_T, OP_R, dr, dr, dl * 3 * k, G, dr, fsz, A, dr, 0, ebuf[1 - cur], dr,
+                env, 6, one<R>(), zero<R>()));
+    cur = 1 - cur;
+  }
+  T res[6];
+  for (int a = 0; a < 6; ++a)
+    CK(cudaMemcpyAsync(&res[a], ebuf[cur] + a * env, sizeof(T), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int a = 0; a < 6; ++a) out[a] = (double)res[a].x;
+  return MPDO_OK;
+}
+
+template <typename R>
+int sample(mpdo_ctx* h, int ns, uint64_t seed, uint8_t* bits, double* probs) {
+  using T = cx<R>;
+  cudaStream_t st = h->st;
+  if (h->rev) {
+    int rc = reverse_chain<R>(h);
+    if (rc) return rc;
+  }
+  const int N = h->n;
+  const long chi = h->chi, K = h->kmax;
+  const long env = chi * chi, fsz = chi * 3 * K * chi;
+  // chunk of samples processed together
+  long chunk = (long)((size_t)1 << 30) / (long)(sizeof(T) * (2 * fsz + 5 * env));
+  if (chunk < 1) chunk = 1;
+  if (chunk > ns) chunk = ns;
+  size_t renv_bytes = (size_t)(N + 1) * env * sizeof(T);
+  size_t need = renv_bytes + (size_t)sizeof(T) * (fsz + chunk * (2 * fsz + 5 * env) + env) +
+                (size_t)ns * (N + 8) + 4096;
+  void* mem = nullptr;
+  cudaError_t ce = cudaMalloc(&mem, need);
+  if (ce != cudaSuccess) { cudaGetLastError(); return fail(h, MPDO_ERR_OOM, "sampling buffers"); }
+  std::unique_ptr<void, void (*)(void*)> guard(mem, [](void* p) { cudaFree(p); });
+  T* renv = static_cast<T*>(mem);                 // R_n, n = 0..N, each env
+  T* Y = renv + (N + 1) * env;                    // fsz
+  T* Ecur = Y + fsz;                              // chunk * env
+  T* Ef = Ecur + chunk * env;                     // chunk * fsz
+  T* Fp = Ef + chunk * fsz;                       // chunk * fsz
+  T* Ev = Fp + chunk * fsz;                       // chunk * 3 * env
+  T* Enext = Ev + chunk * 3 * env;                // chunk * env
+  uint8_t* dbits = reinterpret_cast<uint8_t*>(Enext + chunk * env);
+  double* dprob = reinterpret_cast<double*>(((uintptr_t)(dbits + (size_t)ns * N) + 15) & ~15);
+  // right environments with the identity: R_N = 1
+  T o = one<R>();
+  CK(cudaMemcpyAsync(renv + (long)N * env, &o, sizeof(T), cudaMemcpyHostToDevice, st));
+  for (int s = N - 1; s >= 0; --s) {
+    const int dl = h->bond[s], k = h->kd[s], dr = h->bond[s + 1];
+    const T* A = static_cast<const T*>(h->site(h->cur, s));
+    // Y = A (dl*3k x dr) R_{s+1} (dr x dr);  R_s = Y (dl x 3k*dr) A^+
+    CK(cgemm<R>(st, OP_N, OP_N, dl * 3 * k, dr, dr, A, dr, 0, renv + (long)(s + 1) * env, dr, 0,
+                Y, dr, 0, 1, one<R>(), zero<R>()));
+    CK(cgemm<R>(st, OP_N, OP_C, dl, dl, 3L * k * dr, Y, 3L * k * dr, 0, A, 3L * k * dr, 0,
+                renv + (long)s * env, dl, 0, 1, one<R>(), zero<R>()));
+  }
+  for (long c0 = 0; c0 < ns; c0 += chunk) {
+    const int cn = (int)std::min<long>(chunk, ns - c0);
+    // per-sample environments are packed: sample q at Ecur + q * dl * dl (dl = 1 here)
+    std::vector<T> ones(cn, one<R>());
+    CK(cudaMemcpyAsync(Ecur, ones.data(), sizeof(T) * cn, cudaMemcpyHostToDevice, st));
+    for (int s = 0; s < N; ++s) {
+      const int dl = h->bond[s], k = h->kd[s], dr = h->bond[s + 1];
+      const T* A = static_cast<const T*>(h->site(h->cur, s));
+      const long cols = 3L * k * dr, plane = (long)dl * k * dr;
+      // F_q = E_q^T A  (dl x cols), packed per sample (stride dl*cols = 3*plane)
+      CK(cgemm<R>(st, OP_T, OP_N, dl, (int)cols, dl, Ecur, dl, (long)dl * dl, A, cols, 0, Ef,
+                  cols, 3 * plane, cn, one<R>(), zero<R>()));
+      // Fp_q[v][l'][k][r] and Ap[v][l'][k][r] (into Y)
+      CK(swap12<T>(st, cn, dl, 3, (long)k * dr, Ef, Fp));
+      CK(swap12<T>(st, 1, dl, 3, (long)k * dr, A, Y));
+      for (int v = 0; v < 3; ++v)
+        CK(cgemm<R>(st, OP_T, OP_R, dr, dr, dl * k, Fp + v * plane, dr, 3 * plane, Y + v * plane,
+                    dr, 0, Ev + v * (long)dr * dr, dr, 3L * dr * dr, cn, one<R>(), zero<R>()));
+      CK(sample_pick<R>(st, cn, dr, Ev, renv + (long)(s + 1) * env, seed, s, s, N, Enext,
+                        dbits + (size_t)c0 * N, dprob + c0, s == N - 1 ? 1 : 0));
+      std::swap(Ecur, Enext);
+    }
+  }
+  if (bits) CK(cudaMemcpyAsync(bits, dbits, (size_t)ns * N, cudaMemcpyDeviceToHost, st));
+  if (probs) CK(cudaMemcpyAsync(probs, dprob, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return MPDO_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out) {
+  if (!cfg || !out) return fail(nullptr, MPDO_ERR_ARG, "null config or output");
+  if (cfg->n_sites < 2) return fail(nullptr, MPDO_ERR_ARG, "n_sites must be >= 2");
+  if (cfg->d != 3) return fail(nullptr, MPDO_ERR_ARG, "d must be 3");
+  if (cfg->chi_max < 1 || cfg->chi_max > 1024) return fail(nullptr, MPDO_ERR_ARG, "chi_max out of 1..1024");
+  if (cfg->k_max < 1 || cfg->k_max > 1024) return fail(nullptr, MPDO_ERR_ARG, "k_max out of 1..1024");
+  if (cfg->m_max < 1 || (long)cfg->m_max * cfg->k_max > 1024)
+    return fail(nullptr, MPDO_ERR_ARG, "m_max*k_max must be in 1..1024");
+  if (cfg->prec != MPDO_FP64 && cfg->prec != MPDO_C64)
+    return fail(nullptr, MPDO_ERR_ARG, "precision mode not available in this build");
+  std::unique_ptr<mpdo_ctx> h(new (std::nothrow) mpdo_ctx());
+  if (!h) return fail(nullptr, MPDO_ERR_OOM, "host allocation");
+  mpdo_ctx* hp = h.get();
+  h->cfg = *cfg;
+  h->st = static_cast<cudaStream_t>(cfg->cuda_stream);
+  h->n = cfg->n_sites;
+  h->chi = cfg->chi_max;
+  h->kmax = cfg->k_max;
+  h->mmax = cfg->m_max;
+  h->dbl = (cfg->prec == MPDO_FP64);
+  h->elt = h->dbl ? 16 : 8;
+  // Numerical-zero cuts.  Gram eigenvalues resolve only down to ~eps * max, so the cuts
+  // are applied there: bond lambda = s^2 > htol*lambda_0, inner w > kcut^2 * w_0.
+  const double eps = h->dbl ? 1e-16 : 6e-8;
+  h->gtol = 10 * eps;
+  double sv = cfg->sv_cutoff > 0 ? cfg->sv_cutoff : 1e-14;
+  h->htol = std::max(sv * sv, 10 * eps);
+  double kc = cfg->kraus_cutoff > 0 ? cfg->kraus_cutoff : 1e-14;
+  h->kcut = std::max(kc, std::sqrt(10 * eps));
+  h->max_sweeps = h->dbl ? 30 : 20;
+  h->bond.assign(h->n + 1, 1);
+  h->kd.assign(h->n, 1);
+  const long D = h->chi, K = h->kmax, M = h->mmax;
+  const long n3 = 3 * D, n9 = 9 * D, KM = K * M;
+  h->site_cap = (size_t)D * 3 * K * D;
+  int rc;
+  for (int b = 0; b < 2; ++b)
+    if ((rc = alloc_dev(hp, &h->sites[b], h->site_cap * h->elt * h->n))) return rc;
+  const size_t e = h->elt;
+  auto A = [&](void** p, size_t count) { return alloc_dev(hp, p, count * e); };
+  if ((rc = A(&h->wM, D * K * n3)) || (rc = A(&h->wGi, n3 * n3)) || (rc = A(&h->wGj, n3 * n3)) ||
+      (rc = A(&h->wVg, n3 * n3)) || (rc = A(&h->wR, n3 * n3)) || (rc = A(&h->wVs, n3 * n3)) ||
+      (rc = A(&h->wVr, n3 * n3)) || (rc = A(&h->wPhi, n9 * n9)) || (rc = A(&h->wX, n9 * n9)) ||
+      (rc = A(&h->wH, n9 * n9)) || (rc = A(&h->wU, n9 * n9)) || (rc = A(&h->wVgen, n9 * D)) ||
+      (rc = A(&h->wW, n9 * D)) || (rc = A(&h->wTmp, D * K * 3 * D)) ||
+      (rc = A(&h->wQ, D * 3 * M * n3)) || (rc = A(&h->wWB, D * 3 * M * K * D)) ||
+      (rc = A(&h->wBp, D * 3 * M * K * D)) || (rc = A(&h->wWK, KM * KM)) ||
+      (rc = A(&h->wVk, KM * KM)) || (rc = A(&h->wVks, KM * K)) || (rc = A(&h->wCn, K * D * 3 * D)))
+    return rc;
+  const size_t rsz = h->dbl ? 8 : 4;
+  if ((rc = alloc_dev(hp, &h->wRs, n3 * rsz)) || (rc = alloc_dev(hp, &h->wIrs, n3 * rsz)) ||
+      (rc = alloc_dev(hp, (void**)&h->wSig, n3 * 8)) || (rc = alloc_dev(hp, (void**)&h->wLam, n9 * 8)) ||
+      (rc = alloc_dev(hp, (void**)&h->wWv, KM * 8)) || (rc = alloc_dev(hp, (void**)&h->wF, K * 8)))
+    return rc;
+  const int ncap = (int)std::max(n9, KM);
+  size_t eb = h->dbl ? eig_work_bytes<double>(ncap) : eig_work_bytes<float>(ncap);
+  if ((rc = alloc_dev(hp, &h->eigmem, eb))) return rc;
+  if (h->dbl) eig_work_bind<double>(h->eig64, h->eigmem, ncap);
+  else eig_work_bind<float>(h->eig32, h->eigmem, ncap);
+  if ((rc = alloc_dev(hp, (void**)&h->dsc, sizeof(StepScalars))) ||
+      (rc = alloc_dev(hp, (void**)&h->dstats, sizeof(DevStats))))
+    return rc;
+  if (cudaMallocHost((void**)&h->hsc, sizeof(StepScalars)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->hstats, sizeof(DevStats)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, MPDO_ERR_OOM, "pinned host allocation");
+  }
+  rc = init_state(hp, init_site_vec);
+  if (rc) { g_err = h->err; return rc; }
+  *out = h.release();
+  return MPDO_OK;
+}
+
+int mpdo_reset(mpdo_t h, const double* v) {
+  if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
+  return init_state(h, v);
+}
+
+int mpdo_apply_layer(mpdo_t h, const mpdo_layer* layer, mpdo_trunc_stats* stats) {
+  if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
+  int rc = prepare_layer(h, layer, &h->staged, true);
+  if (rc) return rc;
+  return run_ops(h, h->staged.ops, stats, h->chi, h->kmax, h->cfg.use_ppt);
+}
+
+int mpdo_layer_upload(mpdo_t h, const mpdo_layer* layer, mpdo_dlayer* out) {
+  if (!h || !out) return fail(h, MPDO_ERR_ARG, "null handle or output");
+  std::unique_ptr<mpdo_dlayer_s> dl(new (std::nothrow) mpdo_dlayer_s());
+  if (!dl) return fail(h, MPDO_ERR_OOM, "host allocation");
+  int rc = prepare_layer(h, layer, dl.get(), false);
+  if (rc) return rc;
+  *out = dl.release();
+  return MPDO_OK;
+}
+
+int mpdo_apply_dlayer(mpdo_t h, mpdo_dlayer dl, mpdo_trunc_stats* stats) {
+  if (!h || !dl) return fail(h, MPDO_ERR_ARG, "null handle or layer");
+  return run_ops(h, dl->ops, stats, h->chi, h->kmax, h->cfg.use_ppt);
+}
+
+int mpdo_layer_free(mpdo_t h, mpdo_dlayer dl) {
+  if (!dl) return MPDO_OK;
+  if (dl->mem) cudaFree(dl->mem);
+  delete dl;
+  (void)h;
+  return MPDO_OK;
+}
+
+int mpdo_truncate(mpdo_t h, int chi_max, int k_max, int use_ppt, mpdo_trunc_stats* stats) {
+  if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
+  if (chi_max < 1 || chi_max > h->chi || k_max < 1 || k_max > h->kmax)
+    return fail(h, MPDO_ERR_ARG, "truncate limits must be within the handle's capacity");
+  // identity channel, one Kraus operator
+  std::vector<double> idop(2 * 81, 0.0);
+  for (int a = 0; a < 9; ++a) idop[2 * (a * 9 + a)] = 1.0;
+  std::vector<mpdo_op> ops;
+  int c = h->centre;
+  for (int i = c; i < h->n - 1; ++i) ops.push_back(mpdo_op{2, i, 1, idop.data()});
+  for (int i = h->n - 2; i >= 0; --i) ops.push_back(mpdo_op{2, i, 1, idop.data()});
+  mpdo_layer L{(int)ops.size(), ops.data()};
+  int rc = prepare_layer(h, &L, &h->staged, true);
+  if (rc) return rc;
+  return run_ops(h, h->staged.ops, stats, chi_max, k_max, use_ppt);
+}
+
+int mpdo_expect_energy(mpdo_t h, double J, double hx, double b, double* e_raw, double* e_success,
+                       double* success_prob, double* trace) {
+  if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
+  double r[6];
+  int rc = h->dbl ? energy<double>(h, J, hx, b, r) : energy<float>(h, J, hx, b, r);
+  if (rc) return rc;
+  // r: [0] tr(Pi rho) [2] tr(Pi H Pi rho) [3] tr(rho) [5] tr(H rho)
+  if (!(r[3] > 0) || !std::isfinite(r[3])) return fail(h, MPDO_ERR_NUMERIC, "zero trace");
+  if (e_raw) *e_raw = r[5] / r[3];
+  if (e_success) *e_success = r[0] > 0 ? r[2] / r[0] : NAN;
+  if (success_prob) *success_prob = r[0];
+  if (trace) *trace = r[3];
+  return MPDO_OK;
+}
+
+int mpdo_sample_probs(mpdo_t h, int n_samples, uint64_t seed, uint8_t* bits, double* probs) {
+  if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
+  if (n_samples < 0) return fail(h, MPDO_ERR_ARG, "n_samples < 0");
+  if (n_samples == 0) return MPDO_OK;
+  return h->dbl ? sample<double>(h, n_samples, seed, bits, probs)
+                : sample<float>(h, n_samples, seed, bits, probs);
+}
+
+int mpdo_get_dims(mpdo_t h, int* bond_dims, int* kraus_dims, int* centre) {
+  if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
+  for (int u = 0; u < h->n; ++u) {
+    int s = h->rev ? h->n - 1 - u : u;
+    if (kraus_dims) kraus_dims[u] = h->kd[s];
+    if (bond_dims && u < h->n - 1) bond_dims[u] = h->rev ? h->bond[s] : h->bond[s + 1];
+  }
+  if (centre) *centre = h->centre;
+  return MPDO_OK;
+}
+
+int mpdo_get_site(mpdo_t h, int n, double* out, size_t cap, int* dims) {
+  if (!h || !out || !dims) return fail(h, MPDO_ERR_ARG, "null argument");
+  if (n < 0 || n >= h->n) return fail(h, MPDO_ERR_ARG, "site out of range");
+  int s = h->rev ? h->n - 1 - n : n;
+  int dl = h->bond[s], k = h->kd[s], dr = h->bond[s + 1];
+  size_t cnt = (size_t)dl * 3 * k * dr;
+  if (cap < cnt) return fail(h, MPDO_ERR_ARG, "output capacity too small");
+  std::vector<double> tmp(2 * cnt);
+  if (h->dbl) {
+    CK(cudaMemcpyAsync(tmp.data(), h->site(h->cur, s), cnt * 16, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  } else {
+    std::vector<float> f(2 * cnt);
+    CK(cudaMemcpyAsync(f.data(), h->site(h->cur, s), cnt * 8, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (size_t a = 0; a < 2 * cnt; ++a) tmp[a] = f[a];
+  }
+  if (!h->rev) {
+    std::memcpy(out, tmp.data(), cnt * 16);
+    dims[0] = dl; dims[1] = 3; dims[2] = k; dims[3] = dr;
+  } else {
+    // storage [r_u][s][k][l_u] -> user [l_u][s][k][r_u]
+    for (int a = 0; a < dl; ++a)
+      for (int q = 0; q < 3; ++q)
+        for (int kk = 0; kk < k; ++kk)
+          for (int b = 0; b < dr; ++b) {
+            size_t src = (((size_t)a * 3 + q) * k + kk) * dr + b;
+            size_t dst = (((size_t)b * 3 + q) * k + kk) * dl + a;
+            out[2 * dst] = tmp[2 * src];
+            out[2 * dst + 1] = tmp[2 * src + 1];
+          }
+    dims[0] = dr; dims[1] = 3; dims[2] = k; dims[3] = dl;
+  }
+  return MPDO_OK;
+}
+
+int mpdo_destroy(mpdo_t h) {
+  if (!h) return MPDO_OK;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->staged.mem) cudaFree(h->staged.mem);
+  if (h->obs) cudaFree(h->obs);
+  if (h->hsc) cudaFreeHost(h->hsc);
+  if (h->hstats) cudaFreeHost(h->hstats);
+  delete h;
+  return MPDO_OK;
+}
+
+const char* mpdo_last_error(mpdo_t h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int mpdo_kernel_cgemm(int prec, int opa, int opb, int m, int n, int k, const void* a, long lda,
+                      long sa, const void* b, long ldb, long sb, void* c, long ldc, long sc,
+                      int batch, void* stream) {
+  if (opa < 0 || opa > 3 || opb < 0 || opb > 3 || m < 0 || n < 0 || k < 0 || batch < 0)
+    return fail(nullptr, MPDO_ERR_ARG, "bad gemm arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (prec == 0)
+    e = cgemm<double>(st, opa, opb, m, n, k, (const double2*)a, lda, sa, (const double2*)b, ldb,
+                      sb, (double2*)c, ldc, sc, batch, one<double>(), zero<double>());
+  else
+    e = cgemm<float>(st, opa, opb, m, n, k, (const float2*)a, lda, sa, (const float2*)b, ldb, sb,
+                     (float2*)c, ldc, sc, batch, one<float>(), zero<float>());
+  if (e != cudaSuccess) return fail(nullptr, MPDO_ERR_CUDA, cudaGetErrorString(e));
+  return MPDO_OK;
+}
+
+int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, void* stream) {
+  if (n < 1 || n > 4096 || !a || !v || !w) return fail(nullptr, MPDO_ERR_ARG, "bad heig arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* mem = nullptr;
+  size_t bytes = prec == 0 ? eig_work_bytes<double>(n) : eig_work_bytes<float>(n);
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) { cudaGetLastError(); return fail(nullptr, MPDO_ERR_OOM, "heig work"); }
+  cudaError_t e;
+  int* counters;
+  if (prec == 0) {
+    EigWork<double> wk;
+    eig_work_bind<double>(wk, mem, n);
+    counters = wk.counters;
+    e = heig<double>(st, n, (const double2*)a, n, (double2*)v, n, w, wk, 30);
+  } else {
+    EigWork<float> wk;
+    eig_work_bind<float>(wk, mem, n);
+    counters = wk.counters;
+    e = heig<float>(st, n, (const float2*)a, n, (float2*)v, n, w, wk, 20);
+  }
+  int sw = -1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&sw, counters + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(mem);
+  if (e != cudaSuccess) return fail(nullptr, MPDO_ERR_CUDA, cudaGetErrorString(e));
+  if (sweeps) *sweeps = sw;
+  return MPDO_OK;
+}
+
+}  // extern "C"

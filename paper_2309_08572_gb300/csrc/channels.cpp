@@ -1,0 +1,308 @@
+// Host channel builder (FP64, off the hot path): the noisy ZZ block of the QAOA layer in
+// the gate-level model and the layer's ordered op list.
+//
+// Local basis 0 = |0>, 1 = |1>, 2 = |r>.  Two-site operators are 9x9 on s_i*3 + s_j.
+//  * ZZ block (Sec. IV, Eq. HZ_block_representation): CNOT (I (x) exp(-i a S^z)) CNOT,
+//    CNOT = (I (x) Had) CZ (I (x) Had); Had and S^z act on the qubit levels, CZ flips the
+//    sign of |11>.
+//  * Crosstalk (Sec. III.B, reduced to the active pair): exp(-i phi n_r (x) n_r) first.
+//  * Post-promotion (Sec. IV.A): exp(-i dPP (|1><r| + |r><1|)) on both atoms after the block.
+//  * Noise: one unit of the single-atom Lindblad evolution with the jump operators of
+//    Sec. II, L_j = sqrt(g b_j)|j><r| and dephasing sqrt(gp/2)(|0><0| - |1><1|) (linear-rate
+//    reading), solved in closed form: r-population e^{-g}, qubit-Rydberg coherences
+//    e^{-g/2 - gp/4}, rho_01 e^{-gp}, b_j (1 - e^{-g}) of the r-population moved to |j>
+//    (the dark share b_d leaves the simulated space).
+//  * The Kraus set is read off the Choi matrix of the composed superoperator by a cyclic
+//    Jacobi eigendecomposition (eigenvalues below eta * lambda_max dropped).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "../../include/mpdo.h"
+
+namespace {
+
+using zc = std::complex<double>;
+using Mat = std::vector<zc>;  // row-major square
+
+Mat eye(int n) {
+  Mat m(n * n, 0.0);
+  for (int i = 0; i < n; ++i) m[i * n + i] = 1.0;
+  return m;
+}
+Mat matmul(const Mat& a, const Mat& b, int n) {
+  Mat c(n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      zc aik = a[i * n + k];
+      if (aik == 0.0) continue;
+      for (int j = 0; j < n; ++j) c[i * n + j] += aik * b[k * n + j];
+    }
+  return c;
+}
+Mat kron(const Mat& a, int na, const Mat& b, int nb) {
+  int n = na * nb;
+  Mat c(n * n);
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < na; ++j)
+      for (int k = 0; k < nb; ++k)
+        for (int l = 0; l < nb; ++l) c[(i * nb + k) * n + j * nb + l] = a[i * na + j] * b[k * nb + l];
+  return c;
+}
+Mat dagger(const Mat& a, int n) {
+  Mat c(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) c[j * n + i] = std::conj(a[i * n + j]);
+  return c;
+}
+Mat conjm(const Mat& a) {
+  Mat c(a.size());
+  for (size_t i = 0; i < a.size(); ++i) c[i] = std::conj(a[i]);
+  return c;
+}
+
+// Cyclic two-sided Jacobi for a Hermitian matrix: a = V diag(w) V^+.
+void jacobi_herm(Mat a, int n, std::vector<double>& w, Mat& v) {
+  v = eye(n);
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0, diag = 0;
+    for (int i = 0; i < n; ++i) {
+      diag += std::norm(a[i * n + i]);
+      for (int j = i + 1; j < n; ++j) off += std::norm(a[i * n + j]);
+    }
+    if (off <= 1e-32 * (diag + off) || off == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        zc g = a[p * n + q];
+        double ag = std::abs(g);
+        if (ag < 1e-300) continue;
+        double al = a[p * n + p].real(), be = a[q * n + q].real();
+        double tau = (be - al) / (2 * ag);
+        double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1 + tau * tau));
+        double c = 1 / std::sqrt(1 + t * t), s = t * c;
+        zc e = g / ag;
+        // columns: a <- a U, U = [[c, s e], [-s conj(e), c]] on (p, q)
+        for (int r = 0; r < n; ++r) {
+          zc x = a[r * n + p], y = a[r * n + q];
+          a[r * n + p] = c * x - s * std::conj(e) * y;
+          a[r * n + q] = s * e * x + c * y;
+          zc vx = v[r * n + p], vy = v[r * n + q];
+          v[r * n + p] = c * vx - s * std::conj(e) * vy;
+          v[r * n + q] = s * e * vx + c * vy;
+        }
+        // rows: a <- U^+ a
+        for (int col = 0; col < n; ++col) {
+          zc x = a[p * n + col], y = a[q * n + col];
+          a[p * n + col] = c * x - s * e * y;
+          a[q * n + col] = s * std::conj(e) * x + c * y;
+        }
+        a[p * n + q] = 0.0;
+        a[q * n + p] = 0.0;
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = a[i * n + i].real();
+}
+
+// exp(-i theta h), h Hermitian
+Mat expmh(double theta, const Mat& h, int n) {
+  std::vector<double> w;
+  Mat v;
+  jacobi_herm(h, n, w, v);
+  Mat d(n * n, 0.0);
+  for (int i = 0; i < n; ++i) d[i * n + i] = std::exp(zc(0, -theta * w[i]));
+  return matmul(matmul(v, d, n), dagger(v, n), n);
+}
+
+Mat op3(std::initializer_list<zc> vals) { return Mat(vals); }
+
+Mat zq() { return op3({1, 0, 0, 0, -1, 0, 0, 0, 0}); }
+Mat xq() { return op3({0, 1, 0, 1, 0, 0, 0, 0, 0}); }
+Mat nr() { return op3({0, 0, 0, 0, 0, 0, 0, 0, 1}); }
+Mat hadq() {
+  double r = 1 / std::sqrt(2.0);
+  return op3({r, r, 0, r, -r, 0, 0, 0, 1});
+}
+
+// superoperator of rho -> U rho U^+ on row-major vec: U (x) conj(U)
+Mat unitary_superop(const Mat& u, int n) { return kron(u, n, conjm(u), n); }
+
+// closed-form single-atom noise superoperator (9x9 on row-major vec of a 3x3 rho)
+Mat noise_superop(double g, double gp, double b0, double b1) {
+  Mat s(81, 0.0);
+  auto idx = [](int a, int b) { return a * 3 + b; };
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double f;
+      if ((a == 2) != (b == 2)) f = std::exp(-g / 2 - gp / 4);
+      else if (a == 2 && b == 2) f = std::exp(-g);
+      else if (a != b) f = std::exp(-gp);
+      else f = 1.0;
+      s[idx(a, b) * 9 + idx(a, b)] = f;
+    }
+  s[idx(0, 0) * 9 + idx(2, 2)] += b0 * (1 - std::exp(-g));
+  s[idx(1, 1) * 9 + idx(2, 2)] += b1 * (1 - std::exp(-g));
+  return s;
+}
+
+// two-site superoperator of n1 (x) n1: rows/cols of the product are (a,a',b,b'),
+// two-site row-major vec is ((a,b),(a',b')).
+Mat two_site_product(const Mat& n1) {
+  Mat p = kron(n1, 9, n1, 9);  // 81 x 81 on (a,a')(b,b')
+  Mat out(81 * 81);
+  for (int a = 0; a < 3; ++a)
+    for (int ap = 0; ap < 3; ++ap)
+      for (int b = 0; b < 3; ++b)
+        for (int bp = 0; bp < 3; ++bp)
+          for (int c = 0; c < 3; ++c)
+            for (int cp = 0; cp < 3; ++cp)
+              for (int e = 0; e < 3; ++e)
+                for (int ep = 0; ep < 3; ++ep) {
+                  int rin = ((a * 3 + ap) * 3 + b) * 3 + bp;
+                  int cin = ((c * 3 + cp) * 3 + e) * 3 + ep;
+                  int rout = ((a * 3 + b) * 3 + ap) * 3 + bp;
+                  int cout = ((c * 3 + e) * 3 + cp) * 3 + ep;
+                  out[rout * 81 + cout] = p[rin * 81 + cin];
+                }
+  return out;
+}
+
+// Kraus set from a superoperator on n-dim rho (row-major vec), via the Choi reshuffle
+// C[(a,b),(a',b')] = S[(a,a'),(b,b')].
+int kraus_from_superop(const Mat& s, int n, double eta, std::vector<Mat>& out) {
+  int n2 = n * n;
+  Mat c(n2 * n2);
+  for (int a = 0; a < n; ++a)
+    for (int ap = 0; ap < n; ++ap)
+      for (int b = 0; b < n; ++b)
+        for (int bp = 0; bp < n; ++bp)
+          c[(a * n + b) * n2 + ap * n + bp] = s[(a * n + ap) * n2 + b * n + bp];
+  // Hermitian part
+  for (int i = 0; i < n2; ++i)
+    for (int j = i; j < n2; ++j) {
+      zc m = 0.5 * (c[i * n2 + j] + std::conj(c[j * n2 + i]));
+      c[i * n2 + j] = m;
+      c[j * n2 + i] = std::conj(m);
+    }
+  std::vector<double> w;
+  Mat v;
+  jacobi_herm(c, n2, w, v);
+  std::vector<int> ord(n2);
+  for (int i = 0; i < n2; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return w[x] > w[y]; });
+  double wmax = w[ord[0]];
+  if (!(wmax > 0)) return MPDO_ERR_NUMERIC;
+  out.clear();
+  for (int k : ord) {
+    if (w[k] <= eta * wmax) break;
+    double sq = std::sqrt(w[k]);
+    Mat e(n2);
+    for (int i = 0; i < n2; ++i) e[i] = sq * v[i * n2 + k];
+    out.push_back(e);
+  }
+  return MPDO_OK;
+}
+
+Mat zz_block(double angle) {
+  Mat had2 = kron(eye(3), 3, hadq(), 3);
+  Mat cz = eye(9);
+  cz[4 * 9 + 4] = -1.0;
+  Mat cnot = matmul(matmul(had2, cz, 9), had2, 9);
+  Mat rz = kron(eye(3), 3, expmh(angle, zq(), 3), 3);
+  return matmul(matmul(cnot, rz, 9), cnot, 9);
+}
+
+int block_channel(double angle_zz, double gd, double gp, double phi, double dpp, double b0,
+                  double b1, double bd, const Mat* post_l, const Mat* post_r, double eta,
+                  std::vector<Mat>& kraus) {
+  (void)bd;
+  Mat u = zz_block(angle_zz);
+  if (phi != 0.0) u = matmul(u, expmh(phi, kron(nr(), 3, nr(), 3), 9), 9);
+  if (dpp != 0.0) {
+    Mat gen = op3({0, 0, 0, 0, 0, 1, 0, 1, 0});
+    Mat pp = expmh(dpp, gen, 3);
+    u = matmul(kron(pp, 3, pp, 3), u, 9);
+  }
+  Mat s = matmul(two_site_product(noise_superop(gd, gp, b0, b1)), unitary_superop(u, 9), 81);
+  if (post_l || post_r) {
+    Mat v = kron(post_l ? *post_l : eye(3), 3, post_r ? *post_r : eye(3), 3);
+    s = matmul(unitary_superop(v, 9), s, 81);
+  }
+  return kraus_from_superop(s, 9, eta, kraus);
+}
+
+bool finite_all(std::initializer_list<double> xs) {
+  for (double x : xs)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" int mpdo_build_block_channel(double angle_zz, double gamma_diss, double gamma_deph,
+                                        double xtalk_phase, double delta_pp, double b0, double b1,
+                                        double bd, const double* post_left,
+                                        const double* post_right, double eta, double* out,
+                                        int cap, int* n_kraus) {
+  if (!out || !n_kraus || cap < 1) return MPDO_ERR_ARG;
+  if (!finite_all({angle_zz, gamma_diss, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd, eta}))
+    return MPDO_ERR_NUMERIC;
+  if (gamma_diss < 0 || gamma_deph < 0 || b0 < 0 || b1 < 0 || bd < 0) return MPDO_ERR_ARG;
+  Mat pl, pr;
+  if (post_left) {
+    pl.resize(9);
+    for (int i = 0; i < 9; ++i) pl[i] = zc(post_left[2 * i], post_left[2 * i + 1]);
+  }
+  if (post_right) {
+    pr.resize(9);
+    for (int i = 0; i < 9; ++i) pr[i] = zc(post_right[2 * i], post_right[2 * i + 1]);
+  }
+  std::vector<Mat> k;
+  int rc = block_channel(angle_zz, gamma_diss, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd,
+                         post_left ? &pl : nullptr, post_right ? &pr : nullptr, eta, k);
+  if (rc) return rc;
+  *n_kraus = (int)k.size();
+  if ((int)k.size() > cap) return MPDO_ERR_ARG;
+  for (size_t m = 0; m < k.size(); ++m)
+    for (int i = 0; i < 81; ++i) {
+      out[(m * 81 + i) * 2] = k[m][i].real();
+      out[(m * 81 + i) * 2 + 1] = k[m][i].imag();
+    }
+  return MPDO_OK;
+}
+
+extern "C" int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double beta, double J,
+                                     double bz, double gamma_diss, double gamma_deph,
+                                     double xtalk_phase, double delta_pp, double b0, double b1,
+                                     double bd, double eta, int* sites, int* ms, double* out,
+                                     size_t cap) {
+  if (n_sites < 2 || k < 0 || !sites || !ms || !out) return MPDO_ERR_ARG;
+  if (!finite_all({alpha, beta, J, bz})) return MPDO_ERR_NUMERIC;
+  // one-site gate exp(-i beta S^x) exp(-i b J alpha S^z), folded after the last block
+  Mat v = matmul(expmh(beta, xq(), 3), expmh(bz * J * alpha, zq(), 3), 3);
+  std::vector<Mat> both, mid;
+  int rc = block_channel(J * alpha, gamma_diss, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd,
+                         &v, &v, eta, both);
+  if (rc) return rc;
+  const bool ltr = (k % 2 == 0);
+  rc = block_channel(J * alpha, gamma_diss, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd,
+                     ltr ? &v : nullptr, ltr ? nullptr : &v, eta, mid);
+  if (rc) return rc;
+  size_t off = 0;
+  for (int q = 0; q < n_sites - 1; ++q) {
+    int i = ltr ? q : n_sites - 2 - q;
+    bool last = ltr ? (i == n_sites - 2) : (i == 0);
+    const std::vector<Mat>& ch = last ? both : mid;
+    sites[q] = i;
+    ms[q] = (int)ch.size();
+    if (off + ch.size() * 81 > cap) return MPDO_ERR_ARG;
+    for (const Mat& e : ch)
+      for (int a = 0; a < 81; ++a) {
+        out[2 * off] = e[a].real();
+        out[2 * off + 1] = e[a].imag();
+        ++off;
+      }
+  }
+  return MPDO_OK;
+}

@@ -1,0 +1,521 @@
+// Elementwise and small kernels of the MPDO update, observables and sampling.
+// Every kernel here is memory- or latency-bound; the contractions are in gemm.cu.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mpdo {
+namespace {
+
+inline int nblocks(long total, int threads = 256, int cap = 16384) {
+  long b = (total + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// out[i0][i2][i1][i3] = in[i0][i1][i2][i3]
+template <typename T>
+__global__ void swap12_kernel(long n0, long n1, long n2, long n3, const T* __restrict__ in,
+                              T* __restrict__ out) {
+  long total = n0 * n1 * n2 * n3;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long i3 = e % n3;
+    long r = e / n3;
+    long i1 = r % n1;
+    r /= n1;
+    long i2 = r % n2;
+    long i0 = r / n2;
+    // e enumerates the OUTPUT [i0][i2][i1][i3]
+    out[e] = in[((i0 * n1 + i1) * n2 + i2) * n3 + i3];
+  }
+}
+
+// site [l][s][k][r] -> [r][s][k][l]
+template <typename T>
+__global__ void reverse_site_kernel(int dl, int d, int k, int dr, const T* __restrict__ in,
+                                    T* __restrict__ out) {
+  long total = (long)dl * d * k * dr;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    // output index [r][s][k][l]
+    long l = e % dl;
+    long t = e / dl;
+    long kk = t % k;
+    t /= k;
+    long s = t % d;
+    long r = t / d;
+    out[e] = in[((l * d + s) * k + kk) * dr + r];
+  }
+}
+
+// A[l][s][k][r] <- sum_s' U[s][s'] A[l][s'][k][r]
+template <typename R>
+__global__ void one_site_kernel(int dl, int k, int dr, const cx<R>* __restrict__ u,
+                                cx<R>* a) {
+  long plane = (long)k * dr;
+  long total = (long)dl * plane;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long l = e / plane, q = e % plane;
+    cx<R>* base = a + l * 3 * plane + q;
+    cx<R> x0 = base[0], x1 = base[plane], x2 = base[2 * plane];
+    for (int s = 0; s < 3; ++s) {
+      cx<R> acc = mkc<R>(0, 0);
+      cfma(acc, u[s * 3 + 0], x0);
+      cfma(acc, u[s * 3 + 1], x1);
+      cfma(acc, u[s * 3 + 2], x2);
+      base[s * plane] = acc;
+    }
+  }
+}
+
+template <typename R>
+__global__ void product_state_kernel(cx<R> v0, cx<R> v1, cx<R> v2, cx<R>* base, long stride,
+                                     int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    base[i * stride + 0] = v0;
+    base[i * stride + 1] = v1;
+    base[i * stride + 2] = v2;
+  }
+}
+
+// rs/irs from the left-Gram spectrum sigma (descending): numerical rank cut.
+template <typename R>
+__global__ void gram_mask_kernel(int n, const double* __restrict__ sig, double gtol,
+                                 R* rs, R* irs, StepScalars* sc) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  double s0 = sig[0];
+  bool bad = !(s0 > 0.0) || !isfinite(s0);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double s = sig[c];
+    if (!bad && s > gtol * s0) {
+      rs[c] = (R)sqrt(s);
+      irs[c] = (R)(1.0 / sqrt(s));
+      atomicAdd(&cnt, 1);
+    } else {
+      rs[c] = 0;
+      irs[c] = 0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sc->rank_g = cnt;
+    if (bad) sc->flags |= 1;
+  }
+}
+
+// R[c][x] = rs[c] conj(V[x][c]); Vs[x][c] = V[x][c] irs[c]; Vr[x][c] = V[x][c] rs[c]
+template <typename R>
+__global__ void gram_factor_kernel(int n, const cx<R>* __restrict__ v, const R* __restrict__ rs,
+                                   const R* __restrict__ irs, cx<R>* rmat, cx<R>* vs, cx<R>* vr) {
+  long total = (long)n * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    int x = (int)(e / n), c = (int)(e % n);
+    cx<R> val = v[e];
+    vs[e] = cscale(val, irs[c]);
+    vr[e] = cscale(val, rs[c]);
+    rmat[(long)c * n + x] = cscale(cconj(val), rs[c]);
+  }
+}
+
+// Phi[(S,s,b),(S2,s2,b2)] = sum_{t,t2} C[(S,s,t),(S2,s2,t2)] Gj[(b,t),(b2,t2)]
+template <typename R>
+__global__ void build_phi_kernel(int dm, const cx<R>* __restrict__ ct,
+                                 const cx<R>* __restrict__ gj, cx<R>* phi) {
+  long n = 9L * dm;
+  long total = n * n;
+  long ldg = 3L * dm;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long row = e / n, col = e % n;
+    int ss = (int)(row / dm), b = (int)(row % dm);     // ss = S*3 + s
+    int ss2 = (int)(col / dm), b2 = (int)(col % dm);
+    cx<R> acc = mkc<R>(0, 0);
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+#pragma unroll
+      for (int t2 = 0; t2 < 3; ++t2)
+        cfma(acc, ct[(ss * 3 + t) * 27 + ss2 * 3 + t2], gj[(b * 3 + t) * ldg + b2 * 3 + t2]);
+    phi[e] = acc;
+  }
+}
+
+// Bond cut on the spectrum lam (descending, n): keep <= chi values above htol*lam0.
+__global__ void bond_select_kernel(int n, const double* __restrict__ lam, double htol, int chi,
+                                   StepScalars* sc, DevStats* st) {
+  __shared__ double red_tot[256], red_kept[256];
+  __shared__ int s_keep;
+  double l0 = lam[0];
+  bool bad = !(l0 > 0.0) || !isfinite(l0);
+  if (threadIdx.x == 0) {
+    int k = 0;
+    if (!bad) {
+      while (k < n && k < chi && lam[k] > htol * l0) ++k;
+    }
+    if (k < 1) k = 1;
+    s_keep = k;
+  }
+  __syncthreads();
+  int keep = s_keep;
+  double t = 0, kp = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = lam[i] > 0 ? lam[i] : 0.0;
+    t += v;
+    if (i < keep) kp += v;
+  }
+  red_tot[threadIdx.x] = t;
+  red_kept[threadIdx.x] = kp;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red_tot[threadIdx.x] += red_tot[threadIdx.x + s];
+      red_kept[threadIdx.x] += red_kept[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double tot = red_tot[0], kept = red_kept[0];
+    sc->keep = keep;
+    sc->tot = tot;
+    sc->kept = kept;
+    sc->renorm = (kept > 0) ? sqrt(tot / kept) : 0.0;
+    if (bad || !(kept > 0) || !isfinite(tot)) sc->flags |= 1;
+    st->disc_bond_w += (tot > 0) ? (tot - kept) / tot : 0.0;
+    if (keep > st->chi_used_max) st->chi_used_max = keep;
+    st->n_updates += 1;
+  }
+}
+
+// Q[(b',T,m),(b,t)] = renorm * sum_{S,s} conj(W[(S,s,b)][b']) E[m][(S,T),(s,t)]
+template <typename R>
+__global__ void make_q_kernel(int dm, int keep, int m_ops, const cx<R>* __restrict__ w,
+                              const cx<R>* __restrict__ e, const StepScalars* sc, cx<R>* q) {
+  long cols = 3L * dm;
+  long rows = (long)keep * 3 * m_ops;
+  long total = rows * cols;
+  R ren = (R)sc->renorm;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long)gridDim.x * blockDim.x) {
+    long row = idx / cols, col = idx % cols;
+    int m = (int)(row % m_ops);
+    long r2 = row / m_ops;
+    int T = (int)(r2 % 3);
+    int bp = (int)(r2 / 3);
+    int b = (int)(col / 3), t = (int)(col % 3);
+    const cx<R>* em = e + (long)m * 81;
+    cx<R> acc = mkc<R>(0, 0);
+#pragma unroll
+    for (int S = 0; S < 3; ++S)
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        cx<R> wv = w[((long)(S * 3 + s) * dm + b) * keep + bp];
+        cfma(acc, cconj(wv), em[(S * 3 + T) * 9 + s * 3 + t]);
+      }
+    q[idx] = cscale(acc, ren);
+  }
+}
+
+// Inner-index cut + purity-preserving truncation (Sec. III.D Eqs. xiformula / ppt with
+// T = 1, P = identity; theta = 0 when infeasible; clamp negatives; keep the trace).
+// Writes f[k] = sqrt(Lambda~_k / w_k) for k < kk.
+__global__ void kraus_select_kernel(int n, const double* __restrict__ w, double kcut, int kmax,
+                                    int use_ppt, double* f, StepScalars* sc, DevStats* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double w0 = w[0] > 0 ? w[0] : 0.0;
+  bool bad = !(w0 > 0.0) || !isfinite(w0);
+  int kk = 0;
+  if (!bad) {
+    double thr = kcut * kcut * w0;
+    while (kk < n && kk < kmax && w[kk] > thr) ++kk;
+  }
+  if (kk < 1) kk = 1;
+  double sum = 0, sq = 0, sumk = 0, sqk = 0;
+  for (int i = 0; i < n; ++i) {
+    double v = w[i] > 0 ? w[i] : 0.0;
+    sum += v;
+    sq += v * v;
+    if (i < kk) { sumk += v; sqk += v * v; }
+  }
+  double theta = 0.0;
+  int infeas = 0, clamped = 0;
+  double lt[1024];
+  if (use_ppt && !bad) {
+    double nl = sqrt(sq), nlp = sqrt(sqk);
+    double nt = sqrt((double)n), ntp = sqrt((double)kk);
+    double cos_phi = sum / (nl * nt);
+    double cos_sig = sumk / (nlp * ntp);
+    if (cos_sig > 1.0) cos_sig = 1.0;
+    double ratio = nt * cos_phi / ntp;
+    if (ratio > 1.0) { infeas = 1; theta = 0.0; } else { theta = acos(ratio); }
+    double sigma = acos(cos_sig);
+    double x = (sigma == 0.0) ? 0.0 : tan(theta) / tan(sigma) - 1.0;
+    double lsum = 0;
+    for (int i = 0; i < kk; ++i) {
+      double lp = w[i] > 0 ? w[i] : 0.0;
+      double v = (sigma == 0.0) ? lp : lp + x * (lp - nlp * cos_sig / ntp);
+      if (v < 0) { v = 0; ++clamped; }
+      lt[i] = v;
+      lsum += v;
+    }
+    double sc_tr = (lsum > 0) ? sum / lsum : 0.0;
+    for (int i = 0; i < kk; ++i) lt[i] *= sc_tr;
+  } else {
+    double sc_tr = (sumk > 0) ? sum / sumk : 0.0;
+    for (int i = 0; i < kk; ++i) lt[i] = (w[i] > 0 ? w[i] : 0.0) * sc_tr;
+  }
+  for (int i = 0; i < kk; ++i) {
+    double wi = w[i];
+    f[i] = (wi > 0) ? sqrt(lt[i] / wi) : 0.0;
+  }
+  sc->kkeep = kk;
+  sc->ktot = sum;
+  sc->theta = theta;
+  sc->infeasible = infeas;
+  sc->clamped = clamped;
+  if (bad) sc->flags |= 1;
+  st->disc_kraus_w += (sum > 0) ? (sum - sumk) / sum : 0.0;
+  if (use_ppt && theta < st->ppt_theta_min) st->ppt_theta_min = theta;
+  st->ppt_infeasible += infeas;
+  st->ppt_clamped += clamped;
+  if (kk > st->k_used_max) st->k_used_max = kk;
+}
+
+// Vks[kappa][k] = V[kappa][k] * f[k], k < kk (V has leading dimension ldv)
+template <typename R>
+__global__ void scale_vk_kernel(int n, int kk, const cx<R>* __restrict__ v, long ldv,
+                                const double* __restrict__ f, cx<R>* out) {
+  long total = (long)n * kk;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    int r = (int)(e / kk), c = (int)(e % kk);
+    out[e] = cscale(v[(long)r * ldv + c], (R)f[c]);
+  }
+}
+
+// Energy automaton, one-site step: from F0, FZ, F1 (= env^T A for the three states)
+// form G0 = P F0, GZ = Z F0, G1 = P F1 + (-h X - bJ Z) F0 - J Z FZ on the s index.
+// Layout of F*: [l'][s][k][r] with plane = k*dr; proj = 1 uses P = |0><0|+|1><1|,
+// proj = 0 uses the identity.  Six automata are stacked: [0..2] projected, [3..5] raw.
+template <typename R>
+__global__ void energy_mix_kernel(int dl, int plane, const cx<R>* __restrict__ f, long fstride,
+                                  cx<R>* g, long gstride, double J, double hx, double bz) {
+  long total = (long)dl * plane;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long l = e / plane, q = e % plane;
+    long off = l * 3 * plane + q;
+    for (int proj = 1; proj >= 0; --proj) {
+      int base = proj ? 0 : 3;
+      const cx<R>* f0 = f + (base + 0) * fstride + off;
+      const cx<R>* fz = f + (base + 1) * fstride + off;
+      const cx<R>* f1 = f + (base + 2) * fstride + off;
+      cx<R>* g0 = g + (base + 0) * gstride + off;
+      cx<R>* gz = g + (base + 1) * gstride + off;
+      cx<R>* g1 = g + (base + 2) * gstride + off;
+      cx<R> a0 = f0[0], a1 = f0[plane], a2 = f0[2 * plane];
+      cx<R> z0 = fz[0], z1 = fz[plane];
+      cx<R> b0 = f1[0], b1 = f1[plane], b2 = f1[2 * plane];
+      // G0
+      g0[0] = a0;
+      g0[plane] = a1;
+      g0[2 * plane] = proj ? mkc<R>(0, 0) : a2;
+      // GZ: Z = diag(1, -1, 0)
+      gz[0] = a0;
+      gz[plane] = cscale(a1, R(-1));
+      gz[2 * plane] = mkc<R>(0, 0);
+      // G1 = P F1 + (-h X - bJ Z) F0 - J Z FZ  (X swaps s' <- s on the qubit levels)
+      R h = (R)hx, bj = (R)(bz * J), jj = (R)J;
+      cx<R> o0 = cadd(b0, cadd(cscale(a1, -h), cscale(a0, -bj)));
+      o0 = cadd(o0, cscale(z0, -jj));
+      cx<R> o1 = cadd(b1, cadd(cscale(a0, -h), cscale(a1, bj)));
+      o1 = cadd(o1, cscale(z1, jj));
+      g1[0] = o0;
+      g1[plane] = o1;
+      g1[2 * plane] = proj ? mkc<R>(0, 0) : b2;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- sampling
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2,
+                                             uint32_t& c3, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+  uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+  uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+  c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+}
+
+// Philox4x32-10 (Salmon et al., SC'11) on counter (site, sample, 0, 0), key = seed.
+__device__ double philox_uniform(uint64_t seed, uint32_t sample, uint32_t site) {
+  uint32_t c0 = site, c1 = sample, c2 = 0, c3 = 0;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    philox_round(c0, c1, c2, c3, k0, k1);
+  }
+  uint64_t v = ((uint64_t)c0 << 21) | (uint64_t)(c1 >> 11);
+  return (double)v * 0x1.0p-53;
+}
+
+// q[smp][v] = sum_{r,r'} Ev[smp][v][r][r'] Rt[r][r'] ; pick v; copy chosen env.
+template <typename R>
+__global__ void sample_pick_kernel(int dr, const cx<R>* __restrict__ ev, const cx<R>* __restrict__ rt,
+                                   uint64_t seed, int site, int site_user, int n_sites,
+                                   cx<R>* env_out, uint8_t* bits, double* probs, int last) {
+  int smp = blockIdx.x;
+  long plane = (long)dr * dr;
+  const cx<R>* base = ev + (long)smp * 3 * plane;
+  __shared__ double red[3][256];
+  double q[3] = {0, 0, 0};
+  for (long e = threadIdx.x; e < plane; e += blockDim.x) {
+    cx<R> rv = rt[e];
+    for (int v = 0; v < 3; ++v) {
+      cx<R> x = base[v * plane + e];
+      q[v] += (double)x.x * rv.x - (double)x.y * rv.y;
+    }
+  }
+  for (int v = 0; v < 3; ++v) red[v][threadIdx.x] = q[v];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int v = 0; v < 3; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+    __syncthreads();
+  }
+  __shared__ int pick;
+  if (threadIdx.x == 0) {
+    double q0 = red[0][0] > 0 ? red[0][0] : 0, q1 = red[1][0] > 0 ? red[1][0] : 0,
+           q2 = red[2][0] > 0 ? red[2][0] : 0;
+    double tot = q0 + q1 + q2;
+    double u = philox_uniform(seed, (uint32_t)smp, (uint32_t)site_user);
+    int v = 2;
+    if (u < q0 / tot) v = 0;
+    else if (u < (q0 + q1) / tot) v = 1;
+    pick = v;
+    bits[(long)smp * n_sites + site_user] = (uint8_t)v;
+    if (last) {
+      double pv = (v == 0) ? red[0][0] : (v == 1 ? red[1][0] : red[2][0]);
+      probs[smp] = pv;
+    }
+  }
+  __syncthreads();
+  const cx<R>* src = base + pick * plane;
+  for (long e = threadIdx.x; e < plane; e += blockDim.x) env_out[(long)smp * plane + e] = src[e];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers
+template <typename T>
+cudaError_t swap12(cudaStream_t st, long n0, long n1, long n2, long n3, const T* in, T* out) {
+  long total = n0 * n1 * n2 * n3;
+  if (total <= 0) return cudaSuccess;
+  swap12_kernel<T><<<nblocks(total), 256, 0, st>>>(n0, n1, n2, n3, in, out);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t reverse_site(cudaStream_t st, int dl, int d, int k, int dr, const T* in, T* out) {
+  long total = (long)dl * d * k * dr;
+  reverse_site_kernel<T><<<nblocks(total), 256, 0, st>>>(dl, d, k, dr, in, out);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t one_site(cudaStream_t st, int dl, int k, int dr, const cx<R>* u, cx<R>* a) {
+  long total = (long)dl * k * dr;
+  one_site_kernel<R><<<nblocks(total), 256, 0, st>>>(dl, k, dr, u, a);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t product_state(cudaStream_t st, const double* v, cx<R>* base, long stride, int n) {
+  product_state_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(
+      mkc<R>((R)v[0], (R)v[1]), mkc<R>((R)v[2], (R)v[3]), mkc<R>((R)v[4], (R)v[5]), base, stride,
+      n);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t gram_mask(cudaStream_t st, int n, const double* sig, double gtol, R* rs, R* irs,
+                      StepScalars* sc) {
+  gram_mask_kernel<R><<<1, 256, 0, st>>>(n, sig, gtol, rs, irs, sc);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t gram_factor(cudaStream_t st, int n, const cx<R>* v, const R* rs, const R* irs,
+                        cx<R>* rmat, cx<R>* vs, cx<R>* vr) {
+  gram_factor_kernel<R><<<nblocks((long)n * n), 256, 0, st>>>(n, v, rs, irs, rmat, vs, vr);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t build_phi(cudaStream_t st, int dm, const cx<R>* ct, const cx<R>* gj, cx<R>* phi) {
+  long n = 9L * dm;
+  build_phi_kernel<R><<<nblocks(n * n), 256, 0, st>>>(dm, ct, gj, phi);
+  return cudaGetLastError();
+}
+cudaError_t bond_select(cudaStream_t st, int n, const double* lam, double htol, int chi,
+                        StepScalars* sc, DevStats* ds) {
+  bond_select_kernel<<<1, 256, 0, st>>>(n, lam, htol, chi, sc, ds);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t make_q(cudaStream_t st, int dm, int keep, int m_ops, const cx<R>* w, const cx<R>* e,
+                   const StepScalars* sc, cx<R>* q) {
+  long total = (long)keep * 3 * m_ops * 3 * dm;
+  make_q_kernel<R><<<nblocks(total), 256, 0, st>>>(dm, keep, m_ops, w, e, sc, q);
+  return cudaGetLastError();
+}
+cudaError_t kraus_select(cudaStream_t st, int n, const double* w, double kcut, int kmax,
+                         int use_ppt, double* f, StepScalars* sc, DevStats* ds) {
+  kraus_select_kernel<<<1, 32, 0, st>>>(n, w, kcut, kmax, use_ppt, f, sc, ds);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t scale_vk(cudaStream_t st, int n, int kk, const cx<R>* v, long ldv, const double* f,
+                     cx<R>* out) {
+  scale_vk_kernel<R><<<nblocks((long)n * kk), 256, 0, st>>>(n, kk, v, ldv, f, out);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t energy_mix(cudaStream_t st, int dl, int plane, const cx<R>* f, long fstride,
+                       cx<R>* g, long gstride, double J, double hx, double bz) {
+  energy_mix_kernel<R><<<nblocks((long)dl * plane), 256, 0, st>>>(dl, plane, f, fstride, g,
+                                                                    gstride, J, hx, bz);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t sample_pick(cudaStream_t st, int n_samples, int dr, const cx<R>* ev, const cx<R>* rt,
+                        uint64_t seed, int site, int site_user, int n_sites, cx<R>* env_out,
+                        uint8_t* bits, double* probs, int last) {
+  sample_pick_kernel<R><<<n_samples, 256, 0, st>>>(dr, ev, rt, seed, site, site_user, n_sites,
+                                                   env_out, bits, probs, last);
+  return cudaGetLastError();
+}
+
+#define INST(R)                                                                               \
+  template cudaError_t swap12<cx<R>>(cudaStream_t, long, long, long, long, const cx<R>*,     \
+                                     cx<R>*);                                               \
+  template cudaError_t reverse_site<cx<R>>(cudaStream_t, int, int, int, int, const cx<R>*,   \
+                                           cx<R>*);                                         \
+  template cudaError_t one_site<R>(cudaStream_t, int, int, int, const cx<R>*, cx<R>*);      \
+  template cudaError_t product_state<R>(cudaStream_t, const double*, cx<R>*, long, int);     \
+  template cudaError_t gram_mask<R>(cudaStream_t, int, const double*, double, R*, R*,       \
+                                    StepScalars*);                                          \
+  template cudaError_t gram_factor<R>(cudaStream_t, int, const cx<R>*, const R*, const R*,  \
+                                      cx<R>*, cx<R>*, cx<R>*);                              \
+  template cudaError_t build_phi<R>(cudaStream_t, int, const cx<R>*, const cx<R>*, cx<R>*); \
+  template cudaError_t make_q<R>(cudaStream_t, int, int, int, const cx<R>*, const cx<R>*,   \
+                                 const StepScalars*, cx<R>*);                               \
+  template cudaError_t scale_vk<R>(cudaStream_t, int, int, const cx<R>*, long,              \
+                                   const double*, cx<R>*);                                  \
+  template cudaError_t energy_mix<R>(cudaStream_t, int, int, const cx<R>*, long, cx<R>*,    \
+                                     long, double, double, double);                         \
+  template cudaError_t sample_pick<R>(cudaStream_t, int, int, const cx<R>*, const cx<R>*,   \
+                                      uint64_t, int, int, int, cx<R>*, uint8_t*, double*, int);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace mpdo

@@ -1,0 +1,41 @@
+// Launchers of the small kernels in kernels.cu (internal).
+#pragma once
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mpdo {
+template <typename T>
+cudaError_t swap12(cudaStream_t st, long n0, long n1, long n2, long n3, const T* in, T* out);
+template <typename T>
+cudaError_t reverse_site(cudaStream_t st, int dl, int d, int k, int dr, const T* in, T* out);
+template <typename R>
+cudaError_t one_site(cudaStream_t st, int dl, int k, int dr, const cx<R>* u, cx<R>* a);
+template <typename R>
+cudaError_t product_state(cudaStream_t st, const double* v, cx<R>* base, long stride, int n);
+template <typename R>
+cudaError_t gram_mask(cudaStream_t st, int n, const double* sig, double gtol, R* rs, R* irs,
+                      StepScalars* sc);
+template <typename R>
+cudaError_t gram_factor(cudaStream_t st, int n, const cx<R>* v, const R* rs, const R* irs,
+                        cx<R>* rmat, cx<R>* vs, cx<R>* vr);
+template <typename R>
+cudaError_t build_phi(cudaStream_t st, int dm, const cx<R>* ct, const cx<R>* gj, cx<R>* phi);
+cudaError_t bond_select(cudaStream_t st, int n, const double* lam, double htol, int chi,
+                        StepScalars* sc, DevStats* ds);
+template <typename R>
+cudaError_t make_q(cudaStream_t st, int dm, int keep, int m_ops, const cx<R>* w, const cx<R>* e,
+                   const StepScalars* sc, cx<R>* q);
+cudaError_t kraus_select(cudaStream_t st, int n, const double* w, double kcut, int kmax,
+                         int use_ppt, double* f, StepScalars* sc, DevStats* ds);
+template <typename R>
+cudaError_t scale_vk(cudaStream_t st, int n, int kk, const cx<R>* v, long ldv, const double* f,
+                     cx<R>* out);
+template <typename R>
+cudaError_t energy_mix(cudaStream_t st, int dl, int plane, const cx<R>* f, long fstride,
+                       cx<R>* g, long gstride, double J, double hx, double bz);
+template <typename R>
+cudaError_t sample_pick(cudaStream_t st, int n_samples, int dr, const cx<R>* ev, const cx<R>* rt,
+                        uint64_t seed, int site, int site_user, int n_sites, cx<R>* env_out,
+                        uint8_t* bits, double* probs, int last);
+}  // namespace mpdo

@@ -1,0 +1,67 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol include/mpdo.h
+declares, and its host channel builder matches the oracle's channels (superoperators
+are unique, Kraus sets are not)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ops as oops
+from oracle import qaoa as oqaoa
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    import paper_2309_08572_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    return _lib()
+
+
+def test_exports_every_declared_symbol(pkg):
+    hdr = open(os.path.join(ROOT, "include", "mpdo.h")).read()
+    declared = set(re.findall(r"^(?:int|const char\*)\s+(mpdo_\w+)\s*\(", hdr, re.M))
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (mpdo_\w+)$", out, re.M))
+    assert declared and declared <= exported, declared - exported
+
+
+@pytest.mark.parametrize("args", [
+    dict(angle_zz=0.3, gamma_diss=0.01, gamma_deph=0.01, xtalk_phase=0.0, delta_pp=0.01),
+    dict(angle_zz=1.7, gamma_diss=0.2, gamma_deph=0.05, xtalk_phase=0.3, delta_pp=0.2),
+    dict(angle_zz=0.0, gamma_diss=0.0, gamma_deph=0.0, xtalk_phase=0.0, delta_pp=0.0),
+])
+def test_block_channel_superoperator_matches_oracle(pkg, args):
+    v = oqaoa.site_gate(0.4, 0.9, 1.0, 0.2)
+    k_lib = pkg.build_block_channel(**args, post_left=v)
+    k_or = oops.g0_block_channel(**args, b0=1 / 16, b1=1 / 16, bd=7 / 8, post_left=v)
+    assert len(k_lib) == len(k_or)
+    assert np.abs(oops.superop(k_lib) - oops.superop(k_or)).max() < 1e-13
+
+
+def test_qaoa_layer_ops_match_oracle(pkg):
+    c = synth.scaled(synth.chain40(), n_sites=7)
+    for k in range(c.p):
+        lib = pkg.build_qaoa_layer(c.n_sites, k, c.alpha[k], c.beta[k], c.J, c.bz, c.gamma_diss,
+                                   c.gamma_deph, c.xtalk_phase, c.delta_pp)
+        orc = oqaoa.layer_ops(c, k)
+        assert [s for s, _ in lib] == [s for s, _ in orc]
+        for (_, a), (_, b) in zip(lib, orc):
+            assert np.abs(oops.superop(a) - oops.superop(b)).max() < 1e-13
+
+
+def test_invalid_arguments_are_rejected_without_gpu(pkg):
+    with pytest.raises(pkg.MpdoError):
+        pkg.build_block_channel(0.1, -1.0, 0.0)
+    with pytest.raises(pkg.MpdoError):
+        pkg.build_block_channel(float("nan"), 0.0, 0.0)

@@ -1,0 +1,138 @@
+"""GPU parity through the C ABI against the CPU oracle, on the same seeded workloads.
+
+Gauge-invariant outputs are compared (the split is unique only up to unitaries on the
+bond and inner indices): energies, success probability, trace, sampled configurations
+and their probabilities, and the dense rho on tiny chains.  FP64 mode: 1e-10 relative on
+energies.  C64 mode (FP32 arithmetic, FP64 scalars): 2e-5 relative (FP32 rounding,
+eps = 6e-8, through ~1e2 chained contractions and Gram-squared eigenproblems).
+
+The GPU path forms Gram matrices, whose eigenvalues resolve only down to ~eps * max; it
+therefore drops bond/inner values with lambda = s^2 below 1e-15 lambda_max (FP64) or
+6e-7 lambda_max (FP32), where the oracle's SVD keeps s > 1e-14 s_max.  Kept dimensions
+can thus be smaller on the GPU when the spectrum has values between the two floors;
+what is dropped carries a weight below the floor, i.e. amplitude below 3.2e-8 of the
+largest (FP64), which bounds the probability of a configuration with p >= 1e-3 to a
+relative change below 2 * 3.2e-8 / sqrt(1e-3) ~ 2e-6.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense as odense
+from oracle import mpdo as ompdo
+from oracle import observables as oobs
+from oracle import qaoa as oqaoa
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {"fp64": 1e-10, "c64": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2309_08572_gb300 as pkg
+    return pkg
+
+
+def _oracle(c):
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max)
+    for i, k in oqaoa.circuit_ops(c):
+        m.apply_two_site(i, k)
+    return m, oobs.expect_energy(m, c.J, c.hx, c.bz)
+
+
+def _gpu(lib, c, prec, m_max=25):
+    g = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec=prec)
+    stats = [g.apply_layer(layer) for layer in lib.circuit_layers(c)]
+    return g, g.expect_energy(c.J, c.hx, c.bz), stats
+
+
+def _rel(a, b):
+    return abs(a - b) / max(1.0, abs(b))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "c64"])
+def test_tiny_exact_matches_dense(lib, prec):
+    c = dataclasses.replace(synth.tiny(), k_max=40)
+    g, e, _ = _gpu(lib, c, prec)
+    d = odense.DenseRho(c.n_sites, oqaoa.plus_state())
+    for i, k in oqaoa.circuit_ops(c):
+        d.apply_two_site(i, k)
+    r = d.expect(c.J, c.hx, c.bz)
+    for key in r:
+        assert _rel(e[key], r[key]) < TOL[prec], (key, e[key], r[key])
+    rho = g.to_dense()
+    assert np.abs(rho - d.matrix()).max() < (1e-11 if prec == "fp64" else 5e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "c64"])
+@pytest.mark.parametrize("n,chi,k", [(8, 6, 3), (12, 16, 4), (9, 64, 8)])
+def test_truncated_snake_circuit_matches_oracle(lib, prec, n, chi, k):
+    c = synth.scaled(synth.chain40(), n_sites=n, chi_max=chi, k_max=k)
+    ref, r = _oracle(c)
+    g, e, stats = _gpu(lib, c, prec)
+    for key in r:
+        assert _rel(e[key], r[key]) < TOL[prec], (key, e[key], r[key])
+    b, kd, centre = g.dims()
+    assert centre == ref.centre
+    # the GPU's numerical floor is higher than the oracle's: never more kept, caps hold
+    assert all(x <= a.shape[2] for x, a in zip(kd, ref.A)) and max(kd) <= c.k_max
+    assert all(x <= a.shape[3] for x, a in zip(b, ref.A[:-1])) and max(b) <= c.chi_max
+    print(prec, n, chi, k, {key: _rel(e[key], r[key]) for key in r})
+
+
+def test_chain40_full_fp64(lib):
+    c = synth.chain40()
+    ref, r = _oracle(c)
+    g, e, _ = _gpu(lib, c, "fp64")
+    for key in r:
+        assert _rel(e[key], r[key]) < TOL["fp64"], (key, e[key], r[key])
+
+
+def test_sampling_matches_oracle_fp64(lib):
+    c = synth.scaled(synth.chain40(), n_sites=7, chi_max=12, k_max=4)
+    ref, _ = _oracle(c)
+    g, _, _ = _gpu(lib, c, "fp64")
+    bits, probs = g.sample_probs(200, seed=1234)
+    rbits, rprobs = oobs.sample(ref, 200, seed=1234)
+    same = np.all(bits == rbits, axis=1)
+    assert same.mean() > 0.99
+    rel = np.abs(probs[same] - rprobs[same]) / rprobs[same]
+    print("sampling: identical configurations", same.mean(), "max rel prob error", rel.max())
+    assert rel.max() < 2e-6
+
+
+def test_truncate_entry_point(lib):
+    c = synth.scaled(synth.chain40(), n_sites=8, chi_max=16, k_max=6)
+    g, e0, _ = _gpu(lib, c, "fp64")
+    ref, _ = _oracle(c)
+    st = g.truncate(4, 2, True)
+    ref.truncate(4, 2, True)
+    e = g.expect_energy(c.J, c.hx, c.bz)
+    r = oobs.expect_energy(ref, c.J, c.hx, c.bz)
+    for key in r:
+        assert _rel(e[key], r[key]) < 1e-9, (key, e[key], r[key])
+    b, kd, centre = g.dims()
+    assert max(b) <= 4 and max(kd) <= 2 and centre == 0
+
+
+def test_errors_are_reported(lib):
+    g = lib.Mpdo(4, 8, 4, m_max=25)
+    k = lib.build_block_channel(0.3, 0.01, 0.01)
+    with pytest.raises(lib.MpdoError) as ex:
+        g.apply_layer([(2, k)])            # centre is at 0
+    assert ex.value.code == -6
+    bad = k.copy()
+    bad[0, 0, 0] = np.nan
+    with pytest.raises(lib.MpdoError) as ex:
+        g.apply_layer([(0, bad)])
+    assert ex.value.code == -4
+    with pytest.raises(lib.MpdoError):
+        lib.Mpdo(1, 8, 4)
