@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Throughput of the noisy-QAOA MPDO hot path on GB300 through libmpdo's C ABI.
+
+Workload ("chain100"): N = 100 three-level atoms, QAOA p = 3 on the TFIM (J = h = 1),
+chi = 256, K = 16, Rydberg decay 0.005 and dephasing 0.005 per block, crosstalk phase
+0.01 rad, post-promotion 0.01 rad, seeded angles (seed 3).  One step = one full circuit:
+reset to |+>^N, the 3 layers (297 two-site updates: Gram contractions, Jacobi
+eigensolves, split, Kraus truncation with PPT) and the TFIM energy / success probability.
+
+value  = two-site updates per second, whole job (all ranks), device-resident inputs.
+e2e    = the same metric through the host-buffer API (ops uploaded every step, energies
+         read back), wall clock.
+Also reported: QAOA energy evaluations per second, the roofline of the dominant kernel
+class, the CPU oracle on a bounded sample (cpu_baseline), SM clocks during the timed
+region, and the kernel launch count.
+
+Multi-GPU: one circuit does not shard (the bond sweep is sequential), so --gpus N runs N
+independent replicas (weak scaling), launched with torchrun.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "MPDO site-updates/s and QAOA energy evals/s at chi=256, vs FP64 plain at ≤1e-6"
+STEP_SCALARS_BYTES = 64
+DEV_STATS_BYTES = 48
+
+
+def workload():
+    return synth.chain100()
+
+
+def workload_desc(c, prec):
+    return {"workload": f"chain100: N={c.n_sites} atoms (d=3), QAOA p={c.p}, chi={c.chi_max}, "
+                        f"K={c.k_max}, decay {c.gamma_diss}, dephasing {c.gamma_deph}, "
+                        f"crosstalk {c.xtalk_phase} rad, post-promotion {c.delta_pp} rad, "
+                        f"TFIM J={c.J} h={c.hx}, seed {c.seed}",
+            "updates_per_circuit": c.p * (c.n_sites - 1),
+            "precision": prec, "parallelism": "replicas", "gate_model": "G0 (gate level)",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# --------------------------------------------------------------------- CPU oracle
+def oracle_sample(c, budget_s: float, n_steps: int = 0):
+    """Time the oracle on the workload: layers 1..p-1 in full, then layer-p updates (the
+    expensive ones) up to budget_s (or n_steps of them); extrapolate one full circuit."""
+    from oracle import mpdo as ompdo, qaoa as oqaoa
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max)
+    layer_t = []
+    for k in range(c.p - 1):
+        t0 = time.perf_counter()
+        for i, kr in oqaoa.layer_ops(c, k):
+            m.apply_two_site(i, kr)
+        layer_t.append(time.perf_counter() - t0)
+    last = oqaoa.layer_ops(c, c.p - 1)
+    per = []
+    t_start = time.perf_counter()
+    for i, kr in last:
+        t0 = time.perf_counter()
+        m.apply_two_site(i, kr)
+        per.append(time.perf_counter() - t0)
+        if n_steps and len(per) >= n_steps:
+            break
+        if not n_steps and time.perf_counter() - t_start > budget_s:
+            break
+    return layer_t, per, len(last)
+
+
+def oracle_rate(layer_t, per, n_last):
+    t_circ = sum(layer_t) + n_last * statistics.mean(per)
+    return t_circ
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    c = workload()
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import mpdo as ompdo, qaoa as oqaoa
+    t0 = time.perf_counter()
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max)
+    layer_t = []
+    for k in range(c.p - 1):
+        t1 = time.perf_counter()
+        for i, kr in oqaoa.layer_ops(c, k):
+            m.apply_two_site(i, kr)
+        layer_t.append(time.perf_counter() - t1)
+    last = oqaoa.layer_ops(c, c.p - 1)
+    per = []
+    for s, (i, kr) in enumerate(last[: args.warmup + args.steps]):
+        t1 = time.perf_counter()
+        m.apply_two_site(i, kr)
+        if s >= args.warmup:
+            per.append(time.perf_counter() - t1)
+    t_circ = oracle_rate(layer_t, per, len(last))
+    ups = c.p * (c.n_sites - 1) / t_circ
+    sample = (f"layers 1..{c.p - 1} in full ({sum(layer_t):.1f} s), then {args.warmup} untimed + "
+              f"{len(per)} timed layer-{c.p} updates (mean {statistics.mean(per):.2f} s); one "
+              f"circuit extrapolated as layers + {len(last)} x mean")
+    line = {"impl": "reference", "metric": METRIC, "value": ups, "unit": "site-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(per), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_desc(c, "fp64 (CPU oracle)"),
+            "energy_evals_per_s": 1.0 / t_circ,
+            "cpu_baseline": {"value": ups, "unit": "site-updates/s", "cores": cpu_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": ups, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------- GPU arm
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def alu_peak_tflops(prec: str, sm_max_mhz: float) -> float:
+    """CUDA-core FMA peak from unit counts: 152 SMs x lanes/clk x 2 flops x max clock.
+    FP32: 128 FMA lanes per SM; FP64: 2 FMA per SM per clock on GB300."""
+    lanes = 2 if prec == "fp64" else 128
+    return 152 * lanes * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def layer_bytes(layers, elt):
+    tot = 0
+    for layer in layers:
+        for _, k in layer:
+            tot += (2 * k.shape[0] * 81 + 2 * 729) * elt
+    return tot
+
+
+def run_ours(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    c = workload()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        layer_t, per, n_last = oracle_sample(c, args.cpu_budget)
+        t_circ = oracle_rate(layer_t, per, n_last)
+        ups = c.p * (c.n_sites - 1) / t_circ
+        cpu = {"value": ups, "unit": "site-updates/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": (f"chain100 oracle: layers 1..{c.p - 1} in full ({sum(layer_t):.1f} s) "
+                          f"+ {len(per)} layer-{c.p} updates (mean {statistics.mean(per):.2f} s); "
+                          f"circuit time extrapolated as layers + {n_last} x mean = {t_circ:.0f} s")}
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2309_08572_gb300 as lib
+
+    prec = args.prec
+    layers = lib.circuit_layers(c)
+    m_max = max(k.shape[0] for layer in layers for _, k in layer)
+    g = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec=prec)
+    dls = [g.upload_layer(layer) for layer in layers]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        g.reset()
+        st = None
+        for dl in dls:
+            st = g.apply_uploaded(dl)
+        return g.expect_energy(c.J, c.hx, c.bz), st
+
+    for _ in range(args.warmup):
+        e_last, stats = step()
+    torch.cuda.synchronize()
+
+    # one profiled circuit (untimed) to find the dominant kernel class
+    g.profile(7)
+    step()
+    prof = [g.profile_read(k) for k in range(3)]
+    g.profile(0)
+    dom = max(range(3), key=lambda k: prof[k]["ms"])
+    names = {0: "complex GEMM (cgemm_kernel)", 1: "Jacobi eigensolver (jacobi_coop_kernel + pad/sort)",
+             2: "other kernels"}
+
+    # timed region: K steps, each bracketed by events; L2 flushed in between (untimed)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    g.profile(1 << dom)
+    launches0 = lib.kernel_launches()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        e_last, stats = step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = lib.kernel_launches() - launches0
+    dprof = g.profile_read(dom)
+    g.profile(0)
+    ck = clocks.stop()
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    updates = c.p * (c.n_sites - 1)
+    value = world * args.steps * updates / (total_ms / 1e3)
+
+    # end to end through the host-buffer API (ops uploaded and energies read every step)
+    h2d = layer_bytes(layers, 16 if prec == "fp64" else 8) + 6 * 8
+    d2h = 4 * 8 + updates * 2 * STEP_SCALARS_BYTES + c.p * DEV_STATS_BYTES
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.reset()
+        for layer in layers:
+            g.apply_layer(layer)
+        g.expect_energy(c.J, c.hx, c.bz)
+        te.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * sum(te)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * len(te) * updates / (e2e_ms / 1e3)
+
+    # roofline of the dominant class
+    pk = peaks()
+    smax = (ck or {}).get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
+    roof = {"kernel": names[dom], "share_of_step": prof[dom]["ms"] / max(1e-9, sum(p["ms"] for p in prof)),
+            "launches_per_step": dprof["launches"] / max(1, args.steps),
+            "avg_launch_us": 1e3 * dprof["ms"] / max(1, dprof["launches"])}
+    if dom == 0:
+        achieved = dprof["flops"] / (dprof["ms"] / 1e3) / 1e12
+        peak = alu_peak_tflops(prec, smax)
+        roof.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_note": f"CUDA-core {'FP64' if prec == 'fp64' else 'FP32'} FMA peak from "
+                                  f"unit counts at {smax:.0f} MHz"})
+    else:
+        roof.update({"bound": "latency", "achieved": None, "peak": None, "unit": None,
+                     "frac": None, "traffic": None})
+
+    # FP64 plain reference of the same circuit (accuracy and speed), optional
+    fp64 = None
+    if args.fp64_compare and prec != "fp64" and rank == 0:
+        g64 = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec="fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for layer in layers:
+            g64.apply_layer(layer)
+        e64 = g64.expect_energy(c.J, c.hx, c.bz)
+        t64 = time.perf_counter() - t0
+        fp64 = {"ms_per_circuit": 1e3 * t64, "speedup_vs_fp64": (1e3 * t64) / (total_ms / args.steps),
+                "rel_err": {k: abs(e_last[k] - e64[k]) / abs(e64[k]) for k in e64}}
+        g64.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+                "config": workload_desc(c, prec),
+                "energy_evals_per_s": world * args.steps / (total_ms / 1e3),
+                "result": e_last, "trunc_stats_last_layer": stats,
+                "roofline": roof, "kernel_profile_per_step_ms": {names[k]: prof[k]["ms"] for k in range(3)},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": ck, "fp64_plain": fp64}
+        print(json.dumps(line), flush=True)
+    for dl in dls:
+        g.free_uploaded(dl)
+    g.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp64", "c64"], default="c64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--fp64-compare", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -170,6 +170,17 @@ int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double beta, double 
                           double bd, double eta, int* sites, int* ms, double* out,
                           size_t cap);
 
+/* Instrumentation.
+ * mpdo_kernel_launches: number of CUDA kernels this library has launched in the process.
+ * mpdo_profile: time kernel launches of the selected classes on handle h with CUDA events
+ *   recorded on its stream (bit 0: complex GEMMs, bit 1: eigensolver calls, bit 2: all
+ *   other kernels); 0 switches timing off.  Resets the accumulators.
+ * mpdo_profile_read: accumulated device milliseconds, launch count and algorithmic FLOPs
+ *   (8 m n k per complex GEMM; 0 for other classes) of class cls since mpdo_profile. */
+long long mpdo_kernel_launches(void);
+int mpdo_profile(mpdo_t h, int class_mask);
+int mpdo_profile_read(mpdo_t h, int cls, double* ms, long long* launches, double* flops);
+
 /* Kernel-level entry points used by the unit tests (device pointers). */
 /* C[b] = op(A[b]) op(B[b]) for complex matrices; prec 0 = complex128, 1 = complex64.
  * opa/opb: 0 = N, 1 = T, 2 = C (conjugate transpose).  A is m x k after op, etc.;

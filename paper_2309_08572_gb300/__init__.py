@@ -77,6 +77,9 @@ def _load():
         "mpdo_build_block_channel": (I, [D, D, D, D, D, D, D, D, P(D), P(D), D, P(D), I, P(I)]),
         "mpdo_build_qaoa_layer": (I, [I, I, D, D, D, D, D, D, D, D, D, D, D, D, P(I), P(I),
                                       P(D), S]),
+        "mpdo_kernel_launches": (C.c_longlong, []),
+        "mpdo_profile": (I, [VP, I]),
+        "mpdo_profile_read": (I, [VP, I, P(D), P(C.c_longlong), P(D)]),
         "mpdo_kernel_cgemm": (I, [I, I, I, I, I, I, VP, C.c_long, C.c_long, VP, C.c_long,
                                   C.c_long, VP, C.c_long, C.c_long, I, VP]),
         "mpdo_kernel_heig": (I, [I, I, VP, VP, P(D), P(I), VP]),
@@ -251,6 +254,17 @@ class Mpdo:
                self._h)
         return bits, probs
 
+    def profile(self, class_mask: int):
+        """Time launches of the selected kernel classes with CUDA events (bit 0: GEMMs,
+        bit 1: eigensolver, bit 2: other kernels); 0 switches it off."""
+        _check(LIB.mpdo_profile(self._h, class_mask), self._h)
+
+    def profile_read(self, cls: int) -> dict:
+        ms, n, fl = C.c_double(), C.c_longlong(), C.c_double()
+        _check(LIB.mpdo_profile_read(self._h, cls, C.byref(ms), C.byref(n), C.byref(fl)),
+               self._h)
+        return dict(ms=ms.value, launches=n.value, flops=fl.value)
+
     def dims(self):
         b = np.zeros(self.n - 1, dtype=np.int32)
         k = np.zeros(self.n, dtype=np.int32)
@@ -278,6 +292,11 @@ class Mpdo:
             p, s, q, t, r, c = x.shape
             x = x.reshape(p * s, q * t, r, c)
         return x[:, :, 0, 0]
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libmpdo in this process so far."""
+    return int(LIB.mpdo_kernel_launches())
 
 
 # ------------------------------------------------------ kernel-level entry points (tests)

@@ -34,6 +34,10 @@
 
 using namespace mpdo;
 
+namespace mpdo {
+std::atomic<long long> g_launches{0};
+}
+
 namespace {
 
 thread_local std::string g_err;
@@ -91,6 +95,15 @@ struct mpdo_ctx {
   // lazily allocated observable buffers
   void* obs = nullptr;
   size_t obs_bytes = 0;
+  // optional per-class kernel timing (0: GEMM, 1: eigensolver, 2: other kernels)
+  struct ProfRec { int cls; int e0; double flops; };
+  int prof_mask = 0;
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_used = 0;
+  std::vector<ProfRec> prof_recs;
+  double prof_ms[3] = {0, 0, 0};
+  long long prof_cnt[3] = {0, 0, 0};
+  double prof_flops[3] = {0, 0, 0};
 
   void* site(int buf, int s) const {
     return static_cast<char*>(sites[buf]) + (size_t)s * site_cap * elt;
@@ -110,6 +123,39 @@ int cuda_fail(mpdo_ctx* h, cudaError_t e, const char* where) {
   do {                                                    \
     cudaError_t _e = (expr);                              \
     if (_e != cudaSuccess) return cuda_fail(h, _e, #expr); \
+  } while (0)
+
+int prof_begin(mpdo_ctx* h, int cls) {
+  if (!(h->prof_mask & (1 << cls)) || h->prof_used + 2 > (int)h->prof_ev.size()) return -1;
+  int i = h->prof_used;
+  h->prof_used += 2;
+  cudaEventRecord(h->prof_ev[i], h->st);
+  return i;
+}
+void prof_end(mpdo_ctx* h, int cls, int i, double flops) {
+  if (i < 0) return;
+  cudaEventRecord(h->prof_ev[i + 1], h->st);
+  h->prof_recs.push_back({cls, i, flops});
+}
+// called after the stream has been synchronised
+void prof_drain(mpdo_ctx* h) {
+  for (const auto& r : h->prof_recs) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->prof_ev[r.e0], h->prof_ev[r.e0 + 1]) == cudaSuccess) {
+      h->prof_ms[r.cls] += ms;
+      h->prof_cnt[r.cls] += 1;
+      h->prof_flops[r.cls] += r.flops;
+    }
+  }
+  cudaGetLastError();
+  h->prof_recs.clear();
+  h->prof_used = 0;
+}
+#define PO(expr)                     \
+  do {                               \
+    int _pi = prof_begin(h, 2);      \
+    CK(expr);                        \
+    prof_end(h, 2, _pi, 0.0);        \
   } while (0)
 
 template <typename R>
@@ -138,8 +184,27 @@ int alloc_dev(mpdo_ctx* h, void** p, size_t bytes) {
 int read_scalars(mpdo_ctx* h) {
   CK(cudaMemcpyAsync(h->hsc, h->dsc, sizeof(StepScalars), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  prof_drain(h);
   if (h->hsc->flags & 1) return fail(h, MPDO_ERR_NUMERIC, "zero or non-finite state in update");
   return MPDO_OK;
+}
+
+template <typename R>
+cudaError_t pgemm(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<R>* A, long lda,
+                  long sa, const cx<R>* B, long ldb, long sb, cx<R>* C, long ldc, long sc,
+                  int batch) {
+  int pi = prof_begin(h, 0);
+  cudaError_t e = cgemm<R>(h->st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch,
+                           one<R>(), zero<R>());
+  prof_end(h, 0, pi, 8.0 * m * n * (double)k * batch);
+  return e;
+}
+template <typename R>
+cudaError_t peig(mpdo_ctx* h, int n, const cx<R>* a, long lda, cx<R>* v, long ldv, double* w) {
+  int pi = prof_begin(h, 1);
+  cudaError_t e = heig<R>(h->st, n, a, lda, v, ldv, w, eigw<R>(h), h->max_sweeps);
+  prof_end(h, 1, pi, 0.0);
+  return e;
 }
 
 // ------------------------------------------------------------------ the update
@@ -179,56 +244,53 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   T* wCn = static_cast<T*>(h->wCn);
   R* wRs = static_cast<R*>(h->wRs);
   R* wIrs = static_cast<R*>(h->wIrs);
-  const T c1 = one<R>(), c0 = zero<R>();
 
   // a2: Gram matrices of the two site tensors
-  CK(swap12<T>(st, dl, 3, ki, dm, ai, wM));
-  CK(cgemm<R>(st, OP_C, OP_N, n3, n3, dl * ki, wM, n3, 0, wM, n3, 0, wGi, n3, 0, 1, c1, c0));
-  CK(cgemm<R>(st, OP_N, OP_C, n3, n3, kj * dr, aj, (long)kj * dr, 0, aj, (long)kj * dr, 0, wGj,
-              n3, 0, 1, c1, c0));
+  PO(swap12<T>(st, dl, 3, ki, dm, ai, wM));
+  CK(pgemm<R>(h, OP_C, OP_N, n3, n3, dl * ki, wM, n3, 0, wM, n3, 0, wGi, n3, 0, 1));
+  CK(pgemm<R>(h, OP_N, OP_C, n3, n3, kj * dr, aj, (long)kj * dr, 0, aj, (long)kj * dr, 0, wGj,
+              n3, 0, 1));
   // a3: left factor from the eigendecomposition of G_i (numerical rank by gtol)
-  CK(heig<R>(st, n3, wGi, n3, wVg, n3, h->wSig, eigw<R>(h), h->max_sweeps));
-  CK(gram_mask<R>(st, n3, h->wSig, h->gtol, wRs, wIrs, h->dsc));
-  CK(gram_factor<R>(st, n3, wVg, wRs, wIrs, wR, wVs, wVr));
+  CK(peig<R>(h, n3, wGi, n3, wVg, n3, h->wSig));
+  PO(gram_mask<R>(st, n3, h->wSig, h->gtol, wRs, wIrs, h->dsc));
+  PO(gram_factor<R>(st, n3, wVg, wRs, wIrs, wR, wVs, wVr));
   // a4/a5: Phi from the channel and G_j, then H = (I x R) Phi (I x R)^+
-  CK(build_phi<R>(st, dm, Ct, wGj, wPhi));
-  CK(cgemm<R>(st, OP_N, OP_N, n3, n9, n3, wR, n3, 0, wPhi, n9, (long)n3 * n9, wX, n9,
-              (long)n3 * n9, 3, c1, c0));
-  CK(cgemm<R>(st, OP_N, OP_C, n9, n3, n3, wX, n9, n3, wR, n3, 0, wH, n9, n3, 3, c1, c0));
+  PO(build_phi<R>(st, dm, Ct, wGj, wPhi));
+  CK(pgemm<R>(h, OP_N, OP_N, n3, n9, n3, wR, n3, 0, wPhi, n9, (long)n3 * n9, wX, n9,
+              (long)n3 * n9, 3));
+  CK(pgemm<R>(h, OP_N, OP_C, n9, n3, n3, wX, n9, n3, wR, n3, 0, wH, n9, n3, 3));
   // a6: bond eigenpairs and cut
-  CK(heig<R>(st, n9, wH, n9, wU, n9, h->wLam, eigw<R>(h), h->max_sweeps));
-  CK(bond_select(st, n9, h->wLam, h->htol, chi, h->dsc, h->dstats));
+  CK(peig<R>(h, n9, wH, n9, wU, n9, h->wLam));
+  PO(bond_select(st, n9, h->wLam, h->htol, chi, h->dsc, h->dstats));
   int rc = read_scalars(h);
   if (rc) return rc;
   const int keep = h->hsc->keep;
   // a7: split.  Vgen = (I x V sigma^-1/2) U_keep, W = (I x V sigma^1/2) U_keep
-  CK(cgemm<R>(st, OP_N, OP_N, n3, keep, n3, wVs, n3, 0, wU, n9, (long)n3 * n9, wVgen, keep,
-              (long)n3 * keep, 3, c1, c0));
-  CK(cgemm<R>(st, OP_N, OP_N, n3, keep, n3, wVr, n3, 0, wU, n9, (long)n3 * n9, wW, keep,
-              (long)n3 * keep, 3, c1, c0));
-  CK(cgemm<R>(st, OP_N, OP_N, dl * ki, keep, n3, wM, n3, 0, wVgen, keep, (long)n3 * keep, wTmp,
-              3L * keep, keep, 3, c1, c0));
-  CK(swap12<T>(st, dl, ki, 3, keep, wTmp, ai));
-  CK(make_q<R>(st, dm, keep, M, wW, E, h->dsc, wQ));
-  CK(cgemm<R>(st, OP_N, OP_N, keep * 3 * M, kj * dr, n3, wQ, n3, 0, aj, (long)kj * dr, 0, wWB,
-              (long)kj * dr, 0, 1, c1, c0));
+  CK(pgemm<R>(h, OP_N, OP_N, n3, keep, n3, wVs, n3, 0, wU, n9, (long)n3 * n9, wVgen, keep,
+              (long)n3 * keep, 3));
+  CK(pgemm<R>(h, OP_N, OP_N, n3, keep, n3, wVr, n3, 0, wU, n9, (long)n3 * n9, wW, keep,
+              (long)n3 * keep, 3));
+  CK(pgemm<R>(h, OP_N, OP_N, dl * ki, keep, n3, wM, n3, 0, wVgen, keep, (long)n3 * keep, wTmp,
+              3L * keep, keep, 3));
+  PO(swap12<T>(st, dl, ki, 3, keep, wTmp, ai));
+  PO(make_q<R>(st, dm, keep, M, wW, E, h->dsc, wQ));
+  CK(pgemm<R>(h, OP_N, OP_N, keep * 3 * M, kj * dr, n3, wQ, n3, 0, aj, (long)kj * dr, 0, wWB,
+              (long)kj * dr, 0, 1));
   // a8: inner-index Gram of the new centre and its eigenpairs
   const int KM = M * kj;
   const long colsB = (long)keep * 3 * dr;
-  CK(swap12<T>(st, 1, (long)keep * 3, KM, dr, wWB, wBp));
-  CK(cgemm<R>(st, OP_N, OP_C, KM, KM, colsB, wBp, colsB, 0, wBp, colsB, 0, wWK, KM, 0, 1, c1,
-              c0));
-  CK(heig<R>(st, KM, wWK, KM, wVk, KM, h->wWv, eigw<R>(h), h->max_sweeps));
+  PO(swap12<T>(st, 1, (long)keep * 3, KM, dr, wWB, wBp));
+  CK(pgemm<R>(h, OP_N, OP_C, KM, KM, colsB, wBp, colsB, 0, wBp, colsB, 0, wWK, KM, 0, 1));
+  CK(peig<R>(h, KM, wWK, KM, wVk, KM, h->wWv));
   // a9: cut + PPT (FP64 scalars)
-  CK(kraus_select(st, KM, h->wWv, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
+  PO(kraus_select(st, KM, h->wWv, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
   rc = read_scalars(h);
   if (rc) return rc;
   const int kk = h->hsc->kkeep;
   // a10: apply the inner isometry with the PPT scales
-  CK(scale_vk<R>(st, KM, kk, wVk, KM, h->wF, wVks));
-  CK(cgemm<R>(st, OP_C, OP_N, kk, colsB, KM, wVks, kk, 0, wBp, colsB, 0, wCn, colsB, 0, 1, c1,
-              c0));
-  CK(swap12<T>(st, 1, kk, (long)keep * 3, dr, wCn, aj));
+  PO(scale_vk<R>(st, KM, kk, wVk, KM, h->wF, wVks));
+  CK(pgemm<R>(h, OP_C, OP_N, kk, colsB, KM, wVks, kk, 0, wBp, colsB, 0, wCn, colsB, 0, 1));
+  PO(swap12<T>(st, 1, kk, (long)keep * 3, dr, wCn, aj));
   h->bond[i + 1] = keep;
   h->kd[i + 1] = kk;
   return MPDO_OK;
@@ -240,7 +302,7 @@ int reverse_chain(mpdo_ctx* h) {
   int other = 1 - h->cur;
   for (int s = 0; s < h->n; ++s) {
     int t = h->n - 1 - s;
-    CK(reverse_site<T>(h->st, h->bond[s], 3, h->kd[s], h->bond[s + 1],
+    PO(reverse_site<T>(h->st, h->bond[s], 3, h->kd[s], h->bond[s + 1],
                        static_cast<const T*>(h->site(h->cur, s)),
                        static_cast<T*>(h->site(other, t))));
   }
@@ -257,7 +319,7 @@ int apply_ops(mpdo_ctx* h, const std::vector<DevOp>& ops, int chi, int kmax, int
     if (op.kind == 1) {
       int s = h->rev ? h->n - 1 - op.site : op.site;
       int rc = MPDO_OK;
-      CK(one_site<R>(h->st, h->bond[s], h->kd[s], h->bond[s + 1],
+      PO(one_site<R>(h->st, h->bond[s], h->kd[s], h->bond[s + 1],
                      static_cast<const cx<R>*>(op.u), static_cast<cx<R>*>(h->site(h->cur, s))));
       (void)rc;
       continue;
@@ -444,6 +506,7 @@ int reset_stats(mpdo_ctx* h) {
 int read_stats(mpdo_ctx* h, mpdo_trunc_stats* out) {
   CK(cudaMemcpyAsync(h->hstats, h->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  prof_drain(h);
   if (out) {
     const DevStats& s = *h->hstats;
     out->disc_bond_w = s.disc_bond_w;
@@ -514,18 +577,19 @@ int energy(mpdo_ctx* h, double J, double hx, double bz, double out[6]) {
     const T* A = static_cast<const T*>(h->site(h->cur, s));
     const long cols = 3L * k * dr;
     // F[a] = E[a]^T A   (dl x cols)
-    CK(cgemm<R>(st, OP_T, OP_N, dl, (int)cols, dl, ebuf[cur], dl, env, A, cols, 0, F, cols, fsz,
-                6, one<R>(), zero<R>()));
-    CK(energy_mix<R>(st, dl, (int)(k * dr), F, fsz, G, fsz, J, hx, bz));
+    CK(pgemm<R>(h, OP_T, OP_N, dl, (int)cols, dl, ebuf[cur], dl, env, A, cols, 0, F, cols, fsz,
+                6));
+    PO(energy_mix<R>(st, dl, (int)(k * dr), F, fsz, G, fsz, J, hx, bz));
     // E'[a] = G[a]^T conj(A2), both as (dl*3*k) x dr
-    CK(cgemm<R>(st, OP_T, OP_R, dr, dr, dl * 3 * k, G, dr, fsz, A, dr, 0, ebuf[1 - cur], dr,
-                env, 6, one<R>(), zero<R>()));
+    CK(pgemm<R>(h, OP_T, OP_R, dr, dr, dl * 3 * k, G, dr, fsz, A, dr, 0, ebuf[1 - cur], dr,
+                env, 6));
     cur = 1 - cur;
   }
   T res[6];
   for (int a = 0; a < 6; ++a)
     CK(cudaMemcpyAsync(&res[a], ebuf[cur] + a * env, sizeof(T), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  prof_drain(h);
   for (int a = 0; a < 6; ++a) out[a] = (double)res[a].x;
   return MPDO_OK;
 }
@@ -568,10 +632,10 @@ int sample(mpdo_ctx* h, int ns, uint64_t seed, uint8_t* bits, double* probs) {
     const int dl = h->bond[s], k = h->kd[s], dr = h->bond[s + 1];
     const T* A = static_cast<const T*>(h->site(h->cur, s));
     // Y = A (dl*3k x dr) R_{s+1} (dr x dr);  R_s = Y (dl x 3k*dr) A^+
-    CK(cgemm<R>(st, OP_N, OP_N, dl * 3 * k, dr, dr, A, dr, 0, renv + (long)(s + 1) * env, dr, 0,
-                Y, dr, 0, 1, one<R>(), zero<R>()));
-    CK(cgemm<R>(st, OP_N, OP_C, dl, dl, 3L * k * dr, Y, 3L * k * dr, 0, A, 3L * k * dr, 0,
-                renv + (long)s * env, dl, 0, 1, one<R>(), zero<R>()));
+    CK(pgemm<R>(h, OP_N, OP_N, dl * 3 * k, dr, dr, A, dr, 0, renv + (long)(s + 1) * env, dr, 0,
+                Y, dr, 0, 1));
+    CK(pgemm<R>(h, OP_N, OP_C, dl, dl, 3L * k * dr, Y, 3L * k * dr, 0, A, 3L * k * dr, 0,
+                renv + (long)s * env, dl, 0, 1));
   }
   for (long c0 = 0; c0 < ns; c0 += chunk) {
     const int cn = (int)std::min<long>(chunk, ns - c0);
@@ -583,15 +647,15 @@ int sample(mpdo_ctx* h, int ns, uint64_t seed, uint8_t* bits, double* probs) {
       const T* A = static_cast<const T*>(h->site(h->cur, s));
       const long cols = 3L * k * dr, plane = (long)dl * k * dr;
       // F_q = E_q^T A  (dl x cols), packed per sample (stride dl*cols = 3*plane)
-      CK(cgemm<R>(st, OP_T, OP_N, dl, (int)cols, dl, Ecur, dl, (long)dl * dl, A, cols, 0, Ef,
-                  cols, 3 * plane, cn, one<R>(), zero<R>()));
+      CK(pgemm<R>(h, OP_T, OP_N, dl, (int)cols, dl, Ecur, dl, (long)dl * dl, A, cols, 0, Ef,
+                  cols, 3 * plane, cn));
       // Fp_q[v][l'][k][r] and Ap[v][l'][k][r] (into Y)
-      CK(swap12<T>(st, cn, dl, 3, (long)k * dr, Ef, Fp));
-      CK(swap12<T>(st, 1, dl, 3, (long)k * dr, A, Y));
+      PO(swap12<T>(st, cn, dl, 3, (long)k * dr, Ef, Fp));
+      PO(swap12<T>(st, 1, dl, 3, (long)k * dr, A, Y));
       for (int v = 0; v < 3; ++v)
-        CK(cgemm<R>(st, OP_T, OP_R, dr, dr, dl * k, Fp + v * plane, dr, 3 * plane, Y + v * plane,
-                    dr, 0, Ev + v * (long)dr * dr, dr, 3L * dr * dr, cn, one<R>(), zero<R>()));
-      CK(sample_pick<R>(st, cn, dr, Ev, renv + (long)(s + 1) * env, seed, s, s, N, Enext,
+        CK(pgemm<R>(h, OP_T, OP_R, dr, dr, dl * k, Fp + v * plane, dr, 3 * plane, Y + v * plane,
+                    dr, 0, Ev + v * (long)dr * dr, dr, 3L * dr * dr, cn));
+      PO(sample_pick<R>(st, cn, dr, Ev, renv + (long)(s + 1) * env, seed, s, s, N, Enext,
                         dbits + (size_t)c0 * N, dprob + c0, s == N - 1 ? 1 : 0));
       std::swap(Ecur, Enext);
     }
@@ -599,6 +663,7 @@ int sample(mpdo_ctx* h, int ns, uint64_t seed, uint8_t* bits, double* probs) {
   if (bits) CK(cudaMemcpyAsync(bits, dbits, (size_t)ns * N, cudaMemcpyDeviceToHost, st));
   if (probs) CK(cudaMemcpyAsync(probs, dprob, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  prof_drain(h);
   return MPDO_OK;
 }
 
@@ -807,6 +872,7 @@ int mpdo_destroy(mpdo_t h) {
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
   for (void* p : h->allocs) cudaFree(p);
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   if (h->staged.mem) cudaFree(h->staged.mem);
   if (h->obs) cudaFree(h->obs);
   if (h->hsc) cudaFreeHost(h->hsc);
@@ -816,6 +882,32 @@ int mpdo_destroy(mpdo_t h) {
 }
 
 const char* mpdo_last_error(mpdo_t h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+long long mpdo_kernel_launches(void) { return mpdo::g_launches.load(); }
+
+int mpdo_profile(mpdo_t h, int class_mask) {
+  if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
+  if (class_mask & ~7) return fail(h, MPDO_ERR_ARG, "class mask must be within 0..7");
+  if (class_mask && h->prof_ev.empty()) {
+    h->prof_ev.resize(8192);
+    for (auto& e : h->prof_ev) CK(cudaEventCreate(&e));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  prof_drain(h);
+  h->prof_mask = class_mask;
+  for (int c = 0; c < 3; ++c) { h->prof_ms[c] = 0; h->prof_cnt[c] = 0; h->prof_flops[c] = 0; }
+  return MPDO_OK;
+}
+
+int mpdo_profile_read(mpdo_t h, int cls, double* ms, long long* launches, double* flops) {
+  if (!h || cls < 0 || cls > 2) return fail(h, MPDO_ERR_ARG, "bad profile class");
+  CK(cudaStreamSynchronize(h->st));
+  prof_drain(h);
+  if (ms) *ms = h->prof_ms[cls];
+  if (launches) *launches = h->prof_cnt[cls];
+  if (flops) *flops = h->prof_flops[cls];
+  return MPDO_OK;
+}
 
 int mpdo_kernel_cgemm(int prec, int opa, int opb, int m, int n, int k, const void* a, long lda,
                       long sa, const void* b, long ldb, long sb, void* c, long ldc, long sc,

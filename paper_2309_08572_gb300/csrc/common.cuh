@@ -72,6 +72,13 @@ struct DevStats {
   int numeric_error;
 };
 
+// Count of kernels launched by this library (all handles), for throughput reports.
+#include <atomic>
+namespace mpdo {
+extern std::atomic<long long> g_launches;
+inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace mpdo
+
 #define MPDO_CUDA_TRY(expr)                                 \
   do {                                                      \
     cudaError_t _e = (expr);                                \

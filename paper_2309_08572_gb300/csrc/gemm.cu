@@ -107,6 +107,7 @@ cudaError_t cgemm(cudaStream_t st, int opa, int opb, int m, int n, int k, const 
   for (int b0 = 0; b0 < batch; b0 += 65535) {
     int nb = batch - b0 < 65535 ? batch - b0 : 65535;
     dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, nb);
+    count_launch();
     cgemm_kernel<R><<<grid, NT, 0, st>>>(m, n, k, A + (long)b0 * sa, sam, sak, sa, conja,
                                           B + (long)b0 * sb, sbk, sbn, sb, conjb,
                                           C + (long)b0 * sc, ldc, 1, sc, alpha, beta, use_beta);

@@ -311,6 +311,7 @@ cudaError_t heig(cudaStream_t st, int n, const cx<R>* a, long lda, cx<R>* v, lon
   long total = (long)np * np;
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
+  count_launch(3);
   pad_copy_kernel<R><<<blocks, 256, 0, st>>>(n, np, a, lda, work.ap, work.vp, work.counters);
   MPDO_CUDA_TRY(cudaGetLastError());
   int grid = nblk / 2;

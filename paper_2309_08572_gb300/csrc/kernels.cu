@@ -415,23 +415,27 @@ template <typename T>
 cudaError_t swap12(cudaStream_t st, long n0, long n1, long n2, long n3, const T* in, T* out) {
   long total = n0 * n1 * n2 * n3;
   if (total <= 0) return cudaSuccess;
+  count_launch();
   swap12_kernel<T><<<nblocks(total), 256, 0, st>>>(n0, n1, n2, n3, in, out);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t reverse_site(cudaStream_t st, int dl, int d, int k, int dr, const T* in, T* out) {
   long total = (long)dl * d * k * dr;
+  count_launch();
   reverse_site_kernel<T><<<nblocks(total), 256, 0, st>>>(dl, d, k, dr, in, out);
   return cudaGetLastError();
 }
 template <typename R>
 cudaError_t one_site(cudaStream_t st, int dl, int k, int dr, const cx<R>* u, cx<R>* a) {
   long total = (long)dl * k * dr;
+  count_launch();
   one_site_kernel<R><<<nblocks(total), 256, 0, st>>>(dl, k, dr, u, a);
   return cudaGetLastError();
 }
 template <typename R>
 cudaError_t product_state(cudaStream_t st, const double* v, cx<R>* base, long stride, int n) {
+  count_launch();
   product_state_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(
       mkc<R>((R)v[0], (R)v[1]), mkc<R>((R)v[2], (R)v[3]), mkc<R>((R)v[4], (R)v[5]), base, stride,
       n);
@@ -440,23 +444,27 @@ cudaError_t product_state(cudaStream_t st, const double* v, cx<R>* base, long st
 template <typename R>
 cudaError_t gram_mask(cudaStream_t st, int n, const double* sig, double gtol, R* rs, R* irs,
                       StepScalars* sc) {
+  count_launch();
   gram_mask_kernel<R><<<1, 256, 0, st>>>(n, sig, gtol, rs, irs, sc);
   return cudaGetLastError();
 }
 template <typename R>
 cudaError_t gram_factor(cudaStream_t st, int n, const cx<R>* v, const R* rs, const R* irs,
                         cx<R>* rmat, cx<R>* vs, cx<R>* vr) {
+  count_launch();
   gram_factor_kernel<R><<<nblocks((long)n * n), 256, 0, st>>>(n, v, rs, irs, rmat, vs, vr);
   return cudaGetLastError();
 }
 template <typename R>
 cudaError_t build_phi(cudaStream_t st, int dm, const cx<R>* ct, const cx<R>* gj, cx<R>* phi) {
   long n = 9L * dm;
+  count_launch();
   build_phi_kernel<R><<<nblocks(n * n), 256, 0, st>>>(dm, ct, gj, phi);
   return cudaGetLastError();
 }
 cudaError_t bond_select(cudaStream_t st, int n, const double* lam, double htol, int chi,
                         StepScalars* sc, DevStats* ds) {
+  count_launch();
   bond_select_kernel<<<1, 256, 0, st>>>(n, lam, htol, chi, sc, ds);
   return cudaGetLastError();
 }
@@ -464,23 +472,27 @@ template <typename R>
 cudaError_t make_q(cudaStream_t st, int dm, int keep, int m_ops, const cx<R>* w, const cx<R>* e,
                    const StepScalars* sc, cx<R>* q) {
   long total = (long)keep * 3 * m_ops * 3 * dm;
+  count_launch();
   make_q_kernel<R><<<nblocks(total), 256, 0, st>>>(dm, keep, m_ops, w, e, sc, q);
   return cudaGetLastError();
 }
 cudaError_t kraus_select(cudaStream_t st, int n, const double* w, double kcut, int kmax,
                          int use_ppt, double* f, StepScalars* sc, DevStats* ds) {
+  count_launch();
   kraus_select_kernel<<<1, 32, 0, st>>>(n, w, kcut, kmax, use_ppt, f, sc, ds);
   return cudaGetLastError();
 }
 template <typename R>
 cudaError_t scale_vk(cudaStream_t st, int n, int kk, const cx<R>* v, long ldv, const double* f,
                      cx<R>* out) {
+  count_launch();
   scale_vk_kernel<R><<<nblocks((long)n * kk), 256, 0, st>>>(n, kk, v, ldv, f, out);
   return cudaGetLastError();
 }
 template <typename R>
 cudaError_t energy_mix(cudaStream_t st, int dl, int plane, const cx<R>* f, long fstride,
                        cx<R>* g, long gstride, double J, double hx, double bz) {
+  count_launch();
   energy_mix_kernel<R><<<nblocks((long)dl * plane), 256, 0, st>>>(dl, plane, f, fstride, g,
                                                                     gstride, J, hx, bz);
   return cudaGetLastError();
@@ -489,6 +501,7 @@ template <typename R>
 cudaError_t sample_pick(cudaStream_t st, int n_samples, int dr, const cx<R>* ev, const cx<R>* rt,
                         uint64_t seed, int site, int site_user, int n_sites, cx<R>* env_out,
                         uint8_t* bits, double* probs, int last) {
+  count_launch();
   sample_pick_kernel<R><<<n_samples, 256, 0, st>>>(dr, ev, rt, seed, site, site_user, n_sites,
                                                    env_out, bits, probs, last);
   return cudaGetLastError();

@@ -29,7 +29,7 @@ def pkg():
 
 def test_exports_every_declared_symbol(pkg):
     hdr = open(os.path.join(ROOT, "include", "mpdo.h")).read()
-    declared = set(re.findall(r"^(?:int|const char\*)\s+(mpdo_\w+)\s*\(", hdr, re.M))
+    declared = set(re.findall(r"^(?:int|long long|const char\*)\s+(mpdo_\w+)\s*\(", hdr, re.M))
     out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True,
                          text=True, check=True).stdout
     exported = set(re.findall(r" T (mpdo_\w+)$", out, re.M))
