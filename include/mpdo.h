@@ -194,6 +194,24 @@ int mpdo_kernel_cgemm(int prec, int opa, int opb, int m, int n, int k, const voi
  * in *sweeps (host). */
 int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, void* stream);
 
+/* Allocation-free variant of mpdo_kernel_heig.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- processes where every
+ * byte of device memory is owned by an outside allocator or budget (a framework's caching
+ * allocator, a serving process with a fixed memory pool), where a stray cudaMalloc would
+ * fragment or overrun that budget, and latency-critical loops, where cudaMalloc and
+ * cudaFree can synchronise the whole device.  Arguments are those of mpdo_kernel_heig
+ * (a, v, w are caller-owned device arrays; sweeps is an optional host int).
+ * Its scratch is one file-scope device array sized for n <= MPDO_HEIG_NOALLOC_NMAX; larger
+ * n returns MPDO_ERR_ARG with a message in mpdo_last_error(NULL).  No call allocates.
+ * The array's device address is looked up on the first call made on each device (with
+ * that device current); make that first call before any stream capture.  Every GPU that
+ * loads the library holds the array (~1.2 MB) until the process exits.  All calls share
+ * the one array, and each call re-initialises the part it uses (padded matrix, identity
+ * accumulator, zeroed counters); calls that overlap on the GPU -- on different streams
+ * or from different host threads -- race on it and must be serialised by the caller. */
+#define MPDO_HEIG_NOALLOC_NMAX 192
+int mpdo_heig_noalloc(int prec, int n, void* a, void* v, double* w, int* sweeps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

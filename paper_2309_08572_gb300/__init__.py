@@ -83,6 +83,7 @@ def _load():
         "mpdo_kernel_cgemm": (I, [I, I, I, I, I, I, VP, C.c_long, C.c_long, VP, C.c_long,
                                   C.c_long, VP, C.c_long, C.c_long, I, VP]),
         "mpdo_kernel_heig": (I, [I, I, VP, VP, P(D), P(I), VP]),
+        "mpdo_heig_noalloc": (I, [I, I, VP, VP, P(D), P(I), VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -316,4 +317,17 @@ def kernel_heig(prec: int, n: int, a, v, w, stream=None) -> int:
     _check(LIB.mpdo_kernel_heig(prec, n, C.c_void_p(a.data_ptr()), C.c_void_p(v.data_ptr()),
                                 C.cast(C.c_void_p(w.data_ptr()), C.POINTER(C.c_double)),
                                 C.byref(sweeps), st))
+    return sweeps.value
+
+
+HEIG_NOALLOC_NMAX = 192
+
+
+def kernel_heig_noalloc(prec: int, n: int, a, v, w, stream=None) -> int:
+    """Allocation-free eigensolver entry point (scratch in a fixed device array, n <= 192)."""
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    sweeps = C.c_int(0)
+    _check(LIB.mpdo_heig_noalloc(prec, n, C.c_void_p(a.data_ptr()), C.c_void_p(v.data_ptr()),
+                                 C.cast(C.c_void_p(w.data_ptr()), C.POINTER(C.c_double)),
+                                 C.byref(sweeps), st))
     return sweeps.value

@@ -39,8 +39,15 @@ std::atomic<long long> g_launches{0};
 }
 
 namespace {
-
 thread_local std::string g_err;
+}
+
+namespace mpdo {
+// handle-less error message, read back by mpdo_last_error(NULL)
+void set_global_error(const char* msg) { g_err = msg ? msg : ""; }
+}
+
+namespace {
 
 struct DevOp {
   int kind = 2;

@@ -11,6 +11,10 @@
 // L2 (it is at most a few MB).
 #include <cooperative_groups.h>
 
+#include <mutex>
+
+#include "../../include/mpdo.h"
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -335,3 +339,85 @@ template cudaError_t heig<float>(cudaStream_t, int, const float2*, long, float2*
                                  double*, EigWork<float>&, int);
 
 }  // namespace mpdo
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free eigensolver entry point (mpdo_heig_noalloc, declared in mpdo.h).
+// Its scratch -- the padded working matrix, the eigenvector accumulator and the sweep
+// counters -- is one file-scope device array sized for n <= MPDO_HEIG_NOALLOC_NMAX, so a
+// call performs no device allocation.  Host code cannot use the array's name as a device
+// address; the address is looked up with cudaGetSymbolAddress once per device (first call
+// with that device current) and passed to the kernels.
+namespace {
+constexpr int kNoAllocNMax = MPDO_HEIG_NOALLOC_NMAX;
+constexpr size_t kNoAllocBytes = 2ull * kNoAllocNMax * kNoAllocNMax * sizeof(double2) + 256;
+static_assert(kNoAllocNMax % (2 * mpdo::JW) == 0, "maximum must be a whole number of block pairs");
+static __device__ __align__(256) unsigned char g_heig_scratch[kNoAllocBytes];
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+}  // namespace
+
+namespace mpdo {
+void set_global_error(const char* msg);
+}
+
+extern "C" int mpdo_heig_noalloc(int prec, int n, void* a, void* v, double* w, int* sweeps,
+                                 void* stream) {
+  using namespace mpdo;
+  if (prec != 0 && prec != 1) {
+    set_global_error("mpdo_heig_noalloc: prec must be 0 (complex128) or 1 (complex64)");
+    return MPDO_ERR_ARG;
+  }
+  if (n < 1 || n > kNoAllocNMax) {
+    set_global_error("mpdo_heig_noalloc: n must be in 1..MPDO_HEIG_NOALLOC_NMAX (192)");
+    return MPDO_ERR_ARG;
+  }
+  if (!a || !v || !w) {
+    set_global_error("mpdo_heig_noalloc: null matrix, vector or eigenvalue pointer");
+    return MPDO_ERR_ARG;
+  }
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_global_error("mpdo_heig_noalloc: no usable current CUDA device");
+    return MPDO_ERR_CUDA;
+  }
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_heig_scratch);
+      if (e != cudaSuccess || !p) {
+        set_global_error("mpdo_heig_noalloc: cudaGetSymbolAddress of the scratch array failed");
+        return MPDO_ERR_CUDA;
+      }
+      g_scratch_addr[dev] = p;
+    }
+    base = g_scratch_addr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* counters;
+  if (prec == 0) {
+    EigWork<double> wk;
+    eig_work_bind<double>(wk, base, kNoAllocNMax);
+    counters = wk.counters;
+    e = heig<double>(st, n, static_cast<const double2*>(a), n, static_cast<double2*>(v), n, w,
+                     wk, 30);
+  } else {
+    EigWork<float> wk;
+    eig_work_bind<float>(wk, base, kNoAllocNMax);
+    counters = wk.counters;
+    e = heig<float>(st, n, static_cast<const float2*>(a), n, static_cast<float2*>(v), n, w, wk,
+                    20);
+  }
+  if (e == cudaSuccess && sweeps) {
+    e = cudaMemcpyAsync(sweeps, counters + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) {
+    set_global_error(cudaGetErrorString(e));
+    return MPDO_ERR_CUDA;
+  }
+  return MPDO_OK;
+}
