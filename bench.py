@@ -6,6 +6,9 @@ chi = 256, K = 16, Rydberg decay 0.005 and dephasing 0.005 per block, crosstalk 
 0.01 rad, post-promotion 0.01 rad, seeded angles (seed 3).  One step = one full circuit:
 reset to |+>^N, the 3 layers (297 two-site updates: Gram contractions, Jacobi
 eigensolves, split, Kraus truncation with PPT) and the TFIM energy / success probability.
+One step runs a batch of such circuits (--batch, default 16, seeded angle draws)
+concurrently through the library's batch executor (one CUDA stream and host thread per
+circuit in flight); the single-circuit latency is reported beside it.
 
 value  = two-site updates per second, whole job (all ranks), device-resident inputs.
 e2e    = the same metric through the host-buffer API (ops uploaded every step, energies
@@ -38,12 +41,15 @@ STEP_SCALARS_BYTES = 64
 DEV_STATS_BYTES = 48
 
 
+WORKLOAD = "chain100"
+
+
 def workload():
-    return synth.chain100()
+    return synth.chain40() if WORKLOAD == "chain40" else synth.chain100()
 
 
 def workload_desc(c, prec):
-    return {"workload": f"chain100: N={c.n_sites} atoms (d=3), QAOA p={c.p}, chi={c.chi_max}, "
+    return {"workload": f"{WORKLOAD}: N={c.n_sites} atoms (d=3), QAOA p={c.p}, chi={c.chi_max}, "
                         f"K={c.k_max}, decay {c.gamma_diss}, dephasing {c.gamma_deph}, "
                         f"crosstalk {c.xtalk_phase} rad, post-promotion {c.delta_pp} rad, "
                         f"TFIM J={c.J} h={c.hx}, seed {c.seed}",
@@ -204,6 +210,20 @@ def layer_bytes(layers, elt):
     return tot
 
 
+def batch_circuits(c, batch):
+    """The batch of one step: `batch` copies of the workload with seeded angle draws."""
+    out = []
+    for j in range(batch):
+        if j == 0:
+            out.append(c)
+            continue
+        a, b = synth._angles(synth.rng_for(c.seed * 1000 + j), c.p)
+        d = synth.scaled(c)
+        d.alpha, d.beta, d.seed = a, b, c.seed * 1000 + j
+        out.append(d)
+    return out
+
+
 def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -215,7 +235,7 @@ def run_ours(args):
         t_circ = oracle_rate(layer_t, per, n_last)
         ups = c.p * (c.n_sites - 1) / t_circ
         cpu = {"value": ups, "unit": "site-updates/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": (f"chain100 oracle: layers 1..{c.p - 1} in full ({sum(layer_t):.1f} s) "
+               "sample": (f"{WORKLOAD} oracle: layers 1..{c.p - 1} in full ({sum(layer_t):.1f} s) "
                           f"+ {len(per)} layer-{c.p} updates (mean {statistics.mean(per):.2f} s); "
                           f"circuit time extrapolated as layers + {n_last} x mean = {t_circ:.0f} s")}
 
@@ -228,39 +248,47 @@ def run_ours(args):
     import paper_2309_08572_gb300 as lib
 
     prec = args.prec
-    layers = lib.circuit_layers(c)
-    m_max = max(k.shape[0] for layer in layers for _, k in layer)
-    g = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec=prec)
-    dls = [g.upload_layer(layer) for layer in layers]
+    circs = batch_circuits(c, args.batch)
+    host_layers = [lib.circuit_layers(ci) for ci in circs]
+    m_max = max(k.shape[0] for L in host_layers for layer in L for _, k in layer)
+    pool = [lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec=prec, own_stream=True)
+            for _ in range(args.batch)]
+    dls = [[pool[0].upload_layer(layer) for layer in L] for L in host_layers]
+    descs = [dict(n_sites=ci.n_sites, chi_max=ci.chi_max, k_max=ci.k_max, layers=d, J=ci.J,
+                  hx=ci.hx, b=ci.bz) for ci, d in zip(circs, dls)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    updates = c.p * (c.n_sites - 1)
 
     def step():
-        g.reset()
-        st = None
-        for dl in dls:
-            st = g.apply_uploaded(dl)
-        return g.expect_energy(c.J, c.hx, c.bz), st
+        return lib.batch_run(pool, descs)
 
     for _ in range(args.warmup):
-        e_last, stats = step()
+        res = step()
     torch.cuda.synchronize()
 
-    # one profiled circuit (untimed) to find the dominant kernel class
+    # single-circuit latency and kernel-class breakdown (one profiled circuit, untimed)
+    g = pool[0]
     g.profile(7)
-    step()
+    t0 = time.perf_counter()
+    single = lib.batch_run([g], descs[:1])
+    single_ms = 1e3 * (time.perf_counter() - t0)
     prof = [g.profile_read(k) for k in range(3)]
     g.profile(0)
     dom = max(range(3), key=lambda k: prof[k]["ms"])
-    names = {0: "complex GEMM (cgemm_kernel)", 1: "Jacobi eigensolver (jacobi_coop_kernel + pad/sort)",
+    names = {0: "complex GEMM (cgemm_kernel)",
+             1: "Jacobi eigensolver (jacobi_smem_kernel / jacobi_coop_kernel)",
              2: "other kernels"}
 
-    # timed region: K steps, each bracketed by events; L2 flushed in between (untimed)
+    # timed region: K steps (each a batch of circuits run concurrently), events around
+    # each step on the current stream after a device-wide synchronisation; L2 flushed
+    # between steps outside the events
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    g.profile(1 << dom)
+    for m in pool:
+        m.profile(1 << dom)
     launches0 = lib.kernel_launches()
     times = []
     for _ in range(args.steps):
@@ -269,91 +297,108 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        e_last, stats = step()
+        res = step()
+        torch.cuda.synchronize()
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     launches = lib.kernel_launches() - launches0
-    dprof = g.profile_read(dom)
-    g.profile(0)
+    dprofs = [m.profile_read(dom) for m in pool]
+    for m in pool:
+        m.profile(0)
+    dprof = {k: sum(d[k] for d in dprofs) for k in ("ms", "launches", "flops")}
     ck = clocks.stop()
     total_ms = sum(times)
     if dist:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    updates = c.p * (c.n_sites - 1)
-    value = world * args.steps * updates / (total_ms / 1e3)
+    value = world * args.steps * args.batch * updates / (total_ms / 1e3)
 
-    # end to end through the host-buffer API (ops uploaded and energies read every step)
-    h2d = layer_bytes(layers, 16 if prec == "fp64" else 8) + 6 * 8
-    d2h = 4 * 8 + updates * 2 * STEP_SCALARS_BYTES + c.p * DEV_STATS_BYTES
+    # end to end through the host-buffer API: every step uploads each circuit's ops from
+    # host memory, runs the batch and reads the energies back
+    h2d = sum(layer_bytes(L, 16 if prec == "fp64" else 8) for L in host_layers)
+    d2h = args.batch * (4 * 8 + updates * 2 * STEP_SCALARS_BYTES + c.p * DEV_STATS_BYTES)
     torch.cuda.synchronize()
     te = []
     for _ in range(max(1, args.steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g.reset()
-        for layer in layers:
-            g.apply_layer(layer)
-        g.expect_energy(c.J, c.hx, c.bz)
+        fresh = [[pool[0].upload_layer(layer) for layer in L] for L in host_layers]
+        dd = [dict(dsc, layers=f) for dsc, f in zip(descs, fresh)]
+        lib.batch_run(pool, dd)
         te.append(time.perf_counter() - t0)
+        for f in fresh:
+            for dl in f:
+                pool[0].free_uploaded(dl)
     e2e_ms = 1e3 * sum(te)
     if dist:
         t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e_value = world * len(te) * updates / (e2e_ms / 1e3)
+    e2e_value = world * len(te) * args.batch * updates / (e2e_ms / 1e3)
 
     # roofline of the dominant class
     pk = peaks()
     smax = (ck or {}).get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
-    roof = {"kernel": names[dom], "share_of_step": prof[dom]["ms"] / max(1e-9, sum(p["ms"] for p in prof)),
+    roof = {"kernel": names[dom],
+            "share_of_single_circuit": prof[dom]["ms"] / max(1e-9, sum(p["ms"] for p in prof)),
             "launches_per_step": dprof["launches"] / max(1, args.steps),
             "avg_launch_us": 1e3 * dprof["ms"] / max(1, dprof["launches"])}
-    if dom == 0:
+    if dom in (0, 1) and dprof["flops"] > 0:
         achieved = dprof["flops"] / (dprof["ms"] / 1e3) / 1e12
         peak = alu_peak_tflops(prec, smax)
         roof.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
+                     "flops_per_launch": dprof["flops"] / max(1, dprof["launches"]),
                      "peak_note": f"CUDA-core {'FP64' if prec == 'fp64' else 'FP32'} FMA peak from "
-                                  f"unit counts at {smax:.0f} MHz"})
+                                  f"unit counts (152 SMs x {'2' if prec == 'fp64' else '128'} FMA/clk "
+                                  f"x 2) at {smax:.0f} MHz; achieved = flops per launch / mean "
+                                  f"launch duration (concurrent circuits); flops = "
+                                  + ("8 m n k per complex GEMM" if dom == 0 else
+                                     "multiply-adds executed by the Jacobi rotations")})
     else:
         roof.update({"bound": "latency", "achieved": None, "peak": None, "unit": None,
                      "frac": None, "traffic": None})
 
-    # FP64 plain reference of the same circuit (accuracy and speed), optional
     fp64 = None
     if args.fp64_compare and prec != "fp64" and rank == 0:
-        g64 = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec="fp64")
-        torch.cuda.synchronize()
+        g64 = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec="fp64", own_stream=True)
+        dl64 = [g64.upload_layer(layer) for layer in host_layers[0]]
         t0 = time.perf_counter()
-        for layer in layers:
-            g64.apply_layer(layer)
-        e64 = g64.expect_energy(c.J, c.hx, c.bz)
+        r64 = lib.batch_run([g64], [dict(descs[0], layers=dl64)])
         t64 = time.perf_counter() - t0
-        fp64 = {"ms_per_circuit": 1e3 * t64, "speedup_vs_fp64": (1e3 * t64) / (total_ms / args.steps),
-                "rel_err": {k: abs(e_last[k] - e64[k]) / abs(e64[k]) for k in e64}}
+        fp64 = {"ms_per_circuit": 1e3 * t64, "speedup_vs_fp64_single": (1e3 * t64) / single_ms,
+                "rel_err": {k: abs(single[0][j] - r64[0][j]) / abs(r64[0][j])
+                            for j, k in enumerate(("e_raw", "e_succ", "p_succ", "trace"))}}
         g64.close()
 
     if rank == 0:
+        cfg = workload_desc(c, prec)
+        cfg["batch"] = f"{args.batch} circuits per step, run concurrently (one stream each); " \
+                       f"circuit 0 uses seed {c.seed}, circuit j seeded angles {c.seed}*1000+j"
         line = {"metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
-                "config": workload_desc(c, prec),
-                "energy_evals_per_s": world * args.steps / (total_ms / 1e3),
-                "result": e_last, "trunc_stats_last_layer": stats,
-                "roofline": roof, "kernel_profile_per_step_ms": {names[k]: prof[k]["ms"] for k in range(3)},
+                "config": cfg,
+                "energy_evals_per_s": world * args.steps * args.batch / (total_ms / 1e3),
+                "single_circuit": {"ms": single_ms, "site_updates_per_s": updates / (single_ms / 1e3),
+                                   "result": dict(zip(("e_raw", "e_succ", "p_succ", "trace"),
+                                                      single[0].tolist()))},
+                "roofline": roof,
+                "kernel_profile_single_circuit_ms": {names[k]: prof[k]["ms"] for k in range(3)},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "clocks": ck, "fp64_plain": fp64}
         print(json.dumps(line), flush=True)
-    for dl in dls:
-        g.free_uploaded(dl)
-    g.close()
+    for d in dls:
+        for dl in d:
+            pool[0].free_uploaded(dl)
+    for m in pool:
+        m.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -370,7 +415,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--fp64-compare", action="store_true")
+    ap.add_argument("--batch", type=int, default=16,
+                    help="circuits per step, run concurrently by the batch executor")
+    ap.add_argument("--workload", choices=["chain100", "chain40"], default="chain100",
+                    help="chain40 (N=40, p=2, chi=64, K=8) is the small profiling case")
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = args.workload
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

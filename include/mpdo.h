@@ -62,7 +62,7 @@ typedef struct {
   double sv_cutoff;     /* bond values with s <= sv_cutoff*s_max are dropped (<=0: default) */
   double kraus_cutoff;  /* inner values with sqrt(w) <= kraus_cutoff*sqrt(w_max) dropped   */
   int use_ppt;          /* 1: purity-preserving inner truncation; 0: plain + trace renorm  */
-  void* cuda_stream;    /* cudaStream_t to use; NULL = the legacy default stream           */
+  void* cuda_stream;    /* cudaStream_t to use; NULL = a non-blocking stream the handle owns */
 } mpdo_config;
 
 /* One op of a layer.  kind 2: two-site channel on (site, site+1) with n_kraus Kraus
@@ -133,6 +133,28 @@ int mpdo_expect_energy(mpdo_t h, double J, double hx, double b, double* e_raw,
  * <x|rho|x>.  Either output may be NULL. */
 int mpdo_sample_probs(mpdo_t h, int n_samples, uint64_t seed, uint8_t* bits, double* probs);
 
+/* Change the active limits of a handle (each at most what it was created with) and reset
+ * its state to the product state; lets one handle serve circuits of different sizes. */
+int mpdo_reconfigure(mpdo_t h, int n_sites, int chi_max, int k_max, int use_ppt,
+                     const double* init_site_vec);
+
+/* Batched form: many independent circuits advanced concurrently.  Each pool handle runs on
+ * its own CUDA stream, driven by its own host thread, so the kernels of different circuits
+ * overlap on the GPU; circuits are taken from a shared queue in index order.  For circuit i
+ * the worker reconfigures its handle to (n_sites, chi_max, k_max, use_ppt), applies the
+ * device-resident layers in order (each must have been uploaded by a handle of the same
+ * precision on the same device) and evaluates the TFIM energy; out[4i..4i+3] = e_raw,
+ * e_success, success_prob, trace; status[i] (may be NULL) = its return code.  The pool
+ * handles must be distinct and not used by other threads during the call. */
+typedef struct {
+  int n_sites, chi_max, k_max, use_ppt;
+  int n_layers;
+  const mpdo_dlayer* layers;
+  double J, hx, b;
+} mpdo_circuit;
+int mpdo_batch_run(int n_handles, mpdo_t* handles, int n_circuits, const mpdo_circuit* circuits,
+                   double* out, int* status);
+
 /* Current bond dimensions (host int[N-1]), inner dimensions (host int[N]) and centre. */
 int mpdo_get_dims(mpdo_t h, int* bond_dims, int* kraus_dims, int* centre);
 
@@ -176,7 +198,9 @@ int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double beta, double 
  *   recorded on its stream (bit 0: complex GEMMs, bit 1: eigensolver calls, bit 2: all
  *   other kernels); 0 switches timing off.  Resets the accumulators.
  * mpdo_profile_read: accumulated device milliseconds, launch count and algorithmic FLOPs
- *   (8 m n k per complex GEMM; 0 for other classes) of class cls since mpdo_profile. */
+ *   (8 m n k per complex GEMM; for the eigensolver 8 x 3 x 16 x 16 x padded n per active
+ *   block-pair rotation round, the multiply-adds its block Jacobi executes; 0 for other
+ *   kernels) of class cls since mpdo_profile. */
 long long mpdo_kernel_launches(void);
 int mpdo_profile(mpdo_t h, int class_mask);
 int mpdo_profile_read(mpdo_t h, int cls, double* ms, long long* launches, double* flops);

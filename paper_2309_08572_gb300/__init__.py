@@ -43,6 +43,12 @@ class Layer(C.Structure):
     _fields_ = [("n_ops", C.c_int), ("ops", C.POINTER(Op))]
 
 
+class CircuitDesc(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("chi_max", C.c_int), ("k_max", C.c_int),
+                ("use_ppt", C.c_int), ("n_layers", C.c_int), ("layers", C.POINTER(C.c_void_p)),
+                ("J", C.c_double), ("hx", C.c_double), ("b", C.c_double)]
+
+
 class TruncStats(C.Structure):
     _fields_ = [("disc_bond_w", C.c_double), ("disc_kraus_w", C.c_double),
                 ("ppt_theta_min", C.c_double), ("ppt_infeasible", C.c_int),
@@ -71,6 +77,8 @@ def _load():
         "mpdo_expect_energy": (I, [VP, D, D, D, P(D), P(D), P(D), P(D)]),
         "mpdo_sample_probs": (I, [VP, I, C.c_uint64, P(C.c_uint8), P(D)]),
         "mpdo_get_dims": (I, [VP, P(I), P(I), P(I)]),
+        "mpdo_reconfigure": (I, [VP, I, I, I, I, P(D)]),
+        "mpdo_batch_run": (I, [I, P(VP), I, P(CircuitDesc), P(D), P(I)]),
         "mpdo_get_site": (I, [VP, I, P(D), S, P(I)]),
         "mpdo_destroy": (I, [VP]),
         "mpdo_last_error": (C.c_char_p, [VP]),
@@ -191,10 +199,14 @@ class Mpdo:
     def __init__(self, n_sites: int, chi_max: int, k_max: int, m_max: int = 25,
                  prec: str = "fp64", sv_cutoff: float = 0.0, kraus_cutoff: float = 0.0,
                  use_ppt: bool = True, init_vec: Optional[Sequence[complex]] = None,
-                 stream=None):
+                 stream=None, own_stream: bool = False):
         self.n = n_sites
+        if own_stream:
+            st = C.c_void_p(None)            # the library creates a non-blocking stream
+        else:
+            st = _current_stream() if stream is None else C.c_void_p(stream)
         cfg = Config(n_sites, 3, chi_max, k_max, m_max, PREC[prec], sv_cutoff, kraus_cutoff,
-                     int(use_ppt), _current_stream() if stream is None else C.c_void_p(stream))
+                     int(use_ppt), st)
         self._h = C.c_void_p(None)
         v = None if init_vec is None else np.ascontiguousarray(np.asarray(init_vec, complex)).view(float)
         rc = LIB.mpdo_create(C.byref(cfg), None if v is None else _dptr(v), C.byref(self._h))
@@ -255,6 +267,11 @@ class Mpdo:
                self._h)
         return bits, probs
 
+    def reconfigure(self, n_sites: int, chi_max: int, k_max: int, use_ppt: bool = True):
+        _check(LIB.mpdo_reconfigure(self._h, n_sites, chi_max, k_max, int(use_ppt), None),
+               self._h)
+        self.n = n_sites
+
     def profile(self, class_mask: int):
         """Time launches of the selected kernel classes with CUDA events (bit 0: GEMMs,
         bit 1: eigensolver, bit 2: other kernels); 0 switches it off."""
@@ -293,6 +310,32 @@ class Mpdo:
             p, s, q, t, r, c = x.shape
             x = x.reshape(p * s, q * t, r, c)
         return x[:, :, 0, 0]
+
+
+def batch_run(pool: Sequence["Mpdo"], circuits: Sequence[dict]) -> np.ndarray:
+    """Run circuits concurrently on a pool of handles (one stream and host thread each).
+
+    circuits: dicts with n_sites, chi_max, k_max, layers (uploaded with pool[0].upload_layer),
+    and optionally use_ppt, J, hx, b.  Returns an (n, 4) array of e_raw, e_succ, p_succ, trace.
+    """
+    handles = (C.c_void_p * len(pool))(*[m._h.value for m in pool])
+    descs = (CircuitDesc * max(1, len(circuits)))()
+    keep = []
+    for i, c in enumerate(circuits):
+        arr = (C.c_void_p * max(1, len(c["layers"])))(*[dl.value for dl in c["layers"]])
+        keep.append(arr)
+        descs[i] = CircuitDesc(c["n_sites"], c["chi_max"], c["k_max"], int(c.get("use_ppt", True)),
+                               len(c["layers"]), arr, c.get("J", 1.0), c.get("hx", 1.0),
+                               c.get("b", 0.0))
+    out = np.zeros((len(circuits), 4))
+    status = np.zeros(len(circuits), dtype=np.int32)
+    rc = LIB.mpdo_batch_run(len(pool), handles, len(circuits), descs, _dptr(out),
+                            status.ctypes.data_as(C.POINTER(C.c_int)))
+    if rc != 0:
+        bad = [(i, int(x)) for i, x in enumerate(status) if x]
+        msg = LIB.mpdo_last_error(None)
+        raise MpdoError(rc, f"{msg.decode() if msg else ''}; failed circuits {bad[:8]}")
+    return out
 
 
 def kernel_launches() -> int:

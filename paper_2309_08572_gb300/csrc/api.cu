@@ -25,6 +25,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/mpdo.h"
@@ -72,6 +73,10 @@ struct mpdo_ctx {
   cudaStream_t st = nullptr;
   std::string err;
   int n = 0, chi = 0, kmax = 0, mmax = 1;
+  int n_cap = 0, chi_cap = 0, kmax_cap = 0;   // allocation capacity (mpdo_reconfigure)
+  int use_ppt = 1;
+  int device = 0;
+  bool own_stream = false;
   bool dbl = true;     // complex128 state and arithmetic
   bool rev = false;    // chain stored mirrored
   int centre = 0;      // user coordinates
@@ -87,6 +92,7 @@ struct mpdo_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   std::vector<void*> allocs;
+  void *wPol, *wQol, *wGa;   // polar correction of the new left tensor (keep x keep)
   void *wM, *wGi, *wGj, *wVg, *wR, *wVs, *wVr, *wPhi, *wX, *wH, *wU, *wVgen, *wW, *wTmp, *wQ,
       *wWB, *wBp, *wWK, *wVk, *wVks, *wCn, *wRs, *wIrs, *eigmem;
   double *wSig, *wLam, *wWv, *wF;
@@ -103,7 +109,7 @@ struct mpdo_ctx {
   void* obs = nullptr;
   size_t obs_bytes = 0;
   // optional per-class kernel timing (0: GEMM, 1: eigensolver, 2: other kernels)
-  struct ProfRec { int cls; int e0; double flops; };
+  struct ProfRec { int cls; int e0; double flops; int slot; double per_count; };
   int prof_mask = 0;
   std::vector<cudaEvent_t> prof_ev;
   int prof_used = 0;
@@ -111,6 +117,8 @@ struct mpdo_ctx {
   double prof_ms[3] = {0, 0, 0};
   long long prof_cnt[3] = {0, 0, 0};
   double prof_flops[3] = {0, 0, 0};
+  int* prof_counts = nullptr;   // pinned: active pair-rounds of profiled eigensolves
+  int prof_nslots = 0, prof_slot = 0;
 
   void* site(int buf, int s) const {
     return static_cast<char*>(sites[buf]) + (size_t)s * site_cap * elt;
@@ -139,10 +147,10 @@ int prof_begin(mpdo_ctx* h, int cls) {
   cudaEventRecord(h->prof_ev[i], h->st);
   return i;
 }
-void prof_end(mpdo_ctx* h, int cls, int i, double flops) {
+void prof_end(mpdo_ctx* h, int cls, int i, double flops, int slot = -1, double per_count = 0) {
   if (i < 0) return;
   cudaEventRecord(h->prof_ev[i + 1], h->st);
-  h->prof_recs.push_back({cls, i, flops});
+  h->prof_recs.push_back({cls, i, flops, slot, per_count});
 }
 // called after the stream has been synchronised
 void prof_drain(mpdo_ctx* h) {
@@ -152,11 +160,13 @@ void prof_drain(mpdo_ctx* h) {
       h->prof_ms[r.cls] += ms;
       h->prof_cnt[r.cls] += 1;
       h->prof_flops[r.cls] += r.flops;
+      if (r.slot >= 0) h->prof_flops[r.cls] += r.per_count * h->prof_counts[r.slot];
     }
   }
   cudaGetLastError();
   h->prof_recs.clear();
   h->prof_used = 0;
+  h->prof_slot = 0;
 }
 #define PO(expr)                     \
   do {                               \
@@ -210,7 +220,15 @@ template <typename R>
 cudaError_t peig(mpdo_ctx* h, int n, const cx<R>* a, long lda, cx<R>* v, long ldv, double* w) {
   int pi = prof_begin(h, 1);
   cudaError_t e = heig<R>(h->st, n, a, lda, v, ldv, w, eigw<R>(h), h->max_sweeps);
-  prof_end(h, 1, pi, 0.0);
+  if (pi >= 0 && e == cudaSuccess && h->prof_slot < h->prof_nslots) {
+    // executed flops: 8 real flops per complex MAC, 3*16*16*np MACs per active pair-round
+    int slot = h->prof_slot++;
+    e = cudaMemcpyAsync(&h->prof_counts[slot], eigw<R>(h).counters + 3, sizeof(int),
+                        cudaMemcpyDeviceToHost, h->st);
+    prof_end(h, 1, pi, 0.0, slot, 8.0 * 3 * 256 * (double)eig_padded_n(n));
+  } else {
+    prof_end(h, 1, pi, 0.0);
+  }
   return e;
 }
 
@@ -268,7 +286,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   CK(pgemm<R>(h, OP_N, OP_C, n9, n3, n3, wX, n9, n3, wR, n3, 0, wH, n9, n3, 3));
   // a6: bond eigenpairs and cut
   CK(peig<R>(h, n9, wH, n9, wU, n9, h->wLam));
-  PO(bond_select(st, n9, h->wLam, h->htol, chi, h->dsc, h->dstats));
+  PO(bond_select<R>(st, n9, h->wLam, wH, n9, h->htol, chi, h->dsc, h->dstats));
   int rc = read_scalars(h);
   if (rc) return rc;
   const int keep = h->hsc->keep;
@@ -279,7 +297,22 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
               (long)n3 * keep, 3));
   CK(pgemm<R>(h, OP_N, OP_N, dl * ki, keep, n3, wM, n3, 0, wVgen, keep, (long)n3 * keep, wTmp,
               3L * keep, keep, 3));
-  PO(swap12<T>(st, dl, ki, 3, keep, wTmp, ai));
+  // The left factor (M_i x I)(I x V sigma^-1/2) u is an isometry only up to the error of
+  // the small-sigma eigenvectors of G_i, amplified by sigma^-1/2.  One Newton-Schulz polar
+  // step (Higham) restores it: A <- A (3I - A^+A)/2 and, to keep theta' = A B, the centre's
+  // factor W <- W (I + A^+A)/2.
+  {
+    T* wGa = static_cast<T*>(h->wGa);
+    T* wPol = static_cast<T*>(h->wPol);
+    T* wQol = static_cast<T*>(h->wQol);
+    const int rows = dl * ki * 3;
+    CK(pgemm<R>(h, OP_C, OP_N, keep, keep, rows, wTmp, keep, 0, wTmp, keep, 0, wGa, keep, 0, 1));
+    PO(polar_factors<R>(st, keep, wGa, wPol, wQol));
+    CK(pgemm<R>(h, OP_N, OP_N, rows, keep, keep, wTmp, keep, 0, wPol, keep, 0, wM, keep, 0, 1));
+    CK(pgemm<R>(h, OP_N, OP_N, n9, keep, keep, wW, keep, 0, wQol, keep, 0, wVgen, keep, 0, 1));
+    std::swap(wW, wVgen);   // W now holds the corrected factor
+  }
+  PO(swap12<T>(st, dl, ki, 3, keep, wM, ai));
   PO(make_q<R>(st, dm, keep, M, wW, E, h->dsc, wQ));
   CK(pgemm<R>(h, OP_N, OP_N, keep * 3 * M, kj * dr, n3, wQ, n3, 0, aj, (long)kj * dr, 0, wWB,
               (long)kj * dr, 0, 1));
@@ -290,7 +323,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   CK(pgemm<R>(h, OP_N, OP_C, KM, KM, colsB, wBp, colsB, 0, wBp, colsB, 0, wWK, KM, 0, 1));
   CK(peig<R>(h, KM, wWK, KM, wVk, KM, h->wWv));
   // a9: cut + PPT (FP64 scalars)
-  PO(kraus_select(st, KM, h->wWv, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
+  PO(kraus_select<R>(st, KM, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
   rc = read_scalars(h);
   if (rc) return rc;
   const int kk = h->hsc->kkeep;
@@ -693,10 +726,20 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   if (!h) return fail(nullptr, MPDO_ERR_OOM, "host allocation");
   mpdo_ctx* hp = h.get();
   h->cfg = *cfg;
-  h->st = static_cast<cudaStream_t>(cfg->cuda_stream);
-  h->n = cfg->n_sites;
-  h->chi = cfg->chi_max;
-  h->kmax = cfg->k_max;
+  cudaGetDevice(&h->device);
+  if (cfg->cuda_stream) {
+    h->st = static_cast<cudaStream_t>(cfg->cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(nullptr, MPDO_ERR_CUDA, "stream creation failed");
+    }
+    h->own_stream = true;
+  }
+  h->n = h->n_cap = cfg->n_sites;
+  h->chi = h->chi_cap = cfg->chi_max;
+  h->kmax = h->kmax_cap = cfg->k_max;
+  h->use_ppt = cfg->use_ppt;
   h->mmax = cfg->m_max;
   h->dbl = (cfg->prec == MPDO_FP64);
   h->elt = h->dbl ? 16 : 8;
@@ -727,6 +770,8 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
       (rc = A(&h->wQ, D * 3 * M * n3)) || (rc = A(&h->wWB, D * 3 * M * K * D)) ||
       (rc = A(&h->wBp, D * 3 * M * K * D)) || (rc = A(&h->wWK, KM * KM)) ||
       (rc = A(&h->wVk, KM * KM)) || (rc = A(&h->wVks, KM * K)) || (rc = A(&h->wCn, K * D * 3 * D)))
+    return rc;
+  if ((rc = A(&h->wPol, D * D)) || (rc = A(&h->wQol, D * D)) || (rc = A(&h->wGa, D * D)))
     return rc;
   const size_t rsz = h->dbl ? 8 : 4;
   if ((rc = alloc_dev(hp, &h->wRs, n3 * rsz)) || (rc = alloc_dev(hp, &h->wIrs, n3 * rsz)) ||
@@ -761,7 +806,7 @@ int mpdo_apply_layer(mpdo_t h, const mpdo_layer* layer, mpdo_trunc_stats* stats)
   if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
   int rc = prepare_layer(h, layer, &h->staged, true);
   if (rc) return rc;
-  return run_ops(h, h->staged.ops, stats, h->chi, h->kmax, h->cfg.use_ppt);
+  return run_ops(h, h->staged.ops, stats, h->chi, h->kmax, h->use_ppt);
 }
 
 int mpdo_layer_upload(mpdo_t h, const mpdo_layer* layer, mpdo_dlayer* out) {
@@ -776,7 +821,7 @@ int mpdo_layer_upload(mpdo_t h, const mpdo_layer* layer, mpdo_dlayer* out) {
 
 int mpdo_apply_dlayer(mpdo_t h, mpdo_dlayer dl, mpdo_trunc_stats* stats) {
   if (!h || !dl) return fail(h, MPDO_ERR_ARG, "null handle or layer");
-  return run_ops(h, dl->ops, stats, h->chi, h->kmax, h->cfg.use_ppt);
+  return run_ops(h, dl->ops, stats, h->chi, h->kmax, h->use_ppt);
 }
 
 int mpdo_layer_free(mpdo_t h, mpdo_dlayer dl) {
@@ -825,6 +870,74 @@ int mpdo_sample_probs(mpdo_t h, int n_samples, uint64_t seed, uint8_t* bits, dou
   if (n_samples == 0) return MPDO_OK;
   return h->dbl ? sample<double>(h, n_samples, seed, bits, probs)
                 : sample<float>(h, n_samples, seed, bits, probs);
+}
+
+int mpdo_reconfigure(mpdo_t h, int n_sites, int chi_max, int k_max, int use_ppt,
+                     const double* init_site_vec) {
+  if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
+  if (n_sites < 2 || n_sites > h->n_cap || chi_max < 1 || chi_max > h->chi_cap || k_max < 1 ||
+      k_max > h->kmax_cap)
+    return fail(h, MPDO_ERR_ARG, "reconfigure limits exceed the handle's capacity");
+  CK(cudaStreamSynchronize(h->st));
+  h->n = n_sites;
+  h->chi = chi_max;
+  h->kmax = k_max;
+  h->use_ppt = use_ppt;
+  h->bond.assign(h->n + 1, 1);
+  h->kd.assign(h->n, 1);
+  return init_state(h, init_site_vec);
+}
+
+namespace {
+int run_circuit(mpdo_t h, const mpdo_circuit& c, double* out) {
+  int rc = mpdo_reconfigure(h, c.n_sites, c.chi_max, c.k_max, c.use_ppt, nullptr);
+  if (rc) return rc;
+  for (int l = 0; l < c.n_layers; ++l) {
+    if (!c.layers[l]) return fail(h, MPDO_ERR_ARG, "null layer in circuit");
+    rc = run_ops(h, c.layers[l]->ops, nullptr, h->chi, h->kmax, h->use_ppt);
+    if (rc) return rc;
+  }
+  return mpdo_expect_energy(h, c.J, c.hx, c.b, out, out + 1, out + 2, out + 3);
+}
+}  // namespace
+
+int mpdo_batch_run(int n_handles, mpdo_t* handles, int n_circuits, const mpdo_circuit* circuits,
+                   double* out, int* status) {
+  if (n_handles < 1 || !handles || n_circuits < 0 || (n_circuits > 0 && (!circuits || !out)))
+    return fail(nullptr, MPDO_ERR_ARG, "bad batch arguments");
+  for (int k = 0; k < n_handles; ++k)
+    if (!handles[k]) return fail(nullptr, MPDO_ERR_ARG, "null handle in pool");
+  for (int k = 0; k < n_handles; ++k)
+    for (int j = k + 1; j < n_handles; ++j)
+      if (handles[k] == handles[j]) return fail(nullptr, MPDO_ERR_ARG, "handle repeated in pool");
+  std::atomic<int> next{0};
+  std::vector<int> st(n_circuits, MPDO_OK);
+  std::vector<std::string> msg(n_circuits);
+  auto worker = [&](int k) {
+    mpdo_t h = handles[k];
+    cudaSetDevice(h->device);
+    for (;;) {
+      int i = next.fetch_add(1);
+      if (i >= n_circuits) break;
+      st[i] = run_circuit(h, circuits[i], out + 4 * (size_t)i);
+      if (st[i]) msg[i] = h->err;
+    }
+  };
+  const int nt = std::min(n_handles, std::max(1, n_circuits));
+  std::vector<std::thread> pool;
+  for (int k = 1; k < nt; ++k) pool.emplace_back(worker, k);
+  worker(0);
+  for (auto& t : pool) t.join();
+  int first = MPDO_OK;
+  for (int i = 0; i < n_circuits; ++i) {
+    if (status) status[i] = st[i];
+    if (st[i] && first == MPDO_OK) first = st[i];
+  }
+  if (first) {
+    for (int i = 0; i < n_circuits; ++i)
+      if (st[i]) { g_err = "batch: circuit " + std::to_string(i) + ": " + msg[i]; break; }
+  }
+  return first;
 }
 
 int mpdo_get_dims(mpdo_t h, int* bond_dims, int* kraus_dims, int* centre) {
@@ -880,10 +993,12 @@ int mpdo_destroy(mpdo_t h) {
   else cudaDeviceSynchronize();
   for (void* p : h->allocs) cudaFree(p);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+  if (h->prof_counts) cudaFreeHost(h->prof_counts);
   if (h->staged.mem) cudaFree(h->staged.mem);
   if (h->obs) cudaFree(h->obs);
   if (h->hsc) cudaFreeHost(h->hsc);
   if (h->hstats) cudaFreeHost(h->hstats);
+  if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
   return MPDO_OK;
 }
@@ -898,6 +1013,8 @@ int mpdo_profile(mpdo_t h, int class_mask) {
   if (class_mask && h->prof_ev.empty()) {
     h->prof_ev.resize(8192);
     for (auto& e : h->prof_ev) CK(cudaEventCreate(&e));
+    h->prof_nslots = 4096;
+    CK(cudaMallocHost((void**)&h->prof_counts, sizeof(int) * h->prof_nslots));
   }
   CK(cudaStreamSynchronize(h->st));
   prof_drain(h);

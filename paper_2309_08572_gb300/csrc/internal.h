@@ -24,6 +24,9 @@ struct EigWork {
 
 template <typename R>
 size_t eig_work_bytes(int n_cap);
+// padded size used by the eigensolver; each active pair-round of the block Jacobi does
+// 3 * 16 * 16 * padded_n complex multiply-adds (rows, columns and eigenvectors)
+int eig_padded_n(int n);
 template <typename R>
 void eig_work_bind(EigWork<R>& w, void* base, int n_cap);
 

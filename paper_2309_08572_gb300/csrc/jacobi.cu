@@ -11,6 +11,7 @@
 // L2 (it is at most a few MB).
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/mpdo.h"
@@ -27,6 +28,10 @@ constexpr int JW = 8;          // block width
 constexpr int JS = 2 * JW;     // sub-problem size
 constexpr int JT = 256;        // threads per CTA
 constexpr int CH = 64;         // staged chunk (columns in phase A, rows in phase B)
+// Sweeps of the 16x16 sub-problem per block-pair visit.  One sweep per visit is the
+// classic one-sided-update choice: the outer rounds keep rotating the pair, so a fully
+// converged sub-problem buys little and costs 15 warp rounds per extra sweep.
+constexpr int kInnerSweeps = 1;
 
 __device__ __forceinline__ void tourney(int round, int k, int players, int& a, int& b) {
   // circle method: player players-1 fixed, others rotate
@@ -41,8 +46,8 @@ __device__ __forceinline__ void tourney(int round, int k, int players, int& a, i
 }
 
 template <typename R> struct Tol;
-template <> struct Tol<double> { static constexpr double rel = 1e-15, abs = 1e-17; };
-template <> struct Tol<float> { static constexpr float rel = 2e-7f, abs = 1e-9f; };
+template <> struct Tol<double> { static constexpr double rel = 1e-15, abs = 2.2e-16; };
+template <> struct Tol<float> { static constexpr float rel = 2e-7f, abs = 1.2e-7f; };
 
 template <typename R>
 __global__ void pad_copy_kernel(int n, int np, const cx<R>* __restrict__ a, long lda,
@@ -72,15 +77,18 @@ __global__ void __launch_bounds__(JT) jacobi_coop_kernel(int np, int nblk, cx<R>
   __shared__ R rc[JS / 2], rs[JS / 2];
   __shared__ T re[JS / 2];
   __shared__ int ra[JS / 2], rb[JS / 2], rflag[JS / 2];
-  __shared__ int any_rot, any_inner;
+  __shared__ int any_rot;
   __shared__ R s_anorm;
   const int tid = threadIdx.x;
 
-  // |A| scale for the absolute rotation floor: sum of |diag|
-  if (tid == 0) {
-    R s = 0;
-    for (int i = 0; i < np; ++i) s += fabs(ap[(long)i * np + i].x);
-    s_anorm = s;
+  // |A| scale for the absolute rotation floor: sum of |diag| (block reduction)
+  {
+    R part = 0;
+    for (int i = tid; i < np; i += JT) part += fabs(ap[(long)i * np + i].x);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (tid == 0) s_anorm = 0;
+    __syncthreads();
+    if ((tid & 31) == 0) atomicAdd(&s_anorm, part);
   }
   __syncthreads();
   const R atol = Tol<R>::abs * s_anorm;
@@ -97,69 +105,75 @@ __global__ void __launch_bounds__(JT) jacobi_coop_kernel(int np, int nblk, cx<R>
         S[a][b] = ap[(long)idx[a] * np + idx[b]];
         U[a][b] = mkc<R>(a == b ? 1 : 0, 0);
       }
-      if (tid == 0) any_rot = 0;
       __syncthreads();
-      // ---- scalar cyclic Jacobi on S
-      for (int inner = 0; inner < 12; ++inner) {
-        if (tid == 0) any_inner = 0;
-        __syncthreads();
-        for (int r = 0; r < JS - 1; ++r) {
-          if (tid < JS / 2) {
-            int a, b;
-            tourney(r, tid, JS, a, b);
-            if (a > b) { int t = a; a = b; b = t; }
-            T g = S[a][b];
-            R ag = sqrt(cabs2(g));
-            R al = S[a][a].x, be = S[b][b].x;
-            int f = (ag > Tol<R>::rel * sqrt(fabs(al * be))) && (ag > atol);
-            ra[tid] = a; rb[tid] = b; rflag[tid] = f;
-            if (f) {
-              R tau = (be - al) / (2 * ag);
-              R t = (tau >= 0 ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
-              R c = R(1) / sqrt(R(1) + t * t);
-              rc[tid] = c; rs[tid] = t * c;
-              re[tid] = mkc<R>(g.x / ag, g.y / ag);
-              any_inner = 1;
-              any_rot = 1;
+      // ---- scalar cyclic Jacobi on S, by warp 0 alone (warp-level barriers only)
+      if (tid < 32) {
+        const int lane = tid;
+        int rot_seen = 0;
+        for (int inner = 0; inner < kInnerSweeps; ++inner) {
+          int any_inner_w = 0;
+          for (int r = 0; r < JS - 1; ++r) {
+            int f = 0;
+            if (lane < JS / 2) {
+              int a, b;
+              tourney(r, lane, JS, a, b);
+              if (a > b) { int t = a; a = b; b = t; }
+              T g = S[a][b];
+              R ag = sqrt(cabs2(g));
+              R al = S[a][a].x, be = S[b][b].x;
+              f = (ag > Tol<R>::rel * sqrt(fabs(al * be))) && (ag > atol);
+              ra[lane] = a; rb[lane] = b; rflag[lane] = f;
+              if (f) {
+                R tau = (be - al) / (2 * ag);
+                R t = (tau >= 0 ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+                R c = R(1) / sqrt(R(1) + t * t);
+                rc[lane] = c; rs[lane] = t * c;
+                re[lane] = mkc<R>(g.x / ag, g.y / ag);
+              }
             }
-          }
-          __syncthreads();
-          // rows: S <- U^+ S on rows (a, b)
-          for (int e = tid; e < (JS / 2) * JS; e += JT) {
-            int p = e / JS, col = e % JS;
-            if (!rflag[p]) continue;
-            int a = ra[p], b = rb[p];
-            R c = rc[p], s = rs[p];
-            T ee = re[p];
-            T x = S[a][col], y = S[b][col];
-            S[a][col] = csub(cscale(x, c), cscale(cmul(ee, y), s));
-            S[b][col] = cadd(cscale(cmulc(x, ee), s), cscale(y, c));
-          }
-          __syncthreads();
-          // cols: S <- S U and U_acc <- U_acc U on cols (a, b)
-          for (int e = tid; e < (JS / 2) * JS * 2; e += JT) {
-            int which = e / ((JS / 2) * JS);
-            int e2 = e % ((JS / 2) * JS);
-            int p = e2 / JS, row = e2 % JS;
-            if (!rflag[p]) continue;
-            int a = ra[p], b = rb[p];
-            R c = rc[p], s = rs[p];
-            T ee = re[p];
-            if (which) {
-              T x = U[row][a], y = U[row][b];
-              U[row][a] = csub(cscale(x, c), cscale(cmulc(y, ee), s));
-              U[row][b] = cadd(cscale(cmul(x, ee), s), cscale(y, c));
-            } else {
-              T x = S[row][a], y = S[row][b];
-              S[row][a] = csub(cscale(x, c), cscale(cmulc(y, ee), s));
-              S[row][b] = cadd(cscale(cmul(x, ee), s), cscale(y, c));
+            const unsigned any_f = __ballot_sync(0xffffffffu, f);
+            __syncwarp();
+            if (!any_f) continue;
+            any_inner_w = 1;
+            // rows: S <- U^+ S on rows (a, b)
+            for (int e = lane; e < (JS / 2) * JS; e += 32) {
+              int p = e / JS, col = e % JS;
+              if (!rflag[p]) continue;
+              int a = ra[p], b = rb[p];
+              R c = rc[p], s = rs[p];
+              T ee = re[p];
+              T x = S[a][col], y = S[b][col];
+              S[a][col] = csub(cscale(x, c), cscale(cmul(ee, y), s));
+              S[b][col] = cadd(cscale(cmulc(x, ee), s), cscale(y, c));
             }
+            __syncwarp();
+            // cols: S <- S U and U_acc <- U_acc U on cols (a, b)
+            for (int e = lane; e < (JS / 2) * JS * 2; e += 32) {
+              int which = e / ((JS / 2) * JS);
+              int e2 = e % ((JS / 2) * JS);
+              int p = e2 / JS, row = e2 % JS;
+              if (!rflag[p]) continue;
+              int a = ra[p], b = rb[p];
+              R c = rc[p], s = rs[p];
+              T ee = re[p];
+              if (which) {
+                T x = U[row][a], y = U[row][b];
+                U[row][a] = csub(cscale(x, c), cscale(cmulc(y, ee), s));
+                U[row][b] = cadd(cscale(cmul(x, ee), s), cscale(y, c));
+              } else {
+                T x = S[row][a], y = S[row][b];
+                S[row][a] = csub(cscale(x, c), cscale(cmulc(y, ee), s));
+                S[row][b] = cadd(cscale(cmul(x, ee), s), cscale(y, c));
+              }
+            }
+            __syncwarp();
           }
-          __syncthreads();
+          rot_seen |= any_inner_w;
+          if (!any_inner_w) break;
         }
-        if (!any_inner) break;
-        __syncthreads();
+        if (lane == 0) any_rot = rot_seen;
       }
+      __syncthreads();
       const int active = any_rot;
       // One Newton-Schulz polar step U <- U (3I - U^+U)/2 removes the drift of the
       // accumulated rotations from unitarity (quadratic in the drift), so repeated
@@ -229,7 +243,10 @@ __global__ void __launch_bounds__(JT) jacobi_coop_kernel(int np, int nblk, cx<R>
           }
           __syncthreads();
         }
-        if (tid == 0) atomicAdd(&counters[sweep & 1], 1);
+        if (tid == 0) {
+          atomicAdd(&counters[sweep & 1], 1);
+          atomicAdd(&counters[3], 1);  // active pair-rounds, for the flop count
+        }
       }
       grid.sync();
       if (round == 0 && blockIdx.x == 0 && tid == 0) counters[(sweep + 1) & 1] = 0;
@@ -251,8 +268,16 @@ __global__ void eig_finalize_kernel(int n, int np, const cx<R>* __restrict__ ap,
   while (P < n) P <<= 1;
   double* key = reinterpret_cast<double*>(smem_raw);
   int* val = reinterpret_cast<int*>(key + P);
+  __shared__ int s_nan;
+  if (threadIdx.x == 0) s_nan = 0;
+  __syncthreads();
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    key[i] = (i < n) ? (double)ap[(long)i * np + i].x : -INFINITY;
+    double kv = -INFINITY;
+    if (i < n) {
+      kv = (double)ap[(long)i * np + i].x;
+      if (!isfinite(kv)) { s_nan = 1; kv = -INFINITY; }
+    }
+    key[i] = kv;
     val[i] = i;
   }
   __syncthreads();
@@ -273,13 +298,161 @@ __global__ void eig_finalize_kernel(int n, int np, const cx<R>* __restrict__ ap,
       __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = key[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = (s_nan && i == 0) ? NAN : key[i];
   long total = (long)n * n;
   for (long e = threadIdx.x; e < total; e += blockDim.x) {
     int i = (int)(e / n), k = (int)(e % n);
-    v[(long)i * ldv + k] = vp[(long)i * np + val[k]];
+    int col = val[k];
+    col = (col >= 0 && col < n) ? col : k;
+    v[(long)i * ldv + k] = vp[(long)i * np + col];
   }
 }
+
+// ---------------------------------------------------------------------------------------
+// Single-CTA cyclic Jacobi with the whole problem resident in shared memory: the Hermitian
+// matrix A and the accumulator V live in shared memory; each round of the round-robin
+// ordering rotates np/2 disjoint index pairs at once (GVL sym.schur2 with the complex
+// phase factored out): rotation parameters, then the rows, then the columns of A and V,
+// with one block barrier between the three steps.  Rotations act on A itself (two-sided),
+// so eigenvectors are accurate to eps |A| / gap.  Used for n <= smem_jacobi_max<R>().
+constexpr int SJ_THREADS = 1024;
+
+template <typename R>
+__global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
+                                                                 const cx<R>* __restrict__ a,
+                                                                 long lda, cx<R>* v, long ldv,
+                                                                 double* w, int* counters,
+                                                                 int max_sweeps) {
+  using T = cx<R>;
+  extern __shared__ unsigned char sj_raw[];
+  T* A = reinterpret_cast<T*>(sj_raw);       // row-major np x np
+  T* V = A + (size_t)np * np;
+  __shared__ R s_anorm;
+  __shared__ int s_rot;
+  __shared__ double s_key[128];
+  __shared__ int s_val[128];
+  __shared__ R pc[64], ps[64];
+  __shared__ T pe[64];
+  __shared__ int pp[64], pq[64], pf[64];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nthr = blockDim.x;
+  const int half = np / 2;
+  for (int e = tid; e < np * np; e += nthr) {
+    int i = e / np, j = e % np;
+    A[e] = (i < n && j < n) ? a[(long)i * lda + j] : mkc<R>(0, 0);
+    V[e] = mkc<R>(i == j ? 1 : 0, 0);
+  }
+  if (tid == 0) s_anorm = 0;
+  __syncthreads();
+  if (tid < 32) {
+    R part = 0;
+    for (int i = lane; i < n; i += 32) part += fabs(A[(size_t)i * np + i].x);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) s_anorm = part;
+  }
+  __syncthreads();
+  const R atol = Tol<R>::abs * s_anorm;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < np - 1; ++r) {
+      for (int k = tid; k < half; k += nthr) {
+        int p, q;
+        tourney(r, k, np, p, q);
+        if (p > q) { int t = p; p = q; q = t; }
+        T g = A[(size_t)p * np + q];
+        R ag = sqrt(cabs2(g));
+        R al = A[(size_t)p * np + p].x, be = A[(size_t)q * np + q].x;
+        int f = (ag > Tol<R>::rel * sqrt(fabs(al * be))) && (ag > atol);
+        pp[k] = p; pq[k] = q; pf[k] = f;
+        if (f) {
+          R tau = (be - al) / (2 * ag);
+          R t = (tau >= 0 ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+          R c = R(1) / sqrt(R(1) + t * t);
+          pc[k] = c; ps[k] = t * c;
+          pe[k] = mkc<R>(g.x / ag, g.y / ag);
+          atomicAdd(&s_rot, 1);
+        }
+      }
+      __syncthreads();
+      // rows: A <- U^+ A on rows (p, q)
+      for (int e = tid; e < half * np; e += nthr) {
+        int k = e / np, col = e % np;
+        if (!pf[k]) continue;
+        int p = pp[k], q = pq[k];
+        R c = pc[k], s = ps[k];
+        T ee = pe[k];
+        T x = A[(size_t)p * np + col], y = A[(size_t)q * np + col];
+        A[(size_t)p * np + col] = csub(cscale(x, c), cscale(cmul(ee, y), s));
+        A[(size_t)q * np + col] = cadd(cscale(cmulc(x, ee), s), cscale(y, c));
+      }
+      __syncthreads();
+      // columns: A <- A U, V <- V U on columns (p, q)
+      for (int e = tid; e < 2 * half * np; e += nthr) {
+        int isv = e >= half * np;
+        int e2 = isv ? e - half * np : e;
+        int k = e2 / np, row = e2 % np;
+        if (!pf[k]) continue;
+        int p = pp[k], q = pq[k];
+        R c = pc[k], s = ps[k];
+        T ee = pe[k];
+        T* M = isv ? V : A;
+        T x = M[(size_t)row * np + p], y = M[(size_t)row * np + q];
+        M[(size_t)row * np + p] = csub(cscale(x, c), cscale(cmulc(y, ee), s));
+        M[(size_t)row * np + q] = cadd(cscale(cmul(x, ee), s), cscale(y, c));
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) { ++sweep; break; }
+  }
+  // eigenvalues = diagonal; sort descending (n <= 128)
+  __shared__ int s_nan;
+  if (tid == 0) s_nan = 0;
+  __syncthreads();
+  for (int c = tid; c < 128; c += nthr) {
+    double key = -INFINITY;
+    if (c < n) {
+      key = (double)A[(size_t)c * np + c].x;
+      if (!isfinite(key)) { s_nan = 1; key = -INFINITY; }
+    }
+    s_key[c] = key;
+    s_val[c] = c;
+  }
+  __syncthreads();
+  for (int k = 2; k <= 128; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int c = tid; c < 128; c += nthr) {
+        int l = c ^ j;
+        if (l > c) {
+          bool desc = ((c & k) == 0);
+          double ki = s_key[c], kl = s_key[l];
+          if (desc ? (ki < kl) : (ki > kl)) {
+            s_key[c] = kl; s_key[l] = ki;
+            int t = s_val[c]; s_val[c] = s_val[l]; s_val[l] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // a non-finite input is reported as a NaN leading eigenvalue (callers flag it); the
+  // gather index is clamped so a broken permutation can never leave the arrays
+  for (int i = tid; i < n; i += nthr) w[i] = (s_nan && i == 0) ? NAN : s_key[i];
+  for (int e = tid; e < n * n; e += nthr) {
+    int i = e / n, k = e % n;
+    int col = s_val[k];
+    col = (col >= 0 && col < n) ? col : k;
+    v[(long)i * ldv + k] = V[(size_t)i * np + col];
+  }
+  if (tid == 0 && counters) {
+    counters[2] = sweep;
+    counters[3] = 0;
+  }
+}
+
+template <typename R>
+constexpr int smem_jacobi_max() { return sizeof(R) == 8 ? 84 : 118; }
 
 inline int padded_n(int n) {
   int nblk = (n + JW - 1) / JW;
@@ -289,6 +462,8 @@ inline int padded_n(int n) {
 }
 
 }  // namespace
+
+int eig_padded_n(int n) { return padded_n(n); }
 
 template <typename R>
 size_t eig_work_bytes(int n_cap) {
@@ -310,6 +485,24 @@ cudaError_t heig(cudaStream_t st, int n, const cx<R>* a, long lda, cx<R>* v, lon
                  double* w, EigWork<R>& work, int max_sweeps) {
   if (n <= 0) return cudaSuccess;
   if (n > work.n_cap) return cudaErrorInvalidValue;
+  if (n <= smem_jacobi_max<R>()) {
+    int np2 = n + (n & 1);
+    size_t sm = 2ull * np2 * np2 * sizeof(cx<R>);
+    static bool attr_set = false;
+    if (!attr_set) {
+      MPDO_CUDA_TRY(cudaFuncSetAttribute(jacobi_smem_kernel<R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2ull * 118 * 118 * sizeof(float2) > 2ull * 84 * 84 * sizeof(double2)
+                                                   ? 2ull * 118 * 118 * sizeof(float2)
+                                                   : 2ull * 84 * 84 * sizeof(double2))));
+      attr_set = true;
+    }
+    count_launch();
+    int thr = std::min(SJ_THREADS, std::max(64, ((np2 / 2) * np2 + 31) / 32 * 32));
+    jacobi_smem_kernel<R><<<1, thr, sm, st>>>(n, np2, a, lda, v, ldv, w, work.counters,
+                                              max_sweeps);
+    return cudaGetLastError();
+  }
   int np = padded_n(n);
   int nblk = np / JW;
   long total = (long)np * np;

@@ -146,8 +146,11 @@ __global__ void build_phi_kernel(int dm, const cx<R>* __restrict__ ct,
 }
 
 // Bond cut on the spectrum lam (descending, n): keep <= chi values above htol*lam0.
-__global__ void bond_select_kernel(int n, const double* __restrict__ lam, double htol, int chi,
-                                   StepScalars* sc, DevStats* st) {
+// The total weight is the trace of the matrix itself (noise-free in expectation), not
+// the sum of the positive computed eigenvalues, which is biased upward by the noise floor.
+template <typename R>
+__global__ void bond_select_kernel(int n, const double* __restrict__ lam, const cx<R>* __restrict__ hm,
+                                   long ldh, double htol, int chi, StepScalars* sc, DevStats* st) {
   __shared__ double red_tot[256], red_kept[256];
   __shared__ int s_keep;
   double l0 = lam[0];
@@ -164,9 +167,8 @@ __global__ void bond_select_kernel(int n, const double* __restrict__ lam, double
   int keep = s_keep;
   double t = 0, kp = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = lam[i] > 0 ? lam[i] : 0.0;
-    t += v;
-    if (i < keep) kp += v;
+    t += (double)hm[(long)i * ldh + i].x;
+    if (i < keep) kp += lam[i] > 0 ? lam[i] : 0.0;
   }
   red_tot[threadIdx.x] = t;
   red_kept[threadIdx.x] = kp;
@@ -223,8 +225,10 @@ __global__ void make_q_kernel(int dm, int keep, int m_ops, const cx<R>* __restri
 // Inner-index cut + purity-preserving truncation (Sec. III.D Eqs. xiformula / ppt with
 // T = 1, P = identity; theta = 0 when infeasible; clamp negatives; keep the trace).
 // Writes f[k] = sqrt(Lambda~_k / w_k) for k < kk.
-__global__ void kraus_select_kernel(int n, const double* __restrict__ w, double kcut, int kmax,
-                                    int use_ppt, double* f, StepScalars* sc, DevStats* st) {
+template <typename R>
+__global__ void kraus_select_kernel(int n, const double* __restrict__ w, const cx<R>* __restrict__ wm,
+                                    double kcut, int kmax, int use_ppt, double* f, StepScalars* sc,
+                                    DevStats* st) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double w0 = w[0] > 0 ? w[0] : 0.0;
   bool bad = !(w0 > 0.0) || !isfinite(w0);
@@ -237,10 +241,11 @@ __global__ void kraus_select_kernel(int n, const double* __restrict__ w, double 
   double sum = 0, sq = 0, sumk = 0, sqk = 0;
   for (int i = 0; i < n; ++i) {
     double v = w[i] > 0 ? w[i] : 0.0;
-    sum += v;
+    sum += (double)wm[(long)i * n + i].x;   // trace of the Gram = total weight
     sq += v * v;
     if (i < kk) { sumk += v; sqk += v * v; }
   }
+
   double theta = 0.0;
   int infeas = 0, clamped = 0;
   double lt[1024];
@@ -408,6 +413,22 @@ __global__ void sample_pick_kernel(int dr, const cx<R>* __restrict__ ev, const c
   for (long e = threadIdx.x; e < plane; e += blockDim.x) env_out[(long)smp * plane + e] = src[e];
 }
 
+// Newton-Schulz polar step for a near-isometry A with Gram G = A^+A (n x n):
+// P = (3I - G)/2 (applied to A) and Q = (I + G)/2 (applied to the other factor), so that
+// A P has unit Gram to second order and (A P)(Q B) = A B - A E^2 B / 4 with E = G - I.
+template <typename R>
+__global__ void polar_factors_kernel(int n, const cx<R>* __restrict__ g, cx<R>* pm, cx<R>* qm) {
+  long total = (long)n * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    int i = (int)(e / n), j = (int)(e % n);
+    cx<R> v = g[e];
+    R d = (i == j) ? R(1) : R(0);
+    pm[e] = mkc<R>((R)1.5 * d - (R)0.5 * v.x, (R)(-0.5) * v.y);
+    qm[e] = mkc<R>((R)0.5 * d + (R)0.5 * v.x, (R)0.5 * v.y);
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launchers
@@ -462,10 +483,11 @@ cudaError_t build_phi(cudaStream_t st, int dm, const cx<R>* ct, const cx<R>* gj,
   build_phi_kernel<R><<<nblocks(n * n), 256, 0, st>>>(dm, ct, gj, phi);
   return cudaGetLastError();
 }
-cudaError_t bond_select(cudaStream_t st, int n, const double* lam, double htol, int chi,
-                        StepScalars* sc, DevStats* ds) {
+template <typename R>
+cudaError_t bond_select(cudaStream_t st, int n, const double* lam, const cx<R>* hm, long ldh,
+                        double htol, int chi, StepScalars* sc, DevStats* ds) {
   count_launch();
-  bond_select_kernel<<<1, 256, 0, st>>>(n, lam, htol, chi, sc, ds);
+  bond_select_kernel<R><<<1, 256, 0, st>>>(n, lam, hm, ldh, htol, chi, sc, ds);
   return cudaGetLastError();
 }
 template <typename R>
@@ -476,10 +498,11 @@ cudaError_t make_q(cudaStream_t st, int dm, int keep, int m_ops, const cx<R>* w,
   make_q_kernel<R><<<nblocks(total), 256, 0, st>>>(dm, keep, m_ops, w, e, sc, q);
   return cudaGetLastError();
 }
-cudaError_t kraus_select(cudaStream_t st, int n, const double* w, double kcut, int kmax,
-                         int use_ppt, double* f, StepScalars* sc, DevStats* ds) {
+template <typename R>
+cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, double kcut,
+                         int kmax, int use_ppt, double* f, StepScalars* sc, DevStats* ds) {
   count_launch();
-  kraus_select_kernel<<<1, 32, 0, st>>>(n, w, kcut, kmax, use_ppt, f, sc, ds);
+  kraus_select_kernel<R><<<1, 32, 0, st>>>(n, w, wm, kcut, kmax, use_ppt, f, sc, ds);
   return cudaGetLastError();
 }
 template <typename R>
@@ -507,6 +530,13 @@ cudaError_t sample_pick(cudaStream_t st, int n_samples, int dr, const cx<R>* ev,
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<R>* qm) {
+  count_launch();
+  polar_factors_kernel<R><<<nblocks((long)n * n), 256, 0, st>>>(n, g, pm, qm);
+  return cudaGetLastError();
+}
+
 #define INST(R)                                                                               \
   template cudaError_t swap12<cx<R>>(cudaStream_t, long, long, long, long, const cx<R>*,     \
                                      cx<R>*);                                               \
@@ -525,6 +555,11 @@ cudaError_t sample_pick(cudaStream_t st, int n_samples, int dr, const cx<R>* ev,
                                    const double*, cx<R>*);                                  \
   template cudaError_t energy_mix<R>(cudaStream_t, int, int, const cx<R>*, long, cx<R>*,    \
                                      long, double, double, double);                         \
+  template cudaError_t bond_select<R>(cudaStream_t, int, const double*, const cx<R>*, long,  \
+                                      double, int, StepScalars*, DevStats*);                 \
+  template cudaError_t kraus_select<R>(cudaStream_t, int, const double*, const cx<R>*, double, \
+                                       int, int, double*, StepScalars*, DevStats*);          \
+  template cudaError_t polar_factors<R>(cudaStream_t, int, const cx<R>*, cx<R>*, cx<R>*);   \
   template cudaError_t sample_pick<R>(cudaStream_t, int, int, const cx<R>*, const cx<R>*,   \
                                       uint64_t, int, int, int, cx<R>*, uint8_t*, double*, int);
 INST(double)

@@ -21,13 +21,17 @@ cudaError_t gram_factor(cudaStream_t st, int n, const cx<R>* v, const R* rs, con
                         cx<R>* rmat, cx<R>* vs, cx<R>* vr);
 template <typename R>
 cudaError_t build_phi(cudaStream_t st, int dm, const cx<R>* ct, const cx<R>* gj, cx<R>* phi);
-cudaError_t bond_select(cudaStream_t st, int n, const double* lam, double htol, int chi,
-                        StepScalars* sc, DevStats* ds);
+template <typename R>
+cudaError_t bond_select(cudaStream_t st, int n, const double* lam, const cx<R>* hm, long ldh,
+                        double htol, int chi, StepScalars* sc, DevStats* ds);
 template <typename R>
 cudaError_t make_q(cudaStream_t st, int dm, int keep, int m_ops, const cx<R>* w, const cx<R>* e,
                    const StepScalars* sc, cx<R>* q);
-cudaError_t kraus_select(cudaStream_t st, int n, const double* w, double kcut, int kmax,
-                         int use_ppt, double* f, StepScalars* sc, DevStats* ds);
+template <typename R>
+cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<R>* qm);
+template <typename R>
+cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, double kcut,
+                         int kmax, int use_ppt, double* f, StepScalars* sc, DevStats* ds);
 template <typename R>
 cudaError_t scale_vk(cudaStream_t st, int n, int kk, const cx<R>* v, long ldv, const double* f,
                      cx<R>* out);
