@@ -218,6 +218,31 @@ int mpdo_kernel_cgemm(int prec, int opa, int opb, int m, int n, int k, const voi
  * in *sweeps (host). */
 int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, void* stream);
 
+/* MLP surrogate (no counterpart in the paper; the workload's learned part).  A fully
+ * connected network with tanh hidden layers and a linear output maps a circuit description
+ * (chain length, noise rates, QAOA angles; scaled by the caller) to (energy per site,
+ * success probability).  Trained on the GPU on samples the MPDO engine produced; its input
+ * gradient proposes angles that the engine then re-scores.  FP32 parameters and
+ * arithmetic.  Parameters are one flat array W_0 b_0 W_1 b_1 ... with W_l stored
+ * [fan_in][fan_out] row-major.  x, t, y, gx are device arrays [batch][width], row-major;
+ * batch <= max_batch.  stream NULL = the network owns a non-blocking stream.
+ *   mpdo_mlp_loss_grad: forward, mean-squared loss (host *loss), backward into the
+ *     network's gradient buffer (copied to grad_host when not NULL, n_params floats)
+ *   mpdo_mlp_adam_step: one Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) with the last
+ *     gradient
+ *   mpdo_mlp_input_grad: gx = d(sum_j wout_j y_j)/dx, wout host [n_out] */
+typedef struct mpdo_mlp_s* mpdo_mlp;
+int mpdo_mlp_create(int n_layers, const int* widths, int max_batch, void* stream, mpdo_mlp* out);
+long long mpdo_mlp_n_params(mpdo_mlp m);
+int mpdo_mlp_set_params(mpdo_mlp m, const float* host_params);
+int mpdo_mlp_get_params(mpdo_mlp m, float* host_params);
+int mpdo_mlp_forward(mpdo_mlp m, int batch, const float* x, float* y);
+int mpdo_mlp_loss_grad(mpdo_mlp m, int batch, const float* x, const float* t, float* loss,
+                       float* grad_host);
+int mpdo_mlp_adam_step(mpdo_mlp m, float lr);
+int mpdo_mlp_input_grad(mpdo_mlp m, int batch, const float* x, const float* wout_host, float* gx);
+int mpdo_mlp_destroy(mpdo_mlp m);
+
 /* Allocation-free variant of mpdo_kernel_heig.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- processes where every
  * byte of device memory is owned by an outside allocator or budget (a framework's caching

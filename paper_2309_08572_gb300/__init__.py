@@ -88,6 +88,15 @@ def _load():
         "mpdo_kernel_launches": (C.c_longlong, []),
         "mpdo_profile": (I, [VP, I]),
         "mpdo_profile_read": (I, [VP, I, P(D), P(C.c_longlong), P(D)]),
+        "mpdo_mlp_create": (I, [I, P(I), I, VP, P(VP)]),
+        "mpdo_mlp_n_params": (C.c_longlong, [VP]),
+        "mpdo_mlp_set_params": (I, [VP, P(C.c_float)]),
+        "mpdo_mlp_get_params": (I, [VP, P(C.c_float)]),
+        "mpdo_mlp_forward": (I, [VP, I, VP, VP]),
+        "mpdo_mlp_loss_grad": (I, [VP, I, VP, VP, P(C.c_float), P(C.c_float)]),
+        "mpdo_mlp_adam_step": (I, [VP, C.c_float]),
+        "mpdo_mlp_input_grad": (I, [VP, I, VP, P(C.c_float), VP]),
+        "mpdo_mlp_destroy": (I, [VP]),
         "mpdo_kernel_cgemm": (I, [I, I, I, I, I, I, VP, C.c_long, C.c_long, VP, C.c_long,
                                   C.c_long, VP, C.c_long, C.c_long, I, VP]),
         "mpdo_kernel_heig": (I, [I, I, VP, VP, P(D), P(I), VP]),
@@ -335,6 +344,81 @@ def batch_run(pool: Sequence["Mpdo"], circuits: Sequence[dict]) -> np.ndarray:
         bad = [(i, int(x)) for i, x in enumerate(status) if x]
         msg = LIB.mpdo_last_error(None)
         raise MpdoError(rc, f"{msg.decode() if msg else ''}; failed circuits {bad[:8]}")
+    return out
+
+
+class Mlp:
+    """MLP surrogate on the GPU (tanh hidden layers, linear output), FP32."""
+
+    def __init__(self, widths: Sequence[int], max_batch: int, stream=None):
+        """stream: CUDA stream for the network's kernels; default torch's current stream,
+        so device inputs written by torch are ordered before the network reads them."""
+        arr = (C.c_int * len(widths))(*widths)
+        self._h = C.c_void_p(None)
+        st = _current_stream() if stream is None else C.c_void_p(stream)
+        _check(LIB.mpdo_mlp_create(len(widths) - 1, arr, max_batch, st, C.byref(self._h)))
+        self.widths = list(widths)
+        self.n_params = int(LIB.mpdo_mlp_n_params(self._h))
+
+    def close(self):
+        if self._h:
+            LIB.mpdo_mlp_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _fptr(a):
+        return a.ctypes.data_as(C.POINTER(C.c_float))
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.n_params
+        _check(LIB.mpdo_mlp_set_params(self._h, self._fptr(flat)))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(LIB.mpdo_mlp_get_params(self._h, self._fptr(out)))
+        return out
+
+    def forward(self, x, y):
+        _check(LIB.mpdo_mlp_forward(self._h, x.shape[0], C.c_void_p(x.data_ptr()),
+                                    C.c_void_p(y.data_ptr())))
+
+    def loss_grad(self, x, t, want_grad: bool = False):
+        loss = C.c_float(0)
+        g = np.zeros(self.n_params, dtype=np.float32) if want_grad else None
+        _check(LIB.mpdo_mlp_loss_grad(self._h, x.shape[0], C.c_void_p(x.data_ptr()),
+                                      C.c_void_p(t.data_ptr()), C.byref(loss),
+                                      None if g is None else self._fptr(g)))
+        return loss.value, g
+
+    def adam_step(self, lr: float):
+        _check(LIB.mpdo_mlp_adam_step(self._h, lr))
+
+    def input_grad(self, x, wout, gx):
+        w = np.ascontiguousarray(wout, dtype=np.float32)
+        _check(LIB.mpdo_mlp_input_grad(self._h, x.shape[0], C.c_void_p(x.data_ptr()),
+                                       self._fptr(w), C.c_void_p(gx.data_ptr())))
+
+
+def mlp_flat(params) -> np.ndarray:
+    """[(W_l, b_l)] -> the flat parameter layout of the library."""
+    return np.concatenate([np.concatenate([w.reshape(-1), b.reshape(-1)]) for w, b in params])
+
+
+def mlp_unflat(flat, widths):
+    out, off = [], 0
+    for a, b in zip(widths[:-1], widths[1:]):
+        w = flat[off: off + a * b].reshape(a, b)
+        off += a * b
+        bb = flat[off: off + b]
+        off += b
+        out.append((w, bb))
     return out
 
 

@@ -320,16 +320,31 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   const int KM = M * kj;
   const long colsB = (long)keep * 3 * dr;
   PO(swap12<T>(st, 1, (long)keep * 3, KM, dr, wWB, wBp));
-  CK(pgemm<R>(h, OP_N, OP_C, KM, KM, colsB, wBp, colsB, 0, wBp, colsB, 0, wWK, KM, 0, 1));
-  CK(peig<R>(h, KM, wWK, KM, wVk, KM, h->wWv));
-  // a9: cut + PPT (FP64 scalars)
-  PO(kraus_select<R>(st, KM, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
-  rc = read_scalars(h);
-  if (rc) return rc;
-  const int kk = h->hsc->kkeep;
-  // a10: apply the inner isometry with the PPT scales
-  PO(scale_vk<R>(st, KM, kk, wVk, KM, h->wF, wVks));
-  CK(pgemm<R>(h, OP_C, OP_N, kk, colsB, KM, wVks, kk, 0, wBp, colsB, 0, wCn, colsB, 0, 1));
+  int kk;
+  if (colsB < KM) {
+    // the inner Gram W = B B^+ has rank <= colsB: diagonalise the smaller dual B^+ B
+    const int nc = (int)colsB;
+    CK(pgemm<R>(h, OP_C, OP_N, nc, nc, KM, wBp, colsB, 0, wBp, colsB, 0, wWK, nc, 0, 1));
+    CK(peig<R>(h, nc, wWK, nc, wVk, nc, h->wWv));
+    // a9: cut + PPT (FP64 scalars); tr(B^+B) = tr(B B^+)
+    PO(kraus_select<R>(st, nc, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
+    rc = read_scalars(h);
+    if (rc) return rc;
+    kk = h->hsc->kkeep;
+    // a10: kept rows f_k sqrt(w_k) y_k^+
+    PO(dual_rows<R>(st, kk, nc, wVk, nc, h->wF, h->wWv, wCn));
+  } else {
+    CK(pgemm<R>(h, OP_N, OP_C, KM, KM, colsB, wBp, colsB, 0, wBp, colsB, 0, wWK, KM, 0, 1));
+    CK(peig<R>(h, KM, wWK, KM, wVk, KM, h->wWv));
+    // a9: cut + PPT (FP64 scalars)
+    PO(kraus_select<R>(st, KM, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
+    rc = read_scalars(h);
+    if (rc) return rc;
+    kk = h->hsc->kkeep;
+    // a10: apply the inner isometry with the PPT scales
+    PO(scale_vk<R>(st, KM, kk, wVk, KM, h->wF, wVks));
+    CK(pgemm<R>(h, OP_C, OP_N, kk, colsB, KM, wVks, kk, 0, wBp, colsB, 0, wCn, colsB, 0, 1));
+  }
   PO(swap12<T>(st, 1, kk, (long)keep * 3, dr, wCn, aj));
   h->bond[i + 1] = keep;
   h->kd[i + 1] = kk;

@@ -410,7 +410,9 @@ __global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
   __shared__ int s_nan;
   if (tid == 0) s_nan = 0;
   __syncthreads();
-  for (int c = tid; c < 128; c += nthr) {
+  int P = 2;
+  while (P < n) P <<= 1;                       // n <= 118 -> P <= 128
+  for (int c = tid; c < P; c += nthr) {
     double key = -INFINITY;
     if (c < n) {
       key = (double)A[(size_t)c * np + c].x;
@@ -420,9 +422,9 @@ __global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
     s_val[c] = c;
   }
   __syncthreads();
-  for (int k = 2; k <= 128; k <<= 1) {
+  for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int c = tid; c < 128; c += nthr) {
+      for (int c = tid; c < P; c += nthr) {
         int l = c ^ j;
         if (l > c) {
           bool desc = ((c & k) == 0);

@@ -429,6 +429,23 @@ __global__ void polar_factors_kernel(int n, const cx<R>* __restrict__ g, cx<R>* 
   }
 }
 
+// Inner-index truncation through the dual Gram W' = B^+B (used when B has fewer columns
+// than rows): with W' y_k = w_k y_k, the kept rows of the new centre are
+// f_k x_k^+ B = f_k sqrt(w_k) y_k^+  (x_k = B y_k / sqrt(w_k)), so no product with B is needed.
+template <typename R>
+__global__ void dual_rows_kernel(int kk, int cols, const cx<R>* __restrict__ y, long ldy,
+                                 const double* __restrict__ f, const double* __restrict__ w,
+                                 cx<R>* out) {
+  long total = (long)kk * cols;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    int k = (int)(e / cols), c = (int)(e % cols);
+    double wk = w[k] > 0 ? w[k] : 0.0;
+    R sc = (R)(f[k] * sqrt(wk));
+    out[e] = cscale(cconj(y[(long)c * ldy + k]), sc);
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launchers
@@ -537,6 +554,14 @@ cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t dual_rows(cudaStream_t st, int kk, int cols, const cx<R>* y, long ldy, const double* f,
+                      const double* w, cx<R>* out) {
+  count_launch();
+  dual_rows_kernel<R><<<nblocks((long)kk * cols), 256, 0, st>>>(kk, cols, y, ldy, f, w, out);
+  return cudaGetLastError();
+}
+
 #define INST(R)                                                                               \
   template cudaError_t swap12<cx<R>>(cudaStream_t, long, long, long, long, const cx<R>*,     \
                                      cx<R>*);                                               \
@@ -559,6 +584,8 @@ cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<
                                       double, int, StepScalars*, DevStats*);                 \
   template cudaError_t kraus_select<R>(cudaStream_t, int, const double*, const cx<R>*, double, \
                                        int, int, double*, StepScalars*, DevStats*);          \
+  template cudaError_t dual_rows<R>(cudaStream_t, int, int, const cx<R>*, long, const double*, \
+                                    const double*, cx<R>*);                                 \
   template cudaError_t polar_factors<R>(cudaStream_t, int, const cx<R>*, cx<R>*, cx<R>*);   \
   template cudaError_t sample_pick<R>(cudaStream_t, int, int, const cx<R>*, const cx<R>*,   \
                                       uint64_t, int, int, int, cx<R>*, uint8_t*, double*, int);

@@ -28,6 +28,9 @@ template <typename R>
 cudaError_t make_q(cudaStream_t st, int dm, int keep, int m_ops, const cx<R>* w, const cx<R>* e,
                    const StepScalars* sc, cx<R>* q);
 template <typename R>
+cudaError_t dual_rows(cudaStream_t st, int kk, int cols, const cx<R>* y, long ldy, const double* f,
+                      const double* w, cx<R>* out);
+template <typename R>
 cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<R>* qm);
 template <typename R>
 cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, double kcut,

@@ -173,3 +173,30 @@ def test_batch_executor_matches_oracle_fp64(lib):
             assert _rel(row[j], r[key]) < 1e-9, (c.n_sites, key, row[j], r[key])
     for m in pool:
         m.close()
+
+
+def test_batch512_sample_through_executor(lib):
+    """The batched workload (512 circuits, N ~ U{20..100}, chi in {32,64,128}, K=8,
+    p in {1,2}, log-uniform rates): 24 of its circuits run concurrently in complex64 on a
+    pool sized for the largest; the two shortest single-layer ones are checked against the
+    oracle, the rest for finite physical outputs (0 < p_succ <= trace <= 1)."""
+    circs = synth.batch512()[:24]
+    m_max = 25
+    pool = [lib.Mpdo(100, 128, 8, m_max=m_max, prec="c64", own_stream=True) for _ in range(8)]
+    descs = []
+    for c in circs:
+        dls = [pool[0].upload_layer(layer) for layer in lib.circuit_layers(c)]
+        descs.append(dict(n_sites=c.n_sites, chi_max=c.chi_max, k_max=c.k_max, layers=dls,
+                          J=c.J, hx=c.hx, b=c.bz))
+    out = lib.batch_run(pool, descs)
+    assert np.all(np.isfinite(out))
+    # complex64: tr(rho) carries the FP32 rounding of ~1e2 renormalisations (~1e-4)
+    assert np.all(out[:, 2] > 0) and np.all(out[:, 2] <= out[:, 3] + 1e-6)
+    assert np.all(out[:, 3] <= 1 + 2e-4)
+    order = sorted(range(len(circs)), key=lambda i: (circs[i].p, circs[i].n_sites))[:2]
+    for i in order:
+        _, r = _oracle(circs[i])
+        for j, key in enumerate(("e_raw", "e_succ", "p_succ", "trace")):
+            assert _rel(out[i][j], r[key]) < TOL["c64"], (i, key, out[i][j], r[key])
+    for m in pool:
+        m.close()
