@@ -45,7 +45,8 @@ enum {
 /* Arithmetic of the hot path.
  *  MPDO_FP64 : complex128 state, FP64 GEMMs and FP64 Jacobi eigensolves.
  *  MPDO_C64  : complex64 state, FP32 GEMMs (FP32 accumulation), FP32 Jacobi;
- *              cutoff, PPT and trace renormalisation in FP64 scalars.
+ *              cutoff, PPT and trace renormalisation in FP64 scalars.  With
+ *              mpdo_config.gram_fp64 = 1 the Grams and the small matrices are FP64.
  *  MPDO_TF32X3, MPDO_BF16X3 : as MPDO_C64 with the large contractions on the
  *              tensor cores in split precision (3 products per real product). */
 typedef enum { MPDO_FP64 = 0, MPDO_C64 = 1, MPDO_TF32X3 = 2, MPDO_BF16X3 = 3 } mpdo_prec;
@@ -63,6 +64,12 @@ typedef struct {
   double kraus_cutoff;  /* inner values with sqrt(w) <= kraus_cutoff*sqrt(w_max) dropped   */
   int use_ppt;          /* 1: purity-preserving inner truncation; 0: plain + trace renorm  */
   void* cuda_stream;    /* cudaStream_t to use; NULL = a non-blocking stream the handle owns */
+  int gram_fp64;        /* MPDO_C64 only.  1 = mixed precision: the Gram matrices (a2, a8)
+                           are formed from the FP32 tensors with FP64 products and sums, and
+                           everything derived from them (Jacobi eigenpairs, bond factors,
+                           Phi and H, the cuts, PPT) is FP64; site tensors and the large
+                           contractions stay FP32.  The numerical floor of the cuts drops
+                           from ~6e-7 to ~1e-13 of the largest weight.  Ignored otherwise. */
 } mpdo_config;
 
 /* One op of a layer.  kind 2: two-site channel on (site, site+1) with n_kraus Kraus

@@ -31,7 +31,8 @@ class MpdoError(RuntimeError):
 class Config(C.Structure):
     _fields_ = [("n_sites", C.c_int), ("d", C.c_int), ("chi_max", C.c_int), ("k_max", C.c_int),
                 ("m_max", C.c_int), ("prec", C.c_int), ("sv_cutoff", C.c_double),
-                ("kraus_cutoff", C.c_double), ("use_ppt", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("kraus_cutoff", C.c_double), ("use_ppt", C.c_int), ("cuda_stream", C.c_void_p),
+                ("gram_fp64", C.c_int)]
 
 
 class Op(C.Structure):
@@ -208,14 +209,14 @@ class Mpdo:
     def __init__(self, n_sites: int, chi_max: int, k_max: int, m_max: int = 25,
                  prec: str = "fp64", sv_cutoff: float = 0.0, kraus_cutoff: float = 0.0,
                  use_ppt: bool = True, init_vec: Optional[Sequence[complex]] = None,
-                 stream=None, own_stream: bool = False):
+                 stream=None, own_stream: bool = False, gram_fp64: bool = False):
         self.n = n_sites
         if own_stream:
             st = C.c_void_p(None)            # the library creates a non-blocking stream
         else:
             st = _current_stream() if stream is None else C.c_void_p(stream)
         cfg = Config(n_sites, 3, chi_max, k_max, m_max, PREC[prec], sv_cutoff, kraus_cutoff,
-                     int(use_ppt), st)
+                     int(use_ppt), st, int(gram_fp64))
         self._h = C.c_void_p(None)
         v = None if init_vec is None else np.ascontiguousarray(np.asarray(init_vec, complex)).view(float)
         rc = LIB.mpdo_create(C.byref(cfg), None if v is None else _dptr(v), C.byref(self._h))

@@ -26,6 +26,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mpdo.h"
@@ -86,8 +87,7 @@ struct mpdo_ctx {
   std::vector<int> kd;    // storage coords, size n
   size_t elt = 16;        // bytes per complex
   size_t site_cap = 0;    // complex elements per site
-  void* sites[2] = {nullptr, nullptr};
-  int cur = 0;
+  void* sites = nullptr;   // one arena: site s at s * site_cap elements
   // workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -98,6 +98,10 @@ struct mpdo_ctx {
   double *wSig, *wLam, *wWv, *wF;
   EigWork<double> eig64;
   EigWork<float> eig32;
+  // FP32 site tensors with FP64 Gram matrices and small-matrix arithmetic (cfg.gram_fp64)
+  bool mixed = false;
+  size_t eltm = 16;          // bytes per complex of the Gram-derived matrices
+  void* wVgenS = nullptr;    // FP32 copy of Vgen (mixed only)
   StepScalars* dsc = nullptr;
   StepScalars* hsc = nullptr;  // pinned
   DevStats* dstats = nullptr;
@@ -120,9 +124,7 @@ struct mpdo_ctx {
   int* prof_counts = nullptr;   // pinned: active pair-rounds of profiled eigensolves
   int prof_nslots = 0, prof_slot = 0;
 
-  void* site(int buf, int s) const {
-    return static_cast<char*>(sites[buf]) + (size_t)s * site_cap * elt;
-  }
+  void* site(int s) const { return static_cast<char*>(sites) + (size_t)s * site_cap * elt; }
 };
 
 namespace {
@@ -219,7 +221,8 @@ cudaError_t pgemm(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<R
 template <typename R>
 cudaError_t peig(mpdo_ctx* h, int n, const cx<R>* a, long lda, cx<R>* v, long ldv, double* w) {
   int pi = prof_begin(h, 1);
-  cudaError_t e = heig<R>(h->st, n, a, lda, v, ldv, w, eigw<R>(h), h->max_sweeps);
+  const int sweeps = std::is_same<R, double>::value ? 30 : 20;
+  cudaError_t e = heig<R>(h->st, n, a, lda, v, ldv, w, eigw<R>(h), sweeps);
   if (pi >= 0 && e == cudaSuccess && h->prof_slot < h->prof_nslots) {
     // executed flops: 8 real flops per complex MAC, 3*16*16*np MACs per active pair-round
     int slot = h->prof_slot++;
@@ -232,90 +235,112 @@ cudaError_t peig(mpdo_ctx* h, int n, const cx<R>* a, long lda, cx<R>* v, long ld
   return e;
 }
 
+// Gram-type product with storage-precision inputs and small-matrix-precision output:
+// FP32 inputs with FP64 products and sums when RS = float and RM = double.
+template <typename RS, typename RM>
+cudaError_t pgram(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<RS>* A, long lda,
+                  const cx<RS>* B, long ldb, cx<RM>* C, long ldc) {
+  if constexpr (std::is_same<RS, RM>::value) {
+    return pgemm<RS>(h, opa, opb, m, n, k, A, lda, 0, B, ldb, 0, C, ldc, 0, 1);
+  } else {
+    int pi = prof_begin(h, 0);
+    cudaError_t e = cgemm_wide(h->st, opa, opb, m, n, k, A, lda, 0, B, ldb, 0, C, ldc, 0, 1);
+    prof_end(h, 0, pi, 8.0 * m * n * (double)k);
+    return e;
+  }
+}
+
 // ------------------------------------------------------------------ the update
-template <typename R>
+// RS: precision of the site tensors and of the large contractions (a4, a7, a10);
+// RM: precision of the Gram matrices and everything derived from them (a2 outputs, a3,
+// a5, a6, a8, a9 and the factors that feed a7 and a10).
+template <typename RS, typename RM>
 int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int kmax,
               int use_ppt) {
-  using T = cx<R>;
+  using T = cx<RS>;
+  using TM = cx<RM>;
   cudaStream_t st = h->st;
   const int dl = h->bond[i], ki = h->kd[i], dm = h->bond[i + 1], kj = h->kd[i + 1],
             dr = h->bond[i + 2];
   const int M = op.m;
   const int n3 = 3 * dm, n9 = 9 * dm;
-  T* ai = static_cast<T*>(h->site(h->cur, i));
-  T* aj = static_cast<T*>(h->site(h->cur, i + 1));
+  T* ai = static_cast<T*>(h->site(i));
+  T* aj = static_cast<T*>(h->site(i + 1));
   const T* E = static_cast<const T*>(mirrored ? op.em : op.e);
-  const T* Ct = static_cast<const T*>(mirrored ? op.ctm : op.ct);
+  const TM* Ct = static_cast<const TM*>(mirrored ? op.ctm : op.ct);
   T* wM = static_cast<T*>(h->wM);
-  T* wGi = static_cast<T*>(h->wGi);
-  T* wGj = static_cast<T*>(h->wGj);
-  T* wVg = static_cast<T*>(h->wVg);
-  T* wR = static_cast<T*>(h->wR);
-  T* wVs = static_cast<T*>(h->wVs);
-  T* wVr = static_cast<T*>(h->wVr);
-  T* wPhi = static_cast<T*>(h->wPhi);
-  T* wX = static_cast<T*>(h->wX);
-  T* wH = static_cast<T*>(h->wH);
-  T* wU = static_cast<T*>(h->wU);
-  T* wVgen = static_cast<T*>(h->wVgen);
+  TM* wGi = static_cast<TM*>(h->wGi);
+  TM* wGj = static_cast<TM*>(h->wGj);
+  TM* wVg = static_cast<TM*>(h->wVg);
+  TM* wR = static_cast<TM*>(h->wR);
+  TM* wVs = static_cast<TM*>(h->wVs);
+  TM* wVr = static_cast<TM*>(h->wVr);
+  TM* wPhi = static_cast<TM*>(h->wPhi);
+  TM* wX = static_cast<TM*>(h->wX);
+  TM* wH = static_cast<TM*>(h->wH);
+  TM* wU = static_cast<TM*>(h->wU);
+  TM* wVgen = static_cast<TM*>(h->wVgen);
+  T* wVgenS = static_cast<T*>(h->wVgenS ? h->wVgenS : h->wVgen);
   T* wW = static_cast<T*>(h->wW);
   T* wTmp = static_cast<T*>(h->wTmp);
   T* wQ = static_cast<T*>(h->wQ);
   T* wWB = static_cast<T*>(h->wWB);
   T* wBp = static_cast<T*>(h->wBp);
-  T* wWK = static_cast<T*>(h->wWK);
-  T* wVk = static_cast<T*>(h->wVk);
+  TM* wWK = static_cast<TM*>(h->wWK);
+  TM* wVk = static_cast<TM*>(h->wVk);
   T* wVks = static_cast<T*>(h->wVks);
   T* wCn = static_cast<T*>(h->wCn);
-  R* wRs = static_cast<R*>(h->wRs);
-  R* wIrs = static_cast<R*>(h->wIrs);
+  RM* wRs = static_cast<RM*>(h->wRs);
+  RM* wIrs = static_cast<RM*>(h->wIrs);
 
   // a2: Gram matrices of the two site tensors
   PO(swap12<T>(st, dl, 3, ki, dm, ai, wM));
-  CK(pgemm<R>(h, OP_C, OP_N, n3, n3, dl * ki, wM, n3, 0, wM, n3, 0, wGi, n3, 0, 1));
-  CK(pgemm<R>(h, OP_N, OP_C, n3, n3, kj * dr, aj, (long)kj * dr, 0, aj, (long)kj * dr, 0, wGj,
-              n3, 0, 1));
+  CK((pgram<RS, RM>(h, OP_C, OP_N, n3, n3, dl * ki, wM, n3, wM, n3, wGi, n3)));
+  CK((pgram<RS, RM>(h, OP_N, OP_C, n3, n3, kj * dr, aj, (long)kj * dr, aj, (long)kj * dr, wGj,
+                    n3)));
   // a3: left factor from the eigendecomposition of G_i (numerical rank by gtol)
-  CK(peig<R>(h, n3, wGi, n3, wVg, n3, h->wSig));
-  PO(gram_mask<R>(st, n3, h->wSig, h->gtol, wRs, wIrs, h->dsc));
-  PO(gram_factor<R>(st, n3, wVg, wRs, wIrs, wR, wVs, wVr));
+  CK(peig<RM>(h, n3, wGi, n3, wVg, n3, h->wSig));
+  PO(gram_mask<RM>(st, n3, h->wSig, h->gtol, wRs, wIrs, h->dsc));
+  PO(gram_factor<RM>(st, n3, wVg, wRs, wIrs, wR, wVs, wVr));
   // a4/a5: Phi from the channel and G_j, then H = (I x R) Phi (I x R)^+
-  PO(build_phi<R>(st, dm, Ct, wGj, wPhi));
-  CK(pgemm<R>(h, OP_N, OP_N, n3, n9, n3, wR, n3, 0, wPhi, n9, (long)n3 * n9, wX, n9,
-              (long)n3 * n9, 3));
-  CK(pgemm<R>(h, OP_N, OP_C, n9, n3, n3, wX, n9, n3, wR, n3, 0, wH, n9, n3, 3));
+  PO(build_phi<RM>(st, dm, Ct, wGj, wPhi));
+  CK(pgemm<RM>(h, OP_N, OP_N, n3, n9, n3, wR, n3, 0, wPhi, n9, (long)n3 * n9, wX, n9,
+               (long)n3 * n9, 3));
+  CK(pgemm<RM>(h, OP_N, OP_C, n9, n3, n3, wX, n9, n3, wR, n3, 0, wH, n9, n3, 3));
   // a6: bond eigenpairs and cut
-  CK(peig<R>(h, n9, wH, n9, wU, n9, h->wLam));
-  PO(bond_select<R>(st, n9, h->wLam, wH, n9, h->htol, chi, h->dsc, h->dstats));
+  CK(peig<RM>(h, n9, wH, n9, wU, n9, h->wLam));
+  PO(bond_select<RM>(st, n9, h->wLam, wH, n9, h->htol, chi, h->dsc, h->dstats));
   int rc = read_scalars(h);
   if (rc) return rc;
   const int keep = h->hsc->keep;
-  // a7: split.  Vgen = (I x V sigma^-1/2) U_keep, W = (I x V sigma^1/2) U_keep
-  CK(pgemm<R>(h, OP_N, OP_N, n3, keep, n3, wVs, n3, 0, wU, n9, (long)n3 * n9, wVgen, keep,
-              (long)n3 * keep, 3));
-  CK(pgemm<R>(h, OP_N, OP_N, n3, keep, n3, wVr, n3, 0, wU, n9, (long)n3 * n9, wW, keep,
-              (long)n3 * keep, 3));
-  CK(pgemm<R>(h, OP_N, OP_N, dl * ki, keep, n3, wM, n3, 0, wVgen, keep, (long)n3 * keep, wTmp,
-              3L * keep, keep, 3));
-  // The left factor (M_i x I)(I x V sigma^-1/2) u is an isometry only up to the error of
-  // the small-sigma eigenvectors of G_i, amplified by sigma^-1/2.  One Newton-Schulz polar
-  // step (Higham) restores it: A <- A (3I - A^+A)/2 and, to keep theta' = A B, the centre's
-  // factor W <- W (I + A^+A)/2.
+  // a7: split.  Vgen = (I x V sigma^-1/2) U_keep
+  CK(pgemm<RM>(h, OP_N, OP_N, n3, keep, n3, wVs, n3, 0, wU, n9, (long)n3 * n9, wVgen, keep,
+               (long)n3 * keep, 3));
+  if constexpr (!std::is_same<RS, RM>::value)
+    CK((convert<RM, RS>(st, n9, keep, wVgen, keep, wVgenS, keep)));
+  CK(pgemm<RS>(h, OP_N, OP_N, dl * ki, keep, n3, wM, n3, 0, wVgenS, keep, (long)n3 * keep, wTmp,
+               3L * keep, keep, 3));
+  // The left factor A = (M_i x I)(I x V sigma^-1/2) U_keep is an isometry only up to the
+  // error of the small-sigma eigenvectors of G_i, amplified by sigma^-1/2.  One
+  // Newton-Schulz polar step (Higham) restores it: A <- A (3I - A^+A)/2, written to wWB.
+  // The centre factor is then the projection of the two-site block onto the kept left
+  // vectors, W_s' = M_i^+ A_s' (= (I x V sigma^1/2) U_keep when the eigenpairs are exact),
+  // so that theta' = A A^+ theta holds to rounding whatever the eigenvector error.
   {
     T* wGa = static_cast<T*>(h->wGa);
     T* wPol = static_cast<T*>(h->wPol);
     T* wQol = static_cast<T*>(h->wQol);
     const int rows = dl * ki * 3;
-    CK(pgemm<R>(h, OP_C, OP_N, keep, keep, rows, wTmp, keep, 0, wTmp, keep, 0, wGa, keep, 0, 1));
-    PO(polar_factors<R>(st, keep, wGa, wPol, wQol));
-    CK(pgemm<R>(h, OP_N, OP_N, rows, keep, keep, wTmp, keep, 0, wPol, keep, 0, wM, keep, 0, 1));
-    CK(pgemm<R>(h, OP_N, OP_N, n9, keep, keep, wW, keep, 0, wQol, keep, 0, wVgen, keep, 0, 1));
-    std::swap(wW, wVgen);   // W now holds the corrected factor
+    CK(pgemm<RS>(h, OP_C, OP_N, keep, keep, rows, wTmp, keep, 0, wTmp, keep, 0, wGa, keep, 0, 1));
+    PO(polar_factors<RS>(st, keep, wGa, wPol, wQol));
+    CK(pgemm<RS>(h, OP_N, OP_N, rows, keep, keep, wTmp, keep, 0, wPol, keep, 0, wWB, keep, 0, 1));
+    CK(pgemm<RS>(h, OP_C, OP_N, n3, keep, dl * ki, wM, n3, 0, wWB, 3L * keep, keep, wW, keep,
+                 (long)n3 * keep, 3));
   }
-  PO(swap12<T>(st, dl, ki, 3, keep, wM, ai));
-  PO(make_q<R>(st, dm, keep, M, wW, E, h->dsc, wQ));
-  CK(pgemm<R>(h, OP_N, OP_N, keep * 3 * M, kj * dr, n3, wQ, n3, 0, aj, (long)kj * dr, 0, wWB,
-              (long)kj * dr, 0, 1));
+  PO(swap12<T>(st, dl, ki, 3, keep, wWB, ai));
+  PO(make_q<RS>(st, dm, keep, M, wW, E, h->dsc, wQ));
+  CK(pgemm<RS>(h, OP_N, OP_N, keep * 3 * M, kj * dr, n3, wQ, n3, 0, aj, (long)kj * dr, 0, wWB,
+               (long)kj * dr, 0, 1));
   // a8: inner-index Gram of the new centre and its eigenpairs
   const int KM = M * kj;
   const long colsB = (long)keep * 3 * dr;
@@ -324,26 +349,26 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   if (colsB < KM) {
     // the inner Gram W = B B^+ has rank <= colsB: diagonalise the smaller dual B^+ B
     const int nc = (int)colsB;
-    CK(pgemm<R>(h, OP_C, OP_N, nc, nc, KM, wBp, colsB, 0, wBp, colsB, 0, wWK, nc, 0, 1));
-    CK(peig<R>(h, nc, wWK, nc, wVk, nc, h->wWv));
+    CK((pgram<RS, RM>(h, OP_C, OP_N, nc, nc, KM, wBp, colsB, wBp, colsB, wWK, nc)));
+    CK(peig<RM>(h, nc, wWK, nc, wVk, nc, h->wWv));
     // a9: cut + PPT (FP64 scalars); tr(B^+B) = tr(B B^+)
-    PO(kraus_select<R>(st, nc, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
+    PO(kraus_select<RM>(st, nc, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
     rc = read_scalars(h);
     if (rc) return rc;
     kk = h->hsc->kkeep;
     // a10: kept rows f_k sqrt(w_k) y_k^+
-    PO(dual_rows<R>(st, kk, nc, wVk, nc, h->wF, h->wWv, wCn));
+    PO((dual_rows<RM, RS>(st, kk, nc, wVk, nc, h->wF, h->wWv, wCn)));
   } else {
-    CK(pgemm<R>(h, OP_N, OP_C, KM, KM, colsB, wBp, colsB, 0, wBp, colsB, 0, wWK, KM, 0, 1));
-    CK(peig<R>(h, KM, wWK, KM, wVk, KM, h->wWv));
+    CK((pgram<RS, RM>(h, OP_N, OP_C, KM, KM, colsB, wBp, colsB, wBp, colsB, wWK, KM)));
+    CK(peig<RM>(h, KM, wWK, KM, wVk, KM, h->wWv));
     // a9: cut + PPT (FP64 scalars)
-    PO(kraus_select<R>(st, KM, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
+    PO(kraus_select<RM>(st, KM, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
     rc = read_scalars(h);
     if (rc) return rc;
     kk = h->hsc->kkeep;
     // a10: apply the inner isometry with the PPT scales
-    PO(scale_vk<R>(st, KM, kk, wVk, KM, h->wF, wVks));
-    CK(pgemm<R>(h, OP_C, OP_N, kk, colsB, KM, wVks, kk, 0, wBp, colsB, 0, wCn, colsB, 0, 1));
+    PO((scale_vk<RM, RS>(st, KM, kk, wVk, KM, h->wF, wVks)));
+    CK(pgemm<RS>(h, OP_C, OP_N, kk, colsB, KM, wVks, kk, 0, wBp, colsB, 0, wCn, colsB, 0, 1));
   }
   PO(swap12<T>(st, 1, kk, (long)keep * 3, dr, wCn, aj));
   h->bond[i + 1] = keep;
@@ -351,31 +376,40 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   return MPDO_OK;
 }
 
+// Mirror the chain in place: site s <-> site N-1-s with [l][s][k][r] -> [r][s][k][l].
+// Each pair goes through the two B_j work buffers (each at least one site's capacity).
 template <typename R>
 int reverse_chain(mpdo_ctx* h) {
   using T = cx<R>;
-  int other = 1 - h->cur;
-  for (int s = 0; s < h->n; ++s) {
+  T* t1 = static_cast<T*>(h->wWB);
+  T* t2 = static_cast<T*>(h->wBp);
+  const size_t elt = sizeof(T);
+  for (int s = 0; s <= (h->n - 1) / 2; ++s) {
     int t = h->n - 1 - s;
+    size_t ns = (size_t)h->bond[s] * 3 * h->kd[s] * h->bond[s + 1];
+    size_t nt = (size_t)h->bond[t] * 3 * h->kd[t] * h->bond[t + 1];
     PO(reverse_site<T>(h->st, h->bond[s], 3, h->kd[s], h->bond[s + 1],
-                       static_cast<const T*>(h->site(h->cur, s)),
-                       static_cast<T*>(h->site(other, t))));
+                       static_cast<const T*>(h->site(s)), t1));
+    if (t != s)
+      PO(reverse_site<T>(h->st, h->bond[t], 3, h->kd[t], h->bond[t + 1],
+                         static_cast<const T*>(h->site(t)), t2));
+    CK(cudaMemcpyAsync(h->site(t), t1, ns * elt, cudaMemcpyDeviceToDevice, h->st));
+    if (t != s) CK(cudaMemcpyAsync(h->site(s), t2, nt * elt, cudaMemcpyDeviceToDevice, h->st));
   }
-  h->cur = other;
   std::reverse(h->bond.begin(), h->bond.end());
   std::reverse(h->kd.begin(), h->kd.end());
   h->rev = !h->rev;
   return MPDO_OK;
 }
 
-template <typename R>
+template <typename R, typename RM>
 int apply_ops(mpdo_ctx* h, const std::vector<DevOp>& ops, int chi, int kmax, int use_ppt) {
   for (const DevOp& op : ops) {
     if (op.kind == 1) {
       int s = h->rev ? h->n - 1 - op.site : op.site;
       int rc = MPDO_OK;
       PO(one_site<R>(h->st, h->bond[s], h->kd[s], h->bond[s + 1],
-                     static_cast<const cx<R>*>(op.u), static_cast<cx<R>*>(h->site(h->cur, s))));
+                     static_cast<const cx<R>*>(op.u), static_cast<cx<R>*>(h->site(s))));
       (void)rc;
       continue;
     }
@@ -393,7 +427,7 @@ int apply_ops(mpdo_ctx* h, const std::vector<DevOp>& ops, int chi, int kmax, int
       if (rc) return rc;
     }
     int is = h->rev ? h->n - 2 - i : i;
-    int rc = update_lr<R>(h, is, op, h->rev, chi, kmax, use_ppt);
+    int rc = update_lr<R, RM>(h, is, op, h->rev, chi, kmax, use_ppt);
     if (rc) return rc;
     h->centre = ltr ? i + 1 : i;
   }
@@ -449,7 +483,10 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
                                          " outside 1..m_max=" + std::to_string(h->mmax));
       if ((size_t)op.n_kraus * h->kmax > 1024)
         return fail(h, MPDO_ERR_ARG, "n_kraus*k_max exceeds 1024");
-      total += (size_t)(2 * op.n_kraus * 81 + 2 * 729) * elt;
+      // same layout as the copy loop below: each part starts on a 16-byte boundary
+      const size_t sizes[4] = {(size_t)op.n_kraus * 81 * elt, (size_t)op.n_kraus * 81 * elt,
+                               729 * h->eltm, 729 * h->eltm};
+      for (size_t sz : sizes) total = ((total + 15) & ~(size_t)15) + sz;
     } else if (op.kind == 1) {
       if (op.site < 0 || op.site > h->n - 1) return fail(h, MPDO_ERR_ARG, "one-site op site");
       if (op.n_kraus != 1) return fail(h, MPDO_ERR_ARG, "one-site op needs n_kraus == 1");
@@ -477,14 +514,19 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
         return fail(h, MPDO_ERR_NUMERIC, "non-finite value in op " + std::to_string(k));
       e[a] = zc(re, im);
     }
-    std::vector<std::pair<const zc*, int>> parts;
+    // (data, count, double precision?): Kraus operators in the storage precision, the
+    // channel partial traces (inputs of Phi) in the Gram precision
+    struct Part { const zc* p; int n; bool dbl; };
+    std::vector<Part> parts;
     std::vector<zc> em, ct(729), ctm(729);
     if (op.kind == 2) {
       em.resize(nval);
       mirror_ops(e.data(), op.n_kraus, em.data());
       channel_c(e.data(), op.n_kraus, ct.data());
       channel_c(em.data(), op.n_kraus, ctm.data());
-      parts = {{e.data(), nval}, {em.data(), nval}, {ct.data(), 729}, {ctm.data(), 729}};
+      const bool gd = h->eltm == 16;
+      parts = {{e.data(), nval, h->dbl}, {em.data(), nval, h->dbl}, {ct.data(), 729, gd},
+               {ctm.data(), 729, gd}};
     } else {
       // one-site ops must be unitary to keep the canonical gauge
       double dev = 0;
@@ -495,14 +537,15 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
           dev = std::max(dev, std::abs(acc - (a == b ? 1.0 : 0.0)));
         }
       if (dev > 1e-10) return fail(h, MPDO_ERR_ARG, "one-site op is not unitary");
-      parts = {{e.data(), nval}};
+      parts = {{e.data(), nval, h->dbl}};
     }
     size_t starts[4];
     for (size_t p = 0; p < parts.size(); ++p) {
+      off = (off + 15) & ~(size_t)15;
       starts[p] = off;
-      for (int a = 0; a < parts[p].second; ++a) {
-        zc v = parts[p].first[a];
-        if (h->dbl) {
+      for (int a = 0; a < parts[p].n; ++a) {
+        zc v = parts[p].p[a];
+        if (parts[p].dbl) {
           double* dst = reinterpret_cast<double*>(host.data() + off) + 2 * a;
           dst[0] = v.real(); dst[1] = v.imag();
         } else {
@@ -510,7 +553,7 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
           dst[0] = (float)v.real(); dst[1] = (float)v.imag();
         }
       }
-      off += (size_t)parts[p].second * elt;
+      off += (size_t)parts[p].n * (parts[p].dbl ? 16 : 8);
     }
     off = (off + 255) & ~(size_t)255;
     // pointers are filled after the device buffer exists (store offsets for now)
@@ -580,8 +623,9 @@ int run_ops(mpdo_ctx* h, const std::vector<DevOp>& ops, mpdo_trunc_stats* stats,
             int kmax, int use_ppt) {
   int rc = reset_stats(h);
   if (rc) return rc;
-  rc = h->dbl ? apply_ops<double>(h, ops, chi, kmax, use_ppt)
-              : apply_ops<float>(h, ops, chi, kmax, use_ppt);
+  rc = h->dbl     ? apply_ops<double, double>(h, ops, chi, kmax, use_ppt)
+       : h->mixed ? apply_ops<float, double>(h, ops, chi, kmax, use_ppt)
+                  : apply_ops<float, float>(h, ops, chi, kmax, use_ppt);
   if (rc) return rc;
   return read_stats(h, stats);
 }
@@ -593,13 +637,12 @@ int init_state(mpdo_ctx* h, const double* v) {
     if (!std::isfinite(v[a])) return fail(h, MPDO_ERR_NUMERIC, "non-finite initial vector");
   std::fill(h->bond.begin(), h->bond.end(), 1);
   std::fill(h->kd.begin(), h->kd.end(), 1);
-  h->cur = 0;
   h->rev = false;
   h->centre = 0;
   if (h->dbl)
-    CK(product_state<double>(h->st, v, static_cast<double2*>(h->sites[0]), (long)h->site_cap, h->n));
+    CK(product_state<double>(h->st, v, static_cast<double2*>(h->sites), (long)h->site_cap, h->n));
   else
-    CK(product_state<float>(h->st, v, static_cast<float2*>(h->sites[0]), (long)h->site_cap, h->n));
+    CK(product_state<float>(h->st, v, static_cast<float2*>(h->sites), (long)h->site_cap, h->n));
   CK(cudaStreamSynchronize(h->st));
   return MPDO_OK;
 }
@@ -629,7 +672,7 @@ int energy(mpdo_ctx* h, double J, double hx, double bz, double out[6]) {
   int cur = 0;
   for (int s = 0; s < h->n; ++s) {
     const int dl = h->bond[s], k = h->kd[s], dr = h->bond[s + 1];
-    const T* A = static_cast<const T*>(h->site(h->cur, s));
+    const T* A = static_cast<const T*>(h->site(s));
     const long cols = 3L * k * dr;
     // F[a] = E[a]^T A   (dl x cols)
     CK(pgemm<R>(h, OP_T, OP_N, dl, (int)cols, dl, ebuf[cur], dl, env, A, cols, 0, F, cols, fsz,
@@ -685,7 +728,7 @@ int sample(mpdo_ctx* h, int ns, uint64_t seed, uint8_t* bits, double* probs) {
   CK(cudaMemcpyAsync(renv + (long)N * env, &o, sizeof(T), cudaMemcpyHostToDevice, st));
   for (int s = N - 1; s >= 0; --s) {
     const int dl = h->bond[s], k = h->kd[s], dr = h->bond[s + 1];
-    const T* A = static_cast<const T*>(h->site(h->cur, s));
+    const T* A = static_cast<const T*>(h->site(s));
     // Y = A (dl*3k x dr) R_{s+1} (dr x dr);  R_s = Y (dl x 3k*dr) A^+
     CK(pgemm<R>(h, OP_N, OP_N, dl * 3 * k, dr, dr, A, dr, 0, renv + (long)(s + 1) * env, dr, 0,
                 Y, dr, 0, 1));
@@ -699,7 +742,7 @@ int sample(mpdo_ctx* h, int ns, uint64_t seed, uint8_t* bits, double* probs) {
     CK(cudaMemcpyAsync(Ecur, ones.data(), sizeof(T) * cn, cudaMemcpyHostToDevice, st));
     for (int s = 0; s < N; ++s) {
       const int dl = h->bond[s], k = h->kd[s], dr = h->bond[s + 1];
-      const T* A = static_cast<const T*>(h->site(h->cur, s));
+      const T* A = static_cast<const T*>(h->site(s));
       const long cols = 3L * k * dr, plane = (long)dl * k * dr;
       // F_q = E_q^T A  (dl x cols), packed per sample (stride dl*cols = 3*plane)
       CK(pgemm<R>(h, OP_T, OP_N, dl, (int)cols, dl, Ecur, dl, (long)dl * dl, A, cols, 0, Ef,
@@ -758,45 +801,51 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   h->mmax = cfg->m_max;
   h->dbl = (cfg->prec == MPDO_FP64);
   h->elt = h->dbl ? 16 : 8;
+  h->mixed = !h->dbl && cfg->gram_fp64;
+  h->eltm = (h->dbl || h->mixed) ? 16 : 8;
   // Numerical-zero cuts.  Gram eigenvalues resolve only down to ~eps * max, so the cuts
-  // are applied there: bond lambda = s^2 > htol*lambda_0, inner w > kcut^2 * w_0.
-  const double eps = h->dbl ? 1e-16 : 6e-8;
+  // are applied there: bond lambda = s^2 > htol*lambda_0, inner w > kcut^2 * w_0.  With
+  // FP64 Grams of FP32 tensors the floor is the rounding of the tensors themselves
+  // (relative 6e-8 per entry, i.e. ~4e-15 on lambda), taken as eps = 1e-14.
+  const double eps = h->dbl ? 1e-16 : h->mixed ? 1e-14 : 6e-8;
   h->gtol = 10 * eps;
   double sv = cfg->sv_cutoff > 0 ? cfg->sv_cutoff : 1e-14;
   h->htol = std::max(sv * sv, 10 * eps);
   double kc = cfg->kraus_cutoff > 0 ? cfg->kraus_cutoff : 1e-14;
   h->kcut = std::max(kc, std::sqrt(10 * eps));
-  h->max_sweeps = h->dbl ? 30 : 20;
+  h->max_sweeps = (h->dbl || h->mixed) ? 30 : 20;
   h->bond.assign(h->n + 1, 1);
   h->kd.assign(h->n, 1);
   const long D = h->chi, K = h->kmax, M = h->mmax;
   const long n3 = 3 * D, n9 = 9 * D, KM = K * M;
   h->site_cap = (size_t)D * 3 * K * D;
   int rc;
-  for (int b = 0; b < 2; ++b)
-    if ((rc = alloc_dev(hp, &h->sites[b], h->site_cap * h->elt * h->n))) return rc;
-  const size_t e = h->elt;
+  if ((rc = alloc_dev(hp, &h->sites, h->site_cap * h->elt * h->n))) return rc;
+  const size_t e = h->elt, em = h->eltm;
+  // A: storage precision (site tensors, large contractions); B: Gram-derived matrices
   auto A = [&](void** p, size_t count) { return alloc_dev(hp, p, count * e); };
-  if ((rc = A(&h->wM, D * K * n3)) || (rc = A(&h->wGi, n3 * n3)) || (rc = A(&h->wGj, n3 * n3)) ||
-      (rc = A(&h->wVg, n3 * n3)) || (rc = A(&h->wR, n3 * n3)) || (rc = A(&h->wVs, n3 * n3)) ||
-      (rc = A(&h->wVr, n3 * n3)) || (rc = A(&h->wPhi, n9 * n9)) || (rc = A(&h->wX, n9 * n9)) ||
-      (rc = A(&h->wH, n9 * n9)) || (rc = A(&h->wU, n9 * n9)) || (rc = A(&h->wVgen, n9 * D)) ||
+  auto B = [&](void** p, size_t count) { return alloc_dev(hp, p, count * em); };
+  if ((rc = A(&h->wM, D * K * n3)) || (rc = B(&h->wGi, n3 * n3)) || (rc = B(&h->wGj, n3 * n3)) ||
+      (rc = B(&h->wVg, n3 * n3)) || (rc = B(&h->wR, n3 * n3)) || (rc = B(&h->wVs, n3 * n3)) ||
+      (rc = B(&h->wVr, n3 * n3)) || (rc = B(&h->wPhi, n9 * n9)) || (rc = B(&h->wX, n9 * n9)) ||
+      (rc = B(&h->wH, n9 * n9)) || (rc = B(&h->wU, n9 * n9)) || (rc = B(&h->wVgen, n9 * D)) ||
       (rc = A(&h->wW, n9 * D)) || (rc = A(&h->wTmp, D * K * 3 * D)) ||
       (rc = A(&h->wQ, D * 3 * M * n3)) || (rc = A(&h->wWB, D * 3 * M * K * D)) ||
-      (rc = A(&h->wBp, D * 3 * M * K * D)) || (rc = A(&h->wWK, KM * KM)) ||
-      (rc = A(&h->wVk, KM * KM)) || (rc = A(&h->wVks, KM * K)) || (rc = A(&h->wCn, K * D * 3 * D)))
+      (rc = A(&h->wBp, D * 3 * M * K * D)) || (rc = B(&h->wWK, KM * KM)) ||
+      (rc = B(&h->wVk, KM * KM)) || (rc = A(&h->wVks, KM * K)) || (rc = A(&h->wCn, K * D * 3 * D)))
     return rc;
   if ((rc = A(&h->wPol, D * D)) || (rc = A(&h->wQol, D * D)) || (rc = A(&h->wGa, D * D)))
     return rc;
-  const size_t rsz = h->dbl ? 8 : 4;
+  if (h->mixed && (rc = A(&h->wVgenS, n9 * D))) return rc;
+  const size_t rsz = em / 2;
   if ((rc = alloc_dev(hp, &h->wRs, n3 * rsz)) || (rc = alloc_dev(hp, &h->wIrs, n3 * rsz)) ||
       (rc = alloc_dev(hp, (void**)&h->wSig, n3 * 8)) || (rc = alloc_dev(hp, (void**)&h->wLam, n9 * 8)) ||
       (rc = alloc_dev(hp, (void**)&h->wWv, KM * 8)) || (rc = alloc_dev(hp, (void**)&h->wF, K * 8)))
     return rc;
   const int ncap = (int)std::max(n9, KM);
-  size_t eb = h->dbl ? eig_work_bytes<double>(ncap) : eig_work_bytes<float>(ncap);
+  size_t eb = em == 16 ? eig_work_bytes<double>(ncap) : eig_work_bytes<float>(ncap);
   if ((rc = alloc_dev(hp, &h->eigmem, eb))) return rc;
-  if (h->dbl) eig_work_bind<double>(h->eig64, h->eigmem, ncap);
+  if (em == 16) eig_work_bind<double>(h->eig64, h->eigmem, ncap);
   else eig_work_bind<float>(h->eig32, h->eigmem, ncap);
   if ((rc = alloc_dev(hp, (void**)&h->dsc, sizeof(StepScalars))) ||
       (rc = alloc_dev(hp, (void**)&h->dstats, sizeof(DevStats))))
@@ -975,11 +1024,11 @@ int mpdo_get_site(mpdo_t h, int n, double* out, size_t cap, int* dims) {
   if (cap < cnt) return fail(h, MPDO_ERR_ARG, "output capacity too small");
   std::vector<double> tmp(2 * cnt);
   if (h->dbl) {
-    CK(cudaMemcpyAsync(tmp.data(), h->site(h->cur, s), cnt * 16, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(tmp.data(), h->site(s), cnt * 16, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
   } else {
     std::vector<float> f(2 * cnt);
-    CK(cudaMemcpyAsync(f.data(), h->site(h->cur, s), cnt * 8, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(f.data(), h->site(s), cnt * 8, cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     for (size_t a = 0; a < 2 * cnt; ++a) tmp[a] = f[a];
   }

@@ -10,10 +10,12 @@ namespace mpdo {
 namespace {
 constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
 
-template <typename R>
+// Inputs of precision RI, products and sums in R (RI = float, R = double: the FP32
+// products are exact in FP64 and the sums carry FP64 rounding only).
+template <typename RI, typename R>
 __global__ void __launch_bounds__(NT) cgemm_kernel(
-    int M, int N, int K, const cx<R>* __restrict__ A, long sam, long sak, long sab, int conja,
-    const cx<R>* __restrict__ B, long sbk, long sbn, long sbb, int conjb, cx<R>* C, long scm,
+    int M, int N, int K, const cx<RI>* __restrict__ A, long sam, long sak, long sab, int conja,
+    const cx<RI>* __restrict__ B, long sbk, long sbn, long sbb, int conjb, cx<R>* C, long scm,
     long scn, long scb, cx<R> alpha, cx<R> beta, int use_beta) {
   using T = cx<R>;
   __shared__ T As[BK][BM + 1];
@@ -41,8 +43,8 @@ __global__ void __launch_bounds__(NT) cgemm_kernel(
       int gm = m0 + mi, gk = k0 + ki;
       T v = mkc<R>(0, 0);
       if (gm < M && gk < K) {
-        v = A[gm * sam + gk * sak];
-        if (conja) v.y = -v.y;
+        cx<RI> t = A[gm * sam + gk * sak];
+        v = mkc<R>((R)t.x, conja ? -(R)t.y : (R)t.y);
       }
       As[ki][mi] = v;
     }
@@ -54,8 +56,8 @@ __global__ void __launch_bounds__(NT) cgemm_kernel(
       int gn = n0 + ni, gk = k0 + ki;
       T v = mkc<R>(0, 0);
       if (gn < N && gk < K) {
-        v = B[gk * sbk + gn * sbn];
-        if (conjb) v.y = -v.y;
+        cx<RI> t = B[gk * sbk + gn * sbn];
+        v = mkc<R>((R)t.x, conjb ? -(R)t.y : (R)t.y);
       }
       Bs[ki][ni] = v;
     }
@@ -91,10 +93,10 @@ __global__ void __launch_bounds__(NT) cgemm_kernel(
 }
 }  // namespace
 
-template <typename R>
-cudaError_t cgemm(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<R>* A,
-                  long lda, long sa, const cx<R>* B, long ldb, long sb, cx<R>* C, long ldc,
-                  long sc, int batch, cx<R> alpha, cx<R> beta) {
+template <typename RI, typename R>
+cudaError_t cgemm_impl(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<RI>* A,
+                       long lda, long sa, const cx<RI>* B, long ldb, long sb, cx<R>* C, long ldc,
+                       long sc, int batch, cx<R> alpha, cx<R> beta) {
   if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
   long sam, sak, sbk, sbn;
   int conja = (opa == OP_C || opa == OP_R), conjb = (opb == OP_C || opb == OP_R);
@@ -108,11 +110,27 @@ cudaError_t cgemm(cudaStream_t st, int opa, int opb, int m, int n, int k, const 
     int nb = batch - b0 < 65535 ? batch - b0 : 65535;
     dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, nb);
     count_launch();
-    cgemm_kernel<R><<<grid, NT, 0, st>>>(m, n, k, A + (long)b0 * sa, sam, sak, sa, conja,
-                                          B + (long)b0 * sb, sbk, sbn, sb, conjb,
-                                          C + (long)b0 * sc, ldc, 1, sc, alpha, beta, use_beta);
+    cgemm_kernel<RI, R><<<grid, NT, 0, st>>>(m, n, k, A + (long)b0 * sa, sam, sak, sa, conja,
+                                              B + (long)b0 * sb, sbk, sbn, sb, conjb,
+                                              C + (long)b0 * sc, ldc, 1, sc, alpha, beta,
+                                              use_beta);
   }
   return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t cgemm(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<R>* A,
+                  long lda, long sa, const cx<R>* B, long ldb, long sb, cx<R>* C, long ldc,
+                  long sc, int batch, cx<R> alpha, cx<R> beta) {
+  return cgemm_impl<R, R>(st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch,
+                          alpha, beta);
+}
+
+cudaError_t cgemm_wide(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<float>* A,
+                       long lda, long sa, const cx<float>* B, long ldb, long sb, cx<double>* C,
+                       long ldc, long sc, int batch) {
+  return cgemm_impl<float, double>(st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc,
+                                   batch, mkc<double>(1, 0), mkc<double>(0, 0));
 }
 
 template cudaError_t cgemm<double>(cudaStream_t, int, int, int, int, int, const double2*, long,

@@ -13,6 +13,11 @@ cudaError_t cgemm(cudaStream_t st, int opa, int opb, int m, int n, int k, const 
                   long lda, long sa, const cx<R>* B, long ldb, long sb, cx<R>* C, long ldc,
                   long sc, int batch, cx<R> alpha, cx<R> beta);
 
+// C = op(A) op(B) with FP32 inputs and FP64 products and sums (alpha 1, beta 0).
+cudaError_t cgemm_wide(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<float>* A,
+                       long lda, long sa, const cx<float>* B, long ldb, long sb, cx<double>* C,
+                       long ldc, long sc, int batch);
+
 // Workspace of the Hermitian eigensolver (capacity n_cap).
 template <typename R>
 struct EigWork {

@@ -291,14 +291,15 @@ __global__ void kraus_select_kernel(int n, const double* __restrict__ w, const c
 }
 
 // Vks[kappa][k] = V[kappa][k] * f[k], k < kk (V has leading dimension ldv)
-template <typename R>
+template <typename R, typename RO>
 __global__ void scale_vk_kernel(int n, int kk, const cx<R>* __restrict__ v, long ldv,
-                                const double* __restrict__ f, cx<R>* out) {
+                                const double* __restrict__ f, cx<RO>* out) {
   long total = (long)n * kk;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
     int r = (int)(e / kk), c = (int)(e % kk);
-    out[e] = cscale(v[(long)r * ldv + c], (R)f[c]);
+    cx<R> t = cscale(v[(long)r * ldv + c], (R)f[c]);
+    out[e] = mkc<RO>((RO)t.x, (RO)t.y);
   }
 }
 
@@ -432,23 +433,51 @@ __global__ void polar_factors_kernel(int n, const cx<R>* __restrict__ g, cx<R>* 
 // Inner-index truncation through the dual Gram W' = B^+B (used when B has fewer columns
 // than rows): with W' y_k = w_k y_k, the kept rows of the new centre are
 // f_k x_k^+ B = f_k sqrt(w_k) y_k^+  (x_k = B y_k / sqrt(w_k)), so no product with B is needed.
-template <typename R>
+template <typename R, typename RO>
 __global__ void dual_rows_kernel(int kk, int cols, const cx<R>* __restrict__ y, long ldy,
                                  const double* __restrict__ f, const double* __restrict__ w,
-                                 cx<R>* out) {
+                                 cx<RO>* out) {
   long total = (long)kk * cols;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
        e += (long)gridDim.x * blockDim.x) {
     int k = (int)(e / cols), c = (int)(e % cols);
     double wk = w[k] > 0 ? w[k] : 0.0;
     R sc = (R)(f[k] * sqrt(wk));
-    out[e] = cscale(cconj(y[(long)c * ldy + k]), sc);
+    cx<R> t = cscale(cconj(y[(long)c * ldy + k]), sc);
+    out[e] = mkc<RO>((RO)t.x, (RO)t.y);
   }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------- launchers
+// Rows x cols complex matrix copied between precisions (strided rows on both sides).
+template <typename Ri, typename Ro>
+__global__ void convert_kernel(int rows, int cols, const cx<Ri>* __restrict__ in, long ldi,
+                               cx<Ro>* __restrict__ out, long ldo) {
+  long total = (long)rows * cols;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long r = e / cols, c = e % cols;
+    cx<Ri> v = in[r * ldi + c];
+    out[r * ldo + c] = mkc<Ro>((Ro)v.x, (Ro)v.y);
+  }
+}
+
+template <typename Ri, typename Ro>
+cudaError_t convert(cudaStream_t st, int rows, int cols, const cx<Ri>* in, long ldi, cx<Ro>* out,
+                    long ldo) {
+  long total = (long)rows * cols;
+  if (total <= 0) return cudaSuccess;
+  count_launch();
+  convert_kernel<Ri, Ro><<<nblocks(total), 256, 0, st>>>(rows, cols, in, ldi, out, ldo);
+  return cudaGetLastError();
+}
+template cudaError_t convert<float, double>(cudaStream_t, int, int, const cx<float>*, long,
+                                            cx<double>*, long);
+template cudaError_t convert<double, float>(cudaStream_t, int, int, const cx<double>*, long,
+                                            cx<float>*, long);
+
 template <typename T>
 cudaError_t swap12(cudaStream_t st, long n0, long n1, long n2, long n3, const T* in, T* out) {
   long total = n0 * n1 * n2 * n3;
@@ -522,11 +551,11 @@ cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* w
   kraus_select_kernel<R><<<1, 32, 0, st>>>(n, w, wm, kcut, kmax, use_ppt, f, sc, ds);
   return cudaGetLastError();
 }
-template <typename R>
+template <typename R, typename RO>
 cudaError_t scale_vk(cudaStream_t st, int n, int kk, const cx<R>* v, long ldv, const double* f,
-                     cx<R>* out) {
+                     cx<RO>* out) {
   count_launch();
-  scale_vk_kernel<R><<<nblocks((long)n * kk), 256, 0, st>>>(n, kk, v, ldv, f, out);
+  scale_vk_kernel<R, RO><<<nblocks((long)n * kk), 256, 0, st>>>(n, kk, v, ldv, f, out);
   return cudaGetLastError();
 }
 template <typename R>
@@ -554,11 +583,11 @@ cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<
   return cudaGetLastError();
 }
 
-template <typename R>
+template <typename R, typename RO>
 cudaError_t dual_rows(cudaStream_t st, int kk, int cols, const cx<R>* y, long ldy, const double* f,
-                      const double* w, cx<R>* out) {
+                      const double* w, cx<RO>* out) {
   count_launch();
-  dual_rows_kernel<R><<<nblocks((long)kk * cols), 256, 0, st>>>(kk, cols, y, ldy, f, w, out);
+  dual_rows_kernel<R, RO><<<nblocks((long)kk * cols), 256, 0, st>>>(kk, cols, y, ldy, f, w, out);
   return cudaGetLastError();
 }
 
@@ -576,21 +605,27 @@ cudaError_t dual_rows(cudaStream_t st, int kk, int cols, const cx<R>* y, long ld
   template cudaError_t build_phi<R>(cudaStream_t, int, const cx<R>*, const cx<R>*, cx<R>*); \
   template cudaError_t make_q<R>(cudaStream_t, int, int, int, const cx<R>*, const cx<R>*,   \
                                  const StepScalars*, cx<R>*);                               \
-  template cudaError_t scale_vk<R>(cudaStream_t, int, int, const cx<R>*, long,              \
-                                   const double*, cx<R>*);                                  \
   template cudaError_t energy_mix<R>(cudaStream_t, int, int, const cx<R>*, long, cx<R>*,    \
                                      long, double, double, double);                         \
   template cudaError_t bond_select<R>(cudaStream_t, int, const double*, const cx<R>*, long,  \
                                       double, int, StepScalars*, DevStats*);                 \
   template cudaError_t kraus_select<R>(cudaStream_t, int, const double*, const cx<R>*, double, \
                                        int, int, double*, StepScalars*, DevStats*);          \
-  template cudaError_t dual_rows<R>(cudaStream_t, int, int, const cx<R>*, long, const double*, \
-                                    const double*, cx<R>*);                                 \
   template cudaError_t polar_factors<R>(cudaStream_t, int, const cx<R>*, cx<R>*, cx<R>*);   \
   template cudaError_t sample_pick<R>(cudaStream_t, int, int, const cx<R>*, const cx<R>*,   \
                                       uint64_t, int, int, int, cx<R>*, uint8_t*, double*, int);
 INST(double)
 INST(float)
 #undef INST
+
+#define INST2(R, RO)                                                                          \
+  template cudaError_t scale_vk<R, RO>(cudaStream_t, int, int, const cx<R>*, long,           \
+                                       const double*, cx<RO>*);                              \
+  template cudaError_t dual_rows<R, RO>(cudaStream_t, int, int, const cx<R>*, long,          \
+                                        const double*, const double*, cx<RO>*);
+INST2(double, double)
+INST2(float, float)
+INST2(double, float)
+#undef INST2
 
 }  // namespace mpdo

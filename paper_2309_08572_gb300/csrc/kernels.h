@@ -5,6 +5,10 @@
 #include "common.cuh"
 
 namespace mpdo {
+// out (rows x cols, row stride ldo) = in converted from precision Ri to Ro.
+template <typename Ri, typename Ro>
+cudaError_t convert(cudaStream_t st, int rows, int cols, const cx<Ri>* in, long ldi, cx<Ro>* out,
+                    long ldo);
 template <typename T>
 cudaError_t swap12(cudaStream_t st, long n0, long n1, long n2, long n3, const T* in, T* out);
 template <typename T>
@@ -27,17 +31,17 @@ cudaError_t bond_select(cudaStream_t st, int n, const double* lam, const cx<R>* 
 template <typename R>
 cudaError_t make_q(cudaStream_t st, int dm, int keep, int m_ops, const cx<R>* w, const cx<R>* e,
                    const StepScalars* sc, cx<R>* q);
-template <typename R>
+template <typename R, typename RO>
 cudaError_t dual_rows(cudaStream_t st, int kk, int cols, const cx<R>* y, long ldy, const double* f,
-                      const double* w, cx<R>* out);
+                      const double* w, cx<RO>* out);
 template <typename R>
 cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<R>* qm);
 template <typename R>
 cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, double kcut,
                          int kmax, int use_ppt, double* f, StepScalars* sc, DevStats* ds);
-template <typename R>
+template <typename R, typename RO>
 cudaError_t scale_vk(cudaStream_t st, int n, int kk, const cx<R>* v, long ldv, const double* f,
-                     cx<R>* out);
+                     cx<RO>* out);
 template <typename R>
 cudaError_t energy_mix(cudaStream_t st, int dl, int plane, const cx<R>* f, long fstride,
                        cx<R>* g, long gstride, double J, double hx, double bz);

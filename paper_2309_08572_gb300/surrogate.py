@@ -20,21 +20,42 @@ from . import Mlp, Mpdo, batch_run, circuit_layers
 WIDTH = 256
 
 
+def _angle_block(theta: np.ndarray) -> np.ndarray:
+    """Angle features of the rows of theta (n, 2p): the angle scaled to [-1, 1] and the
+    first two harmonics sin/cos(2 theta), sin/cos(4 theta).  The energy is smooth and
+    close to periodic in each angle, which the raw angle alone hides from the network."""
+    return np.concatenate([2.0 * theta / math.pi - 1.0, np.sin(2 * theta), np.cos(2 * theta),
+                           np.sin(4 * theta), np.cos(4 * theta)], axis=1)
+
+
+def _angle_block_grad(theta: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Chain rule through _angle_block: d/dtheta from the gradient g on its 5 blocks."""
+    q = theta.shape[1]
+    gr, gs2, gc2, gs4, gc4 = (g[:, i * q:(i + 1) * q] for i in range(5))
+    return (gr * (2.0 / math.pi) + 2.0 * (gs2 * np.cos(2 * theta) - gc2 * np.sin(2 * theta))
+            + 4.0 * (gs4 * np.cos(4 * theta) - gc4 * np.sin(4 * theta)))
+
+
+N_FIXED = 4
+
+
+def fixed_features(c) -> np.ndarray:
+    """(N, decay, dephasing, crosstalk) scaled to about [-1, 1]."""
+    return np.asarray([c.n_sites / 50.0 - 1.0,
+                       math.log10(max(c.gamma_diss, 1e-6)) + 3.0,
+                       math.log10(max(c.gamma_deph, 1e-6)) + 3.0,
+                       c.xtalk_phase * 50.0], dtype=np.float32)
+
+
+def n_features(p: int) -> int:
+    return N_FIXED + 10 * p
+
+
 def features(c, p: int) -> np.ndarray:
-    """(N, decay, dephasing, crosstalk, alpha_1..p, beta_1..p) scaled to about [-1, 1]."""
-    f = [c.n_sites / 50.0 - 1.0,
-         (math.log10(max(c.gamma_diss, 1e-6)) + 3.0),
-         (math.log10(max(c.gamma_deph, 1e-6)) + 3.0),
-         c.xtalk_phase * 50.0]
-    f += [2.0 * a / math.pi - 1.0 for a in c.alpha[:p]]
-    f += [2.0 * b / math.pi - 1.0 for b in c.beta[:p]]
-    return np.asarray(f, dtype=np.float32)
-
-
-def angles_from_features(x: np.ndarray, p: int):
-    a = (x[4:4 + p] + 1.0) * math.pi / 2.0
-    b = (x[4 + p:4 + 2 * p] + 1.0) * math.pi / 2.0
-    return [float(v) for v in a], [float(v) for v in b]
+    """Network input of one circuit: fixed_features, then _angle_block of
+    (alpha_1..p, beta_1..p)."""
+    theta = np.asarray([list(c.alpha[:p]) + list(c.beta[:p])], dtype=np.float64)
+    return np.concatenate([fixed_features(c), _angle_block(theta)[0].astype(np.float32)])
 
 
 def simulate(circuits: Sequence, pool: List[Mpdo]) -> np.ndarray:
@@ -83,28 +104,34 @@ def train(net: Mlp, x: np.ndarray, t: np.ndarray, steps: int, lr: float, batch: 
     return losses
 
 
-def propose(net: Mlp, base_feat: np.ndarray, p: int, n_starts: int, steps: int, lr: float,
-            seed: int, weight_success: float = 0.0) -> np.ndarray:
-    """Gradient descent on the angle features of the surrogate's predicted energy (plus
-    -weight_success * success probability) from n_starts random starts; fixed features (N,
-    rates) are held.  Returns the final features, best predicted first."""
+def propose(net: Mlp, c, p: int, n_starts: int, steps: int, lr: float, seed: int,
+            weight_success: float = 0.0) -> np.ndarray:
+    """Gradient descent of the surrogate's predicted energy (plus -weight_success * success
+    probability) over the 2p angles of circuit c, from n_starts random starts; N and the
+    rates are held.  The input gradient comes from the network's backward kernels; the
+    chain rule through the angle features is applied here.  Returns the angles (n_starts,
+    2p) in [0, pi], best predicted first."""
     import torch
     rng = np.random.default_rng(seed)
-    x = np.repeat(base_feat[None, :], n_starts, axis=0).astype(np.float32)
-    x[:, 4:4 + 2 * p] = rng.uniform(-1, 1, (n_starts, 2 * p))
-    tx = torch.tensor(x, dtype=torch.float32, device="cuda")
+    theta = rng.uniform(0.0, math.pi, (n_starts, 2 * p))
+    fixed = np.repeat(fixed_features(c)[None, :], n_starts, axis=0)
+
+    def feats(th):
+        return np.concatenate([fixed, _angle_block(th).astype(np.float32)], axis=1)
+
+    tx = torch.tensor(feats(theta), dtype=torch.float32, device="cuda")
     gx = torch.zeros_like(tx)
     wout = np.array([1.0, -weight_success], dtype=np.float32)
     for _ in range(steps):
         net.input_grad(tx, wout, gx)
-        g = gx.cpu().numpy()
-        x[:, 4:4 + 2 * p] = np.clip(x[:, 4:4 + 2 * p] - lr * g[:, 4:4 + 2 * p], -1.0, 1.0)
-        tx.copy_(torch.from_numpy(x))
+        g = gx.cpu().numpy().astype(np.float64)[:, N_FIXED:]
+        theta = np.clip(theta - lr * _angle_block_grad(theta, g), 0.0, math.pi)
+        tx.copy_(torch.from_numpy(feats(theta)))
     y = torch.zeros((n_starts, 2), dtype=torch.float32, device="cuda")
     net.forward(tx, y)
     yh = y.cpu().numpy()
     order = np.argsort(yh[:, 0] - weight_success * yh[:, 1])
-    return x[order]
+    return theta[order]
 
 
 def with_angles(c, a, b):
