@@ -48,22 +48,40 @@ def workload():
     return synth.chain40() if WORKLOAD == "chain40" else synth.chain100()
 
 
-def workload_desc(c, prec):
+PREC_DESC = {
+    "mixed": "mixed: complex64 site tensors and large contractions (FP32), Gram matrices with "
+             "FP64 products and sums, FP32 Jacobi sweeps with FP64 refinement, FP64 cuts, PPT "
+             "and observables",
+    "c64": "complex64 throughout (FP32 Grams and Jacobi), FP64 scalars and observables",
+    "fp64": "complex128 throughout",
+}
+
+
+def workload_desc(c, prec, sv):
     return {"workload": f"{WORKLOAD}: N={c.n_sites} atoms (d=3), QAOA p={c.p}, chi={c.chi_max}, "
                         f"K={c.k_max}, decay {c.gamma_diss}, dephasing {c.gamma_deph}, "
                         f"crosstalk {c.xtalk_phase} rad, post-promotion {c.delta_pp} rad, "
                         f"TFIM J={c.J} h={c.hx}, seed {c.seed}",
             "updates_per_circuit": c.p * (c.n_sites - 1),
-            "precision": prec, "parallelism": "replicas", "gate_model": "G0 (gate level)",
+            "precision": PREC_DESC[prec], "bond_cut": f"s > {sv:g} s_max" if sv else "numerical floor",
+            "parallelism": "replicas", "gate_model": "G0 (gate level)",
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
 # --------------------------------------------------------------------- CPU oracle
-def oracle_sample(c, budget_s: float, n_steps: int = 0):
+def bond_cut(args):
+    """The bond cut of the timed configuration (s > cut * s_max; 0 = numerical floor)."""
+    if args.sv_cutoff is not None:
+        return args.sv_cutoff
+    return 0.0 if args.prec == "c64" else 1e-4
+
+
+def oracle_sample(c, budget_s: float, n_steps: int = 0, sv: float = 0.0):
     """Time the oracle on the workload: layers 1..p-1 in full, then layer-p updates (the
     expensive ones) up to budget_s (or n_steps of them); extrapolate one full circuit."""
     from oracle import mpdo as ompdo, qaoa as oqaoa
-    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max)
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max,
+                   sv_cutoff=sv if sv > 0 else 1e-14)
     layer_t = []
     for k in range(c.p - 1):
         t0 = time.perf_counter()
@@ -102,8 +120,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     from oracle import mpdo as ompdo, qaoa as oqaoa
+    sv = bond_cut(args)
     t0 = time.perf_counter()
-    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max)
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max,
+                   sv_cutoff=sv if sv > 0 else 1e-14)
     layer_t = []
     for k in range(c.p - 1):
         t1 = time.perf_counter()
@@ -126,7 +146,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(per), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_desc(c, "fp64 (CPU oracle)"),
+            "config": workload_desc(c, args.prec, sv),
+            "oracle": "complex128 NumPy oracle on the host cores, same bond cut",
             "energy_evals_per_s": 1.0 / t_circ,
             "cpu_baseline": {"value": ups, "unit": "site-updates/s", "cores": cpu_cores(),
                              "kind": "oracle", "sample": sample},
@@ -231,7 +252,7 @@ def run_ours(args):
     c = workload()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        layer_t, per, n_last = oracle_sample(c, args.cpu_budget)
+        layer_t, per, n_last = oracle_sample(c, args.cpu_budget, sv=bond_cut(args))
         t_circ = oracle_rate(layer_t, per, n_last)
         ups = c.p * (c.n_sites - 1) / t_circ
         cpu = {"value": ups, "unit": "site-updates/s", "cores": cpu_cores(), "kind": "oracle",
@@ -248,10 +269,13 @@ def run_ours(args):
     import paper_2309_08572_gb300 as lib
 
     prec = args.prec
+    sv = bond_cut(args)
     circs = batch_circuits(c, args.batch)
     host_layers = [lib.circuit_layers(ci) for ci in circs]
     m_max = max(k.shape[0] for L in host_layers for layer in L for _, k in layer)
-    pool = [lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec=prec, own_stream=True)
+    lprec = "fp64" if prec == "fp64" else "c64"
+    pool = [lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec=lprec, own_stream=True,
+                     gram_fp64=(prec == "mixed"), sv_cutoff=sv)
             for _ in range(args.batch)]
     dls = [[pool[0].upload_layer(layer) for layer in L] for L in host_layers]
     descs = [dict(n_sites=ci.n_sites, chi_max=ci.chi_max, k_max=ci.k_max, layers=d, J=ci.J,
@@ -318,6 +342,9 @@ def run_ours(args):
     # end to end through the host-buffer API: every step uploads each circuit's ops from
     # host memory, runs the batch and reads the energies back
     h2d = sum(layer_bytes(L, 16 if prec == "fp64" else 8) for L in host_layers)
+    if prec == "mixed":   # the channel partial traces travel in FP64
+        h2d = sum(sum((2 * k.shape[0] * 81 * 8 + 2 * 729 * 16) for _, k in layer)
+                  for L in host_layers for layer in L)
     d2h = args.batch * (4 * 8 + updates * 2 * STEP_SCALARS_BYTES + c.p * DEV_STATS_BYTES)
     torch.cuda.synchronize()
     te = []
@@ -362,26 +389,37 @@ def run_ours(args):
         roof.update({"bound": "latency", "achieved": None, "peak": None, "unit": None,
                      "frac": None, "traffic": None})
 
+    # the plain FP64 single-circuit form on the same circuit and cut: its time, and the
+    # error of this run's circuit 0 against it, per observable
     fp64 = None
-    if args.fp64_compare and prec != "fp64" and rank == 0:
-        g64 = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec="fp64", own_stream=True)
+    if not args.no_fp64_compare and prec != "fp64" and rank == 0 and world == 1:
+        g64 = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec="fp64", own_stream=True,
+                       sv_cutoff=sv)
         dl64 = [g64.upload_layer(layer) for layer in host_layers[0]]
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         r64 = lib.batch_run([g64], [dict(descs[0], layers=dl64)])
         t64 = time.perf_counter() - t0
-        fp64 = {"ms_per_circuit": 1e3 * t64, "speedup_vs_fp64_single": (1e3 * t64) / single_ms,
-                "rel_err": {k: abs(single[0][j] - r64[0][j]) / abs(r64[0][j])
-                            for j, k in enumerate(("e_raw", "e_succ", "p_succ", "trace"))}}
+        ups64 = updates / t64
+        fp64 = {"ms_per_circuit": 1e3 * t64, "site_updates_per_s": ups64,
+                "factor_batched_vs_fp64_single": value / ups64,
+                "factor_single_vs_fp64_single": (1e3 * t64) / single_ms,
+                "rel_err": {k: abs(res[0][j] - r64[0][j]) / abs(r64[0][j])
+                            for j, k in enumerate(("e_raw", "e_succ", "p_succ", "trace"))},
+                "bond_cut": f"s > {sv:g} s_max" if sv else "numerical floor"}
+        for dl in dl64:
+            g64.free_uploaded(dl)
         g64.close()
 
     if rank == 0:
-        cfg = workload_desc(c, prec)
+        cfg = workload_desc(c, prec, sv)
         cfg["batch"] = f"{args.batch} circuits per step, run concurrently (one stream each); " \
                        f"circuit 0 uses seed {c.seed}, circuit j seeded angles {c.seed}*1000+j"
         line = {"metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+                "dtype": {"fp64": "f64", "c64": "f32", "mixed": "f32+f64"}[prec],
+                "data": "synthetic",
                 "config": cfg,
                 "energy_evals_per_s": world * args.steps * args.batch / (total_ms / 1e3),
                 "single_circuit": {"ms": single_ms, "site_updates_per_s": updates / (single_ms / 1e3),
@@ -411,10 +449,14 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp64", "c64"], default="c64")
+    ap.add_argument("--prec", choices=["mixed", "c64", "fp64"], default="mixed",
+                    help="mixed: FP32 tensors with FP64 Grams and small matrices (default)")
+    ap.add_argument("--sv-cutoff", type=float, default=None,
+                    help="bond cut s > cutoff * s_max (default 1e-4; c64: its numerical floor)")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the plain FP64 single-circuit comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--fp64-compare", action="store_true")
     ap.add_argument("--batch", type=int, default=16,
                     help="circuits per step, run concurrently by the batch executor")
     ap.add_argument("--workload", choices=["chain100", "chain40"], default="chain100",

@@ -63,7 +63,8 @@ typedef struct {
   double sv_cutoff;     /* bond values with s <= sv_cutoff*s_max are dropped (<=0: default) */
   double kraus_cutoff;  /* inner values with sqrt(w) <= kraus_cutoff*sqrt(w_max) dropped   */
   int use_ppt;          /* 1: purity-preserving inner truncation; 0: plain + trace renorm  */
-  void* cuda_stream;    /* cudaStream_t to use; NULL = a non-blocking stream the handle owns */
+  void* cuda_stream;    /* cudaStream_t to use; NULL = a non-blocking stream the handle owns
+                           (pass cudaStreamLegacy to run on the legacy default stream)   */
   int gram_fp64;        /* MPDO_C64 only.  1 = mixed precision: the Gram matrices (a2, a8)
                            are formed from the FP32 tensors with FP64 products and sums, and
                            everything derived from them (Jacobi eigenpairs, bond factors,
@@ -232,7 +233,8 @@ int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, 
  * gradient proposes angles that the engine then re-scores.  FP32 parameters and
  * arithmetic.  Parameters are one flat array W_0 b_0 W_1 b_1 ... with W_l stored
  * [fan_in][fan_out] row-major.  x, t, y, gx are device arrays [batch][width], row-major;
- * batch <= max_batch.  stream NULL = the network owns a non-blocking stream.
+ * batch <= max_batch.  stream NULL = the network owns a non-blocking stream (inputs written
+ * by other streams must then be synchronised first; cudaStreamLegacy is accepted).
  *   mpdo_mlp_loss_grad: forward, mean-squared loss (host *loss), backward into the
  *     network's gradient buffer (copied to grad_host when not NULL, n_params floats)
  *   mpdo_mlp_adam_step: one Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) with the last

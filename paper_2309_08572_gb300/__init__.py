@@ -122,11 +122,17 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+_CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream's handle
+
+
 def _current_stream():
+    """torch's current stream as a cudaStream_t.  torch reports its default stream as 0,
+    which the library reads as "create a stream of your own"; it is passed as
+    cudaStreamLegacy instead, so library kernels stay ordered with torch's work."""
     try:
         import torch
         if torch.cuda.is_available():
-            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream or _CUDA_STREAM_LEGACY)
     except ImportError:
         pass
     return C.c_void_p(None)

@@ -100,8 +100,15 @@ struct mpdo_ctx {
   EigWork<float> eig32;
   // FP32 site tensors with FP64 Gram matrices and small-matrix arithmetic (cfg.gram_fp64)
   bool mixed = false;
+  // inner eigenproblem through a pivoted Cholesky (see inner_eig)
+  void *wW32 = nullptr, *wL = nullptr, *wGs = nullptr, *wZ = nullptr;
+  struct PcOut { int r; int pad; double resid; };
+  PcOut* dpc = nullptr;
+  PcOut* hpc = nullptr;       // pinned
+  MixWork mixw;              // mixed-precision eigensolver workspace (mixed only)
+  void* mixmem = nullptr;
   size_t eltm = 16;          // bytes per complex of the Gram-derived matrices
-  void* wVgenS = nullptr;    // FP32 copy of Vgen (mixed only)
+  void* wAcM = nullptr;      // polar-corrected left factor in FP64 (mixed only)
   StepScalars* dsc = nullptr;
   StepScalars* hsc = nullptr;  // pinned
   DevStats* dstats = nullptr;
@@ -218,11 +225,24 @@ cudaError_t pgemm(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<R
   prof_end(h, 0, pi, 8.0 * m * n * (double)k * batch);
   return e;
 }
+// floor: eigenpairs below floor * lambda_max need not be resolved (used by the mixed mode)
+constexpr int kMixedEigMax = 118;
 template <typename R>
-cudaError_t peig(mpdo_ctx* h, int n, const cx<R>* a, long lda, cx<R>* v, long ldv, double* w) {
+cudaError_t peig(mpdo_ctx* h, int n, const cx<R>* a, long lda, cx<R>* v, long ldv, double* w,
+                 double floor) {
   int pi = prof_begin(h, 1);
   const int sweeps = std::is_same<R, double>::value ? 30 : 20;
-  cudaError_t e = heig<R>(h->st, n, a, lda, v, ldv, w, eigw<R>(h), sweeps);
+  cudaError_t e;
+  if constexpr (std::is_same<R, double>::value) {
+    // mixed mode: FP32 sweeps with FP64 refinement while the sweeps fit one CTA's shared
+    // memory; larger problems take the FP64 solver
+    if (h->mixed && n <= kMixedEigMax) {
+      e = heig_mixed(h->st, n, a, lda, v, ldv, w, floor, h->mixw, nullptr);
+      prof_end(h, 1, pi, 0.0);
+      return e;
+    }
+  }
+  e = heig<R>(h->st, n, a, lda, v, ldv, w, eigw<R>(h), sweeps);
   if (pi >= 0 && e == cudaSuccess && h->prof_slot < h->prof_nslots) {
     // executed flops: 8 real flops per complex MAC, 3*16*16*np MACs per active pair-round
     int slot = h->prof_slot++;
@@ -244,10 +264,102 @@ cudaError_t pgram(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<R
     return pgemm<RS>(h, opa, opb, m, n, k, A, lda, 0, B, ldb, 0, C, ldc, 0, 1);
   } else {
     int pi = prof_begin(h, 0);
-    cudaError_t e = cgemm_wide(h->st, opa, opb, m, n, k, A, lda, 0, B, ldb, 0, C, ldc, 0, 1);
+    cudaError_t e = cgemm_wide<float>(h->st, opa, opb, m, n, k, A, lda, 0, B, ldb, 0, C, ldc, 0, 1);
     prof_end(h, 0, pi, 8.0 * m * n * (double)k);
     return e;
   }
+}
+
+// FP32 A times B of precision RB with FP64 products and sums (mixed mode).
+template <typename RB>
+cudaError_t pwide(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<float>* A,
+                  long lda, long sa, const cx<RB>* B, long ldb, long sb, cx<double>* C, long ldc,
+                  long sc, int batch) {
+  int pi = prof_begin(h, 0);
+  cudaError_t e =
+      cgemm_wide<RB>(h->st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch);
+  prof_end(h, 0, pi, 8.0 * m * n * (double)k * batch);
+  return e;
+}
+
+// a8: eigenpairs of the inner Gram W (nin x nin, in wWK).  Small problems: all of them by
+// Jacobi.  Larger ones: only the leading part matters (at most k_max are kept; the total
+// weight comes from tr W and the PPT's |w|^2 from the eigenvalues, where the tail below the
+// factor's tolerance is negligible), so W ~ L L^+ by a pivoted Cholesky stopping at
+// kInnerTol64 (FP64 mode) or kInnerTol (FP32 factor) of tr W, and the eigenpairs of W are
+// lifted from those of the r x r matrix L^+ L: u_c = L z_c / sqrt(s_c).  A factor that
+// reaches kInnerRmax columns above the tolerance falls back to the full solve.
+// Eigenvectors go to wVk (row stride nin); returns their count.
+constexpr int kInnerDirect = 32;
+constexpr double kInnerTol = 1e-7;
+constexpr double kInnerTol64 = 1e-14;
+constexpr int kInnerRmax = 128;
+
+template <typename RM>
+int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
+  using TM = cx<RM>;
+  cudaStream_t st = h->st;
+  TM* W = static_cast<TM*>(h->wWK);
+  TM* V = static_cast<TM*>(h->wVk);
+  if (nin <= kInnerDirect) {
+    CK(peig<RM>(h, nin, W, nin, V, nin, h->wWv, 1e-10));
+    *nvals = nin;
+    return MPDO_OK;
+  }
+  // FP64 mode: FP64 factor down to 1e-14 of the trace; FP32 and mixed modes: FP32 factor
+  // down to its floor
+  const bool f64 = h->dbl;
+  const double tol = f64 ? kInnerTol64 : kInnerTol;
+  const int rmax = std::min(nin, kInnerRmax);
+  int pi = prof_begin(h, 2);
+  if constexpr (std::is_same<RM, double>::value) {
+    if (f64) {
+      CK(pchol<double>(st, nin, W, rmax, tol, static_cast<double2*>(h->wL), kInnerRmax,
+                       &h->dpc->r, &h->dpc->resid));
+    } else {
+      CK((convert<double, float>(st, nin, nin, W, nin, static_cast<float2*>(h->wW32), nin)));
+      CK(pchol<float>(st, nin, static_cast<const float2*>(h->wW32), rmax, tol,
+                      static_cast<float2*>(h->wL), kInnerRmax, &h->dpc->r, &h->dpc->resid));
+    }
+  } else {
+    CK(pchol<float>(st, nin, W, rmax, tol, static_cast<float2*>(h->wL), kInnerRmax, &h->dpc->r,
+                    &h->dpc->resid));
+  }
+  prof_end(h, 2, pi, 0.0);
+  CK(cudaMemcpyAsync(h->hpc, h->dpc, sizeof(mpdo_ctx::PcOut), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  prof_drain(h);
+  const int r = h->hpc->r;
+  if (r < 1 || (r >= rmax && h->hpc->resid > tol)) {
+    CK(peig<RM>(h, nin, W, nin, V, nin, h->wWv, 1e-10));
+    *nvals = nin;
+    return MPDO_OK;
+  }
+  TM* Gs = static_cast<TM*>(h->wGs);
+  TM* Z = static_cast<TM*>(h->wZ);
+  if constexpr (std::is_same<RM, double>::value) {
+    if (f64) {
+      const double2* L = static_cast<const double2*>(h->wL);
+      CK(pgemm<double>(h, OP_C, OP_N, r, r, nin, L, kInnerRmax, 0, L, kInnerRmax, 0, Gs, r, 0, 1));
+      CK(peig<double>(h, r, Gs, r, Z, r, h->wWv, 1e-10));
+      PO(lift<double>(st, r, Z, h->wWv, Gs));
+      CK(pgemm<double>(h, OP_N, OP_N, nin, r, r, L, kInnerRmax, 0, Gs, r, 0, V, nin, 0, 1));
+    } else {
+      const float2* L = static_cast<const float2*>(h->wL);
+      CK((pgram<float, double>(h, OP_C, OP_N, r, r, nin, L, kInnerRmax, L, kInnerRmax, Gs, r)));
+      CK(peig<double>(h, r, Gs, r, Z, r, h->wWv, 1e-10));
+      PO(lift<double>(st, r, Z, h->wWv, Gs));
+      CK(pwide<double>(h, OP_N, OP_N, nin, r, r, L, kInnerRmax, 0, Gs, r, 0, V, nin, 0, 1));
+    }
+  } else {
+    const float2* L = static_cast<const float2*>(h->wL);
+    CK(pgemm<float>(h, OP_C, OP_N, r, r, nin, L, kInnerRmax, 0, L, kInnerRmax, 0, Gs, r, 0, 1));
+    CK(peig<float>(h, r, Gs, r, Z, r, h->wWv, 1e-10));
+    PO(lift<float>(st, r, Z, h->wWv, Gs));
+    CK(pgemm<float>(h, OP_N, OP_N, nin, r, r, L, kInnerRmax, 0, Gs, r, 0, V, nin, 0, 1));
+  }
+  *nvals = r;
+  return MPDO_OK;
 }
 
 // ------------------------------------------------------------------ the update
@@ -280,7 +392,6 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   TM* wH = static_cast<TM*>(h->wH);
   TM* wU = static_cast<TM*>(h->wU);
   TM* wVgen = static_cast<TM*>(h->wVgen);
-  T* wVgenS = static_cast<T*>(h->wVgenS ? h->wVgenS : h->wVgen);
   T* wW = static_cast<T*>(h->wW);
   T* wTmp = static_cast<T*>(h->wTmp);
   T* wQ = static_cast<T*>(h->wQ);
@@ -299,7 +410,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   CK((pgram<RS, RM>(h, OP_N, OP_C, n3, n3, kj * dr, aj, (long)kj * dr, aj, (long)kj * dr, wGj,
                     n3)));
   // a3: left factor from the eigendecomposition of G_i (numerical rank by gtol)
-  CK(peig<RM>(h, n3, wGi, n3, wVg, n3, h->wSig));
+  CK(peig<RM>(h, n3, wGi, n3, wVg, n3, h->wSig, 0.1 * h->gtol));
   PO(gram_mask<RM>(st, n3, h->wSig, h->gtol, wRs, wIrs, h->dsc));
   PO(gram_factor<RM>(st, n3, wVg, wRs, wIrs, wR, wVs, wVr));
   // a4/a5: Phi from the channel and G_j, then H = (I x R) Phi (I x R)^+
@@ -308,7 +419,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
                (long)n3 * n9, 3));
   CK(pgemm<RM>(h, OP_N, OP_C, n9, n3, n3, wX, n9, n3, wR, n3, 0, wH, n9, n3, 3));
   // a6: bond eigenpairs and cut
-  CK(peig<RM>(h, n9, wH, n9, wU, n9, h->wLam));
+  CK(peig<RM>(h, n9, wH, n9, wU, n9, h->wLam, 0.1 * h->htol));
   PO(bond_select<RM>(st, n9, h->wLam, wH, n9, h->htol, chi, h->dsc, h->dstats));
   int rc = read_scalars(h);
   if (rc) return rc;
@@ -316,21 +427,38 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   // a7: split.  Vgen = (I x V sigma^-1/2) U_keep
   CK(pgemm<RM>(h, OP_N, OP_N, n3, keep, n3, wVs, n3, 0, wU, n9, (long)n3 * n9, wVgen, keep,
                (long)n3 * keep, 3));
-  if constexpr (!std::is_same<RS, RM>::value)
-    CK((convert<RM, RS>(st, n9, keep, wVgen, keep, wVgenS, keep)));
-  CK(pgemm<RS>(h, OP_N, OP_N, dl * ki, keep, n3, wM, n3, 0, wVgenS, keep, (long)n3 * keep, wTmp,
-               3L * keep, keep, 3));
   // The left factor A = (M_i x I)(I x V sigma^-1/2) U_keep is an isometry only up to the
   // error of the small-sigma eigenvectors of G_i, amplified by sigma^-1/2.  One
-  // Newton-Schulz polar step (Higham) restores it: A <- A (3I - A^+A)/2, written to wWB.
-  // The centre factor is then the projection of the two-site block onto the kept left
-  // vectors, W_s' = M_i^+ A_s' (= (I x V sigma^1/2) U_keep when the eigenpairs are exact),
-  // so that theta' = A A^+ theta holds to rounding whatever the eigenvector error.
-  {
+  // Newton-Schulz polar step (Higham) restores it: A <- A (3I - A^+A)/2.  The centre
+  // factor is then the projection of the two-site block onto the kept left vectors,
+  // W_s' = M_i^+ A_s' (= (I x V sigma^1/2) U_keep when the eigenpairs are exact), so that
+  // theta' = A A^+ theta holds to rounding whatever the eigenvector error.
+  const int rows = dl * ki * 3;
+  if constexpr (!std::is_same<RS, RM>::value) {
+    // Mixed precision: A, its polar step and W in FP64 from the stored FP32 M_i.  Rounding
+    // M_i Vgen to FP32 before the step would be amplified by sigma^-1/2 of the smallest
+    // kept sigma (down to 1e-13 of the largest here), beyond what one step can repair.
+    TM* aM = static_cast<TM*>(h->wTmp);
+    TM* acM = static_cast<TM*>(h->wAcM);
+    TM* gaM = static_cast<TM*>(h->wGa);
+    TM* polM = static_cast<TM*>(h->wPol);
+    TM* qolM = static_cast<TM*>(h->wQol);
+    CK(pwide<RM>(h, OP_N, OP_N, dl * ki, keep, n3, wM, n3, 0, wVgen, keep, (long)n3 * keep, aM,
+                 3L * keep, keep, 3));
+    CK(pgemm<RM>(h, OP_C, OP_N, keep, keep, rows, aM, keep, 0, aM, keep, 0, gaM, keep, 0, 1));
+    PO(polar_factors<RM>(st, keep, gaM, polM, qolM));
+    CK(pgemm<RM>(h, OP_N, OP_N, rows, keep, keep, aM, keep, 0, polM, keep, 0, acM, keep, 0, 1));
+    // W in FP64 into wVgen (no longer needed), then rounded to the storage precision
+    CK(pwide<RM>(h, OP_C, OP_N, n3, keep, dl * ki, wM, n3, 0, acM, 3L * keep, keep, wVgen, keep,
+                 (long)n3 * keep, 3));
+    CK((convert<RM, RS>(st, n9, keep, wVgen, keep, wW, keep)));
+    CK((convert<RM, RS>(st, rows, keep, acM, keep, wWB, keep)));
+  } else {
     T* wGa = static_cast<T*>(h->wGa);
     T* wPol = static_cast<T*>(h->wPol);
     T* wQol = static_cast<T*>(h->wQol);
-    const int rows = dl * ki * 3;
+    CK(pgemm<RS>(h, OP_N, OP_N, dl * ki, keep, n3, wM, n3, 0, wVgen, keep, (long)n3 * keep,
+                 wTmp, 3L * keep, keep, 3));
     CK(pgemm<RS>(h, OP_C, OP_N, keep, keep, rows, wTmp, keep, 0, wTmp, keep, 0, wGa, keep, 0, 1));
     PO(polar_factors<RS>(st, keep, wGa, wPol, wQol));
     CK(pgemm<RS>(h, OP_N, OP_N, rows, keep, keep, wTmp, keep, 0, wPol, keep, 0, wWB, keep, 0, 1));
@@ -350,9 +478,12 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
     // the inner Gram W = B B^+ has rank <= colsB: diagonalise the smaller dual B^+ B
     const int nc = (int)colsB;
     CK((pgram<RS, RM>(h, OP_C, OP_N, nc, nc, KM, wBp, colsB, wBp, colsB, wWK, nc)));
-    CK(peig<RM>(h, nc, wWK, nc, wVk, nc, h->wWv));
+    int nv;
+    rc = inner_eig<RM>(h, nc, &nv);
+    if (rc) return rc;
     // a9: cut + PPT (FP64 scalars); tr(B^+B) = tr(B B^+)
-    PO(kraus_select<RM>(st, nc, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
+    PO(kraus_select<RM>(st, nv, h->wWv, wWK, nc, h->kcut, kmax, use_ppt, h->wF, h->dsc,
+                        h->dstats));
     rc = read_scalars(h);
     if (rc) return rc;
     kk = h->hsc->kkeep;
@@ -360,9 +491,12 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
     PO((dual_rows<RM, RS>(st, kk, nc, wVk, nc, h->wF, h->wWv, wCn)));
   } else {
     CK((pgram<RS, RM>(h, OP_N, OP_C, KM, KM, colsB, wBp, colsB, wBp, colsB, wWK, KM)));
-    CK(peig<RM>(h, KM, wWK, KM, wVk, KM, h->wWv));
+    int nv;
+    rc = inner_eig<RM>(h, KM, &nv);
+    if (rc) return rc;
     // a9: cut + PPT (FP64 scalars)
-    PO(kraus_select<RM>(st, KM, h->wWv, wWK, h->kcut, kmax, use_ppt, h->wF, h->dsc, h->dstats));
+    PO(kraus_select<RM>(st, nv, h->wWv, wWK, KM, h->kcut, kmax, use_ppt, h->wF, h->dsc,
+                        h->dstats));
     rc = read_scalars(h);
     if (rc) return rc;
     kk = h->hsc->kkeep;
@@ -476,7 +610,9 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
     const mpdo_op& op = layer->ops[k];
     if (!op.ops) return fail(h, MPDO_ERR_ARG, "op " + std::to_string(k) + " has no data");
     if (op.kind == 2) {
-      if (op.site < 0 || op.site > h->n - 2)
+      // uploaded layers may serve any chain length up to the capacity (checked again when
+      // applied); staged layers are applied to the current chain
+      if (op.site < 0 || op.site > (staged ? h->n : h->n_cap) - 2)
         return fail(h, MPDO_ERR_ARG, "two-site op site out of range");
       if (op.n_kraus < 1 || op.n_kraus > h->mmax)
         return fail(h, MPDO_ERR_ARG, "n_kraus " + std::to_string(op.n_kraus) +
@@ -488,7 +624,8 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
                                729 * h->eltm, 729 * h->eltm};
       for (size_t sz : sizes) total = ((total + 15) & ~(size_t)15) + sz;
     } else if (op.kind == 1) {
-      if (op.site < 0 || op.site > h->n - 1) return fail(h, MPDO_ERR_ARG, "one-site op site");
+      if (op.site < 0 || op.site > (staged ? h->n : h->n_cap) - 1)
+        return fail(h, MPDO_ERR_ARG, "one-site op site");
       if (op.n_kraus != 1) return fail(h, MPDO_ERR_ARG, "one-site op needs n_kraus == 1");
       total += 9 * elt;
     } else {
@@ -621,6 +758,10 @@ int read_stats(mpdo_ctx* h, mpdo_trunc_stats* out) {
 
 int run_ops(mpdo_ctx* h, const std::vector<DevOp>& ops, mpdo_trunc_stats* stats, int chi,
             int kmax, int use_ppt) {
+  for (const DevOp& op : ops)
+    if (op.site < 0 || op.site > h->n - (op.kind == 2 ? 2 : 1))
+      return fail(h, MPDO_ERR_ARG, "op site " + std::to_string(op.site) + " outside the chain of " +
+                                       std::to_string(h->n) + " sites");
   int rc = reset_stats(h);
   if (rc) return rc;
   rc = h->dbl     ? apply_ops<double, double>(h, ops, chi, kmax, use_ppt)
@@ -648,13 +789,32 @@ int init_state(mpdo_ctx* h, const double* v) {
 }
 
 // ---------------------------------------------------------------- observables
+// FP64 product of an FP64 environment-side operand and a site tensor of precision RS.
+template <typename RS>
+cudaError_t penv(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<double>* A,
+                 long lda, long sa, const cx<RS>* B, long ldb, long sb, cx<double>* C, long ldc,
+                 long sc, int batch) {
+  if constexpr (std::is_same<RS, double>::value) {
+    return pgemm<double>(h, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch);
+  } else {
+    int pi = prof_begin(h, 0);
+    cudaError_t e = cgemm_dx(h->st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch);
+    prof_end(h, 0, pi, 8.0 * m * n * (double)k * batch);
+    return e;
+  }
+}
+
+// a11: the environments and the energy automata are FP64 whatever the storage precision
+// (FP32 site tensors are read and widened in the GEMMs): an FP32 transfer chain loses
+// ~1e-5 of the trace over 100 sites.
 template <typename R>
 int energy(mpdo_ctx* h, double J, double hx, double bz, double out[6]) {
   using T = cx<R>;
+  using TD = cx<double>;
   cudaStream_t st = h->st;
   const long chi = h->chi, K = h->kmax;
   const long env = chi * chi, fsz = chi * 3 * K * chi;
-  size_t need = (2 * 6 * env + 2 * 6 * fsz) * sizeof(T) + 512;
+  size_t need = (2 * 6 * env + 2 * 6 * fsz) * sizeof(TD) + 512;
   if (h->obs_bytes < need) {
     if (h->obs) cudaFree(h->obs);
     h->obs = nullptr;
@@ -662,33 +822,34 @@ int energy(mpdo_ctx* h, double J, double hx, double bz, double out[6]) {
     if (ce != cudaSuccess) { cudaGetLastError(); h->obs_bytes = 0; return fail(h, MPDO_ERR_OOM, "energy buffers"); }
     h->obs_bytes = need;
   }
-  T* ebuf[2] = {static_cast<T*>(h->obs), static_cast<T*>(h->obs) + 6 * env};
-  T* F = ebuf[1] + 6 * env;
-  T* G = F + 6 * fsz;
+  TD* ebuf[2] = {static_cast<TD*>(h->obs), static_cast<TD*>(h->obs) + 6 * env};
+  TD* F = ebuf[1] + 6 * env;
+  TD* G = F + 6 * fsz;
   // initial envs (1x1): E0 = 1, EZ = 0, E1 = 0 for both automata
-  T init[6] = {one<R>(), zero<R>(), zero<R>(), one<R>(), zero<R>(), zero<R>()};
+  TD init[6] = {one<double>(), zero<double>(), zero<double>(),
+                one<double>(), zero<double>(), zero<double>()};
   for (int a = 0; a < 6; ++a)
-    CK(cudaMemcpyAsync(ebuf[0] + a * env, &init[a], sizeof(T), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ebuf[0] + a * env, &init[a], sizeof(TD), cudaMemcpyHostToDevice, st));
   int cur = 0;
   for (int s = 0; s < h->n; ++s) {
     const int dl = h->bond[s], k = h->kd[s], dr = h->bond[s + 1];
     const T* A = static_cast<const T*>(h->site(s));
     const long cols = 3L * k * dr;
     // F[a] = E[a]^T A   (dl x cols)
-    CK(pgemm<R>(h, OP_T, OP_N, dl, (int)cols, dl, ebuf[cur], dl, env, A, cols, 0, F, cols, fsz,
-                6));
-    PO(energy_mix<R>(st, dl, (int)(k * dr), F, fsz, G, fsz, J, hx, bz));
+    CK(penv<R>(h, OP_T, OP_N, dl, (int)cols, dl, ebuf[cur], dl, env, A, cols, 0, F, cols, fsz,
+               6));
+    PO(energy_mix<double>(st, dl, (int)(k * dr), F, fsz, G, fsz, J, hx, bz));
     // E'[a] = G[a]^T conj(A2), both as (dl*3*k) x dr
-    CK(pgemm<R>(h, OP_T, OP_R, dr, dr, dl * 3 * k, G, dr, fsz, A, dr, 0, ebuf[1 - cur], dr,
-                env, 6));
+    CK(penv<R>(h, OP_T, OP_R, dr, dr, dl * 3 * k, G, dr, fsz, A, dr, 0, ebuf[1 - cur], dr, env,
+               6));
     cur = 1 - cur;
   }
-  T res[6];
+  TD res[6];
   for (int a = 0; a < 6; ++a)
-    CK(cudaMemcpyAsync(&res[a], ebuf[cur] + a * env, sizeof(T), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&res[a], ebuf[cur] + a * env, sizeof(TD), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   prof_drain(h);
-  for (int a = 0; a < 6; ++a) out[a] = (double)res[a].x;
+  for (int a = 0; a < 6; ++a) out[a] = res[a].x;
   return MPDO_OK;
 }
 
@@ -808,9 +969,11 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   // FP64 Grams of FP32 tensors the floor is the rounding of the tensors themselves
   // (relative 6e-8 per entry, i.e. ~4e-15 on lambda), taken as eps = 1e-14.
   const double eps = h->dbl ? 1e-16 : h->mixed ? 1e-14 : 6e-8;
-  h->gtol = 10 * eps;
   double sv = cfg->sv_cutoff > 0 ? cfg->sv_cutoff : 1e-14;
   h->htol = std::max(sv * sv, 10 * eps);
+  // The left factor's rank cut: directions of G_i below gtol carry less than gtol of the
+  // block's weight each; in mixed mode they need not be resolved below 1% of the bond cut.
+  h->gtol = h->mixed ? std::max(10 * eps, 0.01 * h->htol) : 10 * eps;
   double kc = cfg->kraus_cutoff > 0 ? cfg->kraus_cutoff : 1e-14;
   h->kcut = std::max(kc, std::sqrt(10 * eps));
   h->max_sweeps = (h->dbl || h->mixed) ? 30 : 20;
@@ -829,14 +992,15 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
       (rc = B(&h->wVg, n3 * n3)) || (rc = B(&h->wR, n3 * n3)) || (rc = B(&h->wVs, n3 * n3)) ||
       (rc = B(&h->wVr, n3 * n3)) || (rc = B(&h->wPhi, n9 * n9)) || (rc = B(&h->wX, n9 * n9)) ||
       (rc = B(&h->wH, n9 * n9)) || (rc = B(&h->wU, n9 * n9)) || (rc = B(&h->wVgen, n9 * D)) ||
-      (rc = A(&h->wW, n9 * D)) || (rc = A(&h->wTmp, D * K * 3 * D)) ||
+      (rc = A(&h->wW, n9 * D)) || (rc = B(&h->wTmp, D * K * 3 * D)) ||
       (rc = A(&h->wQ, D * 3 * M * n3)) || (rc = A(&h->wWB, D * 3 * M * K * D)) ||
       (rc = A(&h->wBp, D * 3 * M * K * D)) || (rc = B(&h->wWK, KM * KM)) ||
       (rc = B(&h->wVk, KM * KM)) || (rc = A(&h->wVks, KM * K)) || (rc = A(&h->wCn, K * D * 3 * D)))
     return rc;
-  if ((rc = A(&h->wPol, D * D)) || (rc = A(&h->wQol, D * D)) || (rc = A(&h->wGa, D * D)))
+  // the left factor and its polar step run in the Gram precision in mixed mode
+  if ((rc = B(&h->wPol, D * D)) || (rc = B(&h->wQol, D * D)) || (rc = B(&h->wGa, D * D)))
     return rc;
-  if (h->mixed && (rc = A(&h->wVgenS, n9 * D))) return rc;
+  if (h->mixed && (rc = B(&h->wAcM, D * K * 3 * D))) return rc;
   const size_t rsz = em / 2;
   if ((rc = alloc_dev(hp, &h->wRs, n3 * rsz)) || (rc = alloc_dev(hp, &h->wIrs, n3 * rsz)) ||
       (rc = alloc_dev(hp, (void**)&h->wSig, n3 * 8)) || (rc = alloc_dev(hp, (void**)&h->wLam, n9 * 8)) ||
@@ -847,6 +1011,21 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   if ((rc = alloc_dev(hp, &h->eigmem, eb))) return rc;
   if (em == 16) eig_work_bind<double>(h->eig64, h->eigmem, ncap);
   else eig_work_bind<float>(h->eig32, h->eigmem, ncap);
+  if ((rc = alloc_dev(hp, &h->wL, (size_t)KM * kInnerRmax * em)) ||
+      (rc = B(&h->wGs, (size_t)kInnerRmax * kInnerRmax)) ||
+      (rc = B(&h->wZ, (size_t)kInnerRmax * kInnerRmax)) ||
+      (rc = alloc_dev(hp, (void**)&h->dpc, sizeof(mpdo_ctx::PcOut))))
+    return rc;
+  // FP32 copy of an FP64 inner Gram for the pivoted Cholesky (FP64 and mixed modes)
+  if (em == 16 && (rc = alloc_dev(hp, &h->wW32, (size_t)KM * KM * 8))) return rc;
+  if (cudaMallocHost((void**)&h->hpc, sizeof(mpdo_ctx::PcOut)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, MPDO_ERR_OOM, "pinned host allocation");
+  }
+  if (h->mixed) {
+    if ((rc = alloc_dev(hp, &h->mixmem, mix_work_bytes(ncap)))) return rc;
+    mix_work_bind(h->mixw, h->mixmem, ncap);
+  }
   if ((rc = alloc_dev(hp, (void**)&h->dsc, sizeof(StepScalars))) ||
       (rc = alloc_dev(hp, (void**)&h->dstats, sizeof(DevStats))))
     return rc;
@@ -1062,6 +1241,7 @@ int mpdo_destroy(mpdo_t h) {
   if (h->obs) cudaFree(h->obs);
   if (h->hsc) cudaFreeHost(h->hsc);
   if (h->hstats) cudaFreeHost(h->hstats);
+  if (h->hpc) cudaFreeHost(h->hpc);
   if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
   return MPDO_OK;
@@ -1118,6 +1298,20 @@ int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, 
   if (n < 1 || n > 4096 || !a || !v || !w) return fail(nullptr, MPDO_ERR_ARG, "bad heig arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void* mem = nullptr;
+  if (prec == 2) {
+    // mixed-precision solver on an FP64 matrix (resolved down to 1e-14 of the largest)
+    void* mm = nullptr;
+    if (cudaMalloc(&mm, mix_work_bytes(n)) != cudaSuccess) { cudaGetLastError(); return fail(nullptr, MPDO_ERR_OOM, "heig work"); }
+    MixWork mw;
+    mix_work_bind(mw, mm, n);
+    int lv = 0;
+    cudaError_t e2 = heig_mixed(st, n, (const double2*)a, n, (double2*)v, n, w, 1e-14, mw, &lv);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    cudaFree(mm);
+    if (e2 != cudaSuccess) return fail(nullptr, MPDO_ERR_CUDA, cudaGetErrorString(e2));
+    if (sweeps) *sweeps = lv;
+    return MPDO_OK;
+  }
   size_t bytes = prec == 0 ? eig_work_bytes<double>(n) : eig_work_bytes<float>(n);
   if (cudaMalloc(&mem, bytes) != cudaSuccess) { cudaGetLastError(); return fail(nullptr, MPDO_ERR_OOM, "heig work"); }
   cudaError_t e;

@@ -10,12 +10,12 @@ namespace mpdo {
 namespace {
 constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
 
-// Inputs of precision RI, products and sums in R (RI = float, R = double: the FP32
-// products are exact in FP64 and the sums carry FP64 rounding only).
-template <typename RI, typename R>
+// Inputs of precisions RA and RB, products and sums in R (float inputs, R = double: the
+// FP32 products are exact in FP64 and the sums carry FP64 rounding only).
+template <typename RA, typename RB, typename R>
 __global__ void __launch_bounds__(NT) cgemm_kernel(
-    int M, int N, int K, const cx<RI>* __restrict__ A, long sam, long sak, long sab, int conja,
-    const cx<RI>* __restrict__ B, long sbk, long sbn, long sbb, int conjb, cx<R>* C, long scm,
+    int M, int N, int K, const cx<RA>* __restrict__ A, long sam, long sak, long sab, int conja,
+    const cx<RB>* __restrict__ B, long sbk, long sbn, long sbb, int conjb, cx<R>* C, long scm,
     long scn, long scb, cx<R> alpha, cx<R> beta, int use_beta) {
   using T = cx<R>;
   __shared__ T As[BK][BM + 1];
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(NT) cgemm_kernel(
       int gm = m0 + mi, gk = k0 + ki;
       T v = mkc<R>(0, 0);
       if (gm < M && gk < K) {
-        cx<RI> t = A[gm * sam + gk * sak];
+        cx<RA> t = A[gm * sam + gk * sak];
         v = mkc<R>((R)t.x, conja ? -(R)t.y : (R)t.y);
       }
       As[ki][mi] = v;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(NT) cgemm_kernel(
       int gn = n0 + ni, gk = k0 + ki;
       T v = mkc<R>(0, 0);
       if (gn < N && gk < K) {
-        cx<RI> t = B[gk * sbk + gn * sbn];
+        cx<RB> t = B[gk * sbk + gn * sbn];
         v = mkc<R>((R)t.x, conjb ? -(R)t.y : (R)t.y);
       }
       Bs[ki][ni] = v;
@@ -91,11 +91,61 @@ __global__ void __launch_bounds__(NT) cgemm_kernel(
     }
   }
 }
+// 16 x 16 output tiles, one element per thread: for small products, where 64 x 64 tiles
+// would occupy only a few SMs (FP64 runs at 2 FMA per clock per SM, so spreading matters).
+constexpr int ST = 16;
+template <typename RA, typename RB, typename R>
+__global__ void __launch_bounds__(ST * ST) cgemm_small_kernel(
+    int M, int N, int K, const cx<RA>* __restrict__ A, long sam, long sak, long sab, int conja,
+    const cx<RB>* __restrict__ B, long sbk, long sbn, long sbb, int conjb, cx<R>* C, long scm,
+    long scn, long scb, cx<R> alpha, cx<R> beta, int use_beta) {
+  using T = cx<R>;
+  __shared__ T As[ST][ST + 1];   // [k][m]
+  __shared__ T Bs[ST][ST + 1];   // [k][n]
+  const int tx = threadIdx.x % ST, ty = threadIdx.x / ST;
+  const int m0 = blockIdx.y * ST, n0 = blockIdx.x * ST;
+  const long bz = blockIdx.z;
+  A += bz * sab;
+  B += bz * sbb;
+  C += bz * scb;
+  T acc = mkc<R>(0, 0);
+  for (int k0 = 0; k0 < K; k0 += ST) {
+    {
+      // A tile: thread (ty, tx) loads m = m0 + ty, k = k0 + tx
+      int gm = m0 + ty, gk = k0 + tx;
+      T v = mkc<R>(0, 0);
+      if (gm < M && gk < K) {
+        cx<RA> t = A[gm * sam + gk * sak];
+        v = mkc<R>((R)t.x, conja ? -(R)t.y : (R)t.y);
+      }
+      As[tx][ty] = v;
+      // B tile: k = k0 + ty, n = n0 + tx
+      int gk2 = k0 + ty, gn = n0 + tx;
+      T u = mkc<R>(0, 0);
+      if (gn < N && gk2 < K) {
+        cx<RB> t = B[gk2 * sbk + gn * sbn];
+        u = mkc<R>((R)t.x, conjb ? -(R)t.y : (R)t.y);
+      }
+      Bs[ty][tx] = u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < ST; ++kk) cfma(acc, As[kk][ty], Bs[kk][tx]);
+    __syncthreads();
+  }
+  const int gm = m0 + ty, gn = n0 + tx;
+  if (gm < M && gn < N) {
+    T v = cmul(alpha, acc);
+    T* p = C + gm * scm + gn * scn;
+    if (use_beta) v = cadd(v, cmul(beta, *p));
+    *p = v;
+  }
+}
 }  // namespace
 
-template <typename RI, typename R>
-cudaError_t cgemm_impl(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<RI>* A,
-                       long lda, long sa, const cx<RI>* B, long ldb, long sb, cx<R>* C, long ldc,
+template <typename RA, typename RB, typename R>
+cudaError_t cgemm_impl(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<RA>* A,
+                       long lda, long sa, const cx<RB>* B, long ldb, long sb, cx<R>* C, long ldc,
                        long sc, int batch, cx<R> alpha, cx<R> beta) {
   if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
   long sam, sak, sbk, sbn;
@@ -106,11 +156,20 @@ cudaError_t cgemm_impl(cudaStream_t st, int opa, int opb, int m, int n, int k, c
   if (k <= 0) {  // C = beta C: run with K = 0 (acc = 0)
     k = 0;
   }
+  const long big_tiles = (long)((n + BN - 1) / BN) * ((m + BM - 1) / BM) * batch;
+  const bool small = big_tiles < 152;
   for (int b0 = 0; b0 < batch; b0 += 65535) {
     int nb = batch - b0 < 65535 ? batch - b0 : 65535;
-    dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, nb);
     count_launch();
-    cgemm_kernel<RI, R><<<grid, NT, 0, st>>>(m, n, k, A + (long)b0 * sa, sam, sak, sa, conja,
+    if (small) {
+      dim3 g2((n + ST - 1) / ST, (m + ST - 1) / ST, nb);
+      cgemm_small_kernel<RA, RB, R><<<g2, ST * ST, 0, st>>>(
+          m, n, k, A + (long)b0 * sa, sam, sak, sa, conja, B + (long)b0 * sb, sbk, sbn, sb, conjb,
+          C + (long)b0 * sc, ldc, 1, sc, alpha, beta, use_beta);
+      continue;
+    }
+    dim3 grid((n + BN - 1) / BN, (m + BM - 1) / BM, nb);
+    cgemm_kernel<RA, RB, R><<<grid, NT, 0, st>>>(m, n, k, A + (long)b0 * sa, sam, sak, sa, conja,
                                               B + (long)b0 * sb, sbk, sbn, sb, conjb,
                                               C + (long)b0 * sc, ldc, 1, sc, alpha, beta,
                                               use_beta);
@@ -122,15 +181,29 @@ template <typename R>
 cudaError_t cgemm(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<R>* A,
                   long lda, long sa, const cx<R>* B, long ldb, long sb, cx<R>* C, long ldc,
                   long sc, int batch, cx<R> alpha, cx<R> beta) {
-  return cgemm_impl<R, R>(st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch,
+  return cgemm_impl<R, R, R>(st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch,
                           alpha, beta);
 }
 
+template <typename RB>
 cudaError_t cgemm_wide(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<float>* A,
-                       long lda, long sa, const cx<float>* B, long ldb, long sb, cx<double>* C,
+                       long lda, long sa, const cx<RB>* B, long ldb, long sb, cx<double>* C,
                        long ldc, long sc, int batch) {
-  return cgemm_impl<float, double>(st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc,
-                                   batch, mkc<double>(1, 0), mkc<double>(0, 0));
+  return cgemm_impl<float, RB, double>(st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc,
+                                       batch, mkc<double>(1, 0), mkc<double>(0, 0));
+}
+template cudaError_t cgemm_wide<float>(cudaStream_t, int, int, int, int, int, const float2*,
+                                       long, long, const float2*, long, long, double2*, long,
+                                       long, int);
+template cudaError_t cgemm_wide<double>(cudaStream_t, int, int, int, int, int, const float2*,
+                                        long, long, const double2*, long, long, double2*, long,
+                                        long, int);
+
+cudaError_t cgemm_dx(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<double>* A,
+                     long lda, long sa, const cx<float>* B, long ldb, long sb, cx<double>* C,
+                     long ldc, long sc, int batch) {
+  return cgemm_impl<double, float, double>(st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc,
+                                           sc, batch, mkc<double>(1, 0), mkc<double>(0, 0));
 }
 
 template cudaError_t cgemm<double>(cudaStream_t, int, int, int, int, int, const double2*, long,

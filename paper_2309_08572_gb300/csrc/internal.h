@@ -13,10 +13,17 @@ cudaError_t cgemm(cudaStream_t st, int opa, int opb, int m, int n, int k, const 
                   long lda, long sa, const cx<R>* B, long ldb, long sb, cx<R>* C, long ldc,
                   long sc, int batch, cx<R> alpha, cx<R> beta);
 
-// C = op(A) op(B) with FP32 inputs and FP64 products and sums (alpha 1, beta 0).
+// C = op(A) op(B) with an FP32 A, B of precision RB (float or double), FP64 products and
+// sums (alpha 1, beta 0).
+template <typename RB>
 cudaError_t cgemm_wide(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<float>* A,
-                       long lda, long sa, const cx<float>* B, long ldb, long sb, cx<double>* C,
+                       long lda, long sa, const cx<RB>* B, long ldb, long sb, cx<double>* C,
                        long ldc, long sc, int batch);
+
+// C = op(A) op(B) with an FP64 A and an FP32 B, FP64 products and sums (alpha 1, beta 0).
+cudaError_t cgemm_dx(cudaStream_t st, int opa, int opb, int m, int n, int k, const cx<double>* A,
+                     long lda, long sa, const cx<float>* B, long ldb, long sb, cx<double>* C,
+                     long ldc, long sc, int batch);
 
 // Workspace of the Hermitian eigensolver (capacity n_cap).
 template <typename R>
@@ -40,5 +47,22 @@ void eig_work_bind(EigWork<R>& w, void* base, int n_cap);
 template <typename R>
 cudaError_t heig(cudaStream_t st, int n, const cx<R>* a, long lda, cx<R>* v, long ldv,
                  double* w, EigWork<R>& work, int max_sweeps);
+
+// Workspace of the mixed-precision eigensolver (capacity n_cap).
+struct MixWork {
+  int n_cap = 0;
+  double2 *x = nullptr, *z = nullptr, *z2 = nullptr, *t = nullptr, *s = nullptr, *g = nullptr,
+          *ie = nullptr;
+  float2 *a32 = nullptr, *y32 = nullptr;
+  double *lam = nullptr, *w32 = nullptr, *scan = nullptr;
+  EigWork<float> ew;
+};
+size_t mix_work_bytes(int n_cap);
+void mix_work_bind(MixWork& w, void* base, int n_cap);
+// Eigenpairs of the FP64 Hermitian matrix a (n x n, row-major, lda), descending, resolved
+// down to floor * lambda_max: FP32 Jacobi levels with FP64 refinement.  Synchronises the
+// stream once per level.
+cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, double2* v, long ldv,
+                       double* w, double floor, MixWork& wk, int* levels_out);
 
 }  // namespace mpdo

@@ -227,8 +227,8 @@ __global__ void make_q_kernel(int dm, int keep, int m_ops, const cx<R>* __restri
 // Writes f[k] = sqrt(Lambda~_k / w_k) for k < kk.
 template <typename R>
 __global__ void kraus_select_kernel(int n, const double* __restrict__ w, const cx<R>* __restrict__ wm,
-                                    double kcut, int kmax, int use_ppt, double* f, StepScalars* sc,
-                                    DevStats* st) {
+                                    int ntr, double kcut, int kmax, int use_ppt, double* f,
+                                    StepScalars* sc, DevStats* st) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double w0 = w[0] > 0 ? w[0] : 0.0;
   bool bad = !(w0 > 0.0) || !isfinite(w0);
@@ -239,9 +239,9 @@ __global__ void kraus_select_kernel(int n, const double* __restrict__ w, const c
   }
   if (kk < 1) kk = 1;
   double sum = 0, sq = 0, sumk = 0, sqk = 0;
+  for (int i = 0; i < ntr; ++i) sum += (double)wm[(long)i * ntr + i].x;   // trace = total weight
   for (int i = 0; i < n; ++i) {
     double v = w[i] > 0 ? w[i] : 0.0;
-    sum += (double)wm[(long)i * n + i].x;   // trace of the Gram = total weight
     sq += v * v;
     if (i < kk) { sumk += v; sqk += v * v; }
   }
@@ -448,6 +448,110 @@ __global__ void dual_rows_kernel(int kk, int cols, const cx<R>* __restrict__ y, 
   }
 }
 
+// Pivoted Cholesky of the Hermitian PSD n x n matrix w (precision R, n <= 1024, one CTA):
+// W ~ L L^+ with L n x r (row-major, row stride lr), greedy diagonal pivoting, stopping once
+// the largest remaining diagonal is <= tol * tr W or after rmax (<= 128) columns.
+// *rout = r; *resid = largest remaining diagonal / tr W.
+template <typename R>
+__global__ void __launch_bounds__(1024) pchol_kernel(int n, const cx<R>* __restrict__ w,
+                                                     int rmax, double tol, cx<R>* L, int lr,
+                                                     int* rout, double* resid) {
+  using T = cx<R>;
+  __shared__ double d[1024];
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ T lp[128];
+  __shared__ int s_p;
+  __shared__ double s_dp, s_tr;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  double tp = 0.0;
+  for (int i = tid; i < n; i += blockDim.x) {
+    double v = (double)w[(long)i * n + i].x;
+    d[i] = v > 0 ? v : 0.0;
+    tp += d[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) tp += __shfl_xor_sync(0xffffffffu, tp, o);
+  if (lane == 0) rv[wid] = tp;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0;
+    for (int k = 0; k < nw; ++k) t += rv[k];
+    s_tr = t;
+  }
+  __syncthreads();
+  int r = 0;
+  double last = 0.0;
+  for (int j = 0; j < rmax; ++j) {
+    double bv = -1.0;
+    int bi = -1;
+    for (int i = tid; i < n; i += blockDim.x)
+      if (d[i] > bv) { bv = d[i]; bi = i; }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { rv[wid] = bv; ri[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = -1.0;
+      int p = -1;
+      for (int k = 0; k < nw; ++k)
+        if (rv[k] > b) { b = rv[k]; p = ri[k]; }
+      s_dp = b;
+      s_p = p;
+    }
+    __syncthreads();
+    const double dp = s_dp;
+    const int p = s_p;
+    last = dp;
+    if (!(dp > tol * s_tr) || p < 0) break;
+    for (int k = tid; k < j; k += blockDim.x) lp[k] = L[(long)p * lr + k];
+    __syncthreads();
+    const R inv = (R)(1.0 / sqrt(dp));
+    for (int i = tid; i < n; i += blockDim.x) {
+      T acc = w[(long)i * n + p];
+      const T* li = L + (long)i * lr;
+      for (int k = 0; k < j; ++k) {
+        T a = li[k], b = lp[k];
+        // acc -= a * conj(b)
+        acc.x -= a.x * b.x + a.y * b.y;
+        acc.y -= a.y * b.x - a.x * b.y;
+      }
+      T lij = mkc<R>(acc.x * inv, acc.y * inv);
+      if (i == p) lij = mkc<R>((R)sqrt(dp), R(0));
+      L[(long)i * lr + j] = lij;
+      double nd = (i == p) ? 0.0 : d[i] - ((double)lij.x * lij.x + (double)lij.y * lij.y);
+      d[i] = nd > 0 ? nd : 0.0;
+    }
+    __syncthreads();
+    r = j + 1;
+    last = 0.0;
+  }
+  if (tid == 0) {
+    if (r == rmax) {
+      double b = 0.0;
+      for (int i = 0; i < n; ++i) b = fmax(b, d[i]);
+      last = b;
+    }
+    *rout = r;
+    *resid = s_tr > 0 ? last / s_tr : 0.0;
+  }
+}
+
+// zs[i][c] = z[i][c] / sqrt(s_c) (0 where s_c <= 0): eigenvectors of L L^+ from those of L^+ L
+template <typename R>
+__global__ void lift_kernel(int r, const cx<R>* __restrict__ z, const double* __restrict__ s,
+                            cx<R>* zs) {
+  long total = (long)r * r;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    int c = (int)(e % r);
+    double sc = s[c] > 0 ? 1.0 / sqrt(s[c]) : 0.0;
+    zs[e] = cscale(z[e], (R)sc);
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launchers
@@ -545,10 +649,11 @@ cudaError_t make_q(cudaStream_t st, int dm, int keep, int m_ops, const cx<R>* w,
   return cudaGetLastError();
 }
 template <typename R>
-cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, double kcut,
-                         int kmax, int use_ppt, double* f, StepScalars* sc, DevStats* ds) {
+cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, int ntr,
+                         double kcut, int kmax, int use_ppt, double* f, StepScalars* sc,
+                         DevStats* ds) {
   count_launch();
-  kraus_select_kernel<R><<<1, 32, 0, st>>>(n, w, wm, kcut, kmax, use_ppt, f, sc, ds);
+  kraus_select_kernel<R><<<1, 32, 0, st>>>(n, w, wm, ntr, kcut, kmax, use_ppt, f, sc, ds);
   return cudaGetLastError();
 }
 template <typename R, typename RO>
@@ -591,6 +696,27 @@ cudaError_t dual_rows(cudaStream_t st, int kk, int cols, const cx<R>* y, long ld
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t pchol(cudaStream_t st, int n, const cx<R>* w, int rmax, double tol, cx<R>* L, int lr,
+                  int* rout, double* resid) {
+  if (n < 1 || n > 1024 || rmax < 1 || rmax > 128) return cudaErrorInvalidValue;
+  count_launch();
+  pchol_kernel<R><<<1, 1024, 0, st>>>(n, w, rmax, tol, L, lr, rout, resid);
+  return cudaGetLastError();
+}
+template cudaError_t pchol<float>(cudaStream_t, int, const float2*, int, double, float2*, int,
+                                  int*, double*);
+template cudaError_t pchol<double>(cudaStream_t, int, const double2*, int, double, double2*, int,
+                                   int*, double*);
+template <typename R>
+cudaError_t lift(cudaStream_t st, int r, const cx<R>* z, const double* s, cx<R>* zs) {
+  count_launch();
+  lift_kernel<R><<<nblocks((long)r * r), 256, 0, st>>>(r, z, s, zs);
+  return cudaGetLastError();
+}
+template cudaError_t lift<double>(cudaStream_t, int, const double2*, const double*, double2*);
+template cudaError_t lift<float>(cudaStream_t, int, const float2*, const double*, float2*);
+
 #define INST(R)                                                                               \
   template cudaError_t swap12<cx<R>>(cudaStream_t, long, long, long, long, const cx<R>*,     \
                                      cx<R>*);                                               \
@@ -609,8 +735,8 @@ cudaError_t dual_rows(cudaStream_t st, int kk, int cols, const cx<R>* y, long ld
                                      long, double, double, double);                         \
   template cudaError_t bond_select<R>(cudaStream_t, int, const double*, const cx<R>*, long,  \
                                       double, int, StepScalars*, DevStats*);                 \
-  template cudaError_t kraus_select<R>(cudaStream_t, int, const double*, const cx<R>*, double, \
-                                       int, int, double*, StepScalars*, DevStats*);          \
+  template cudaError_t kraus_select<R>(cudaStream_t, int, const double*, const cx<R>*, int,   \
+                                       double, int, int, double*, StepScalars*, DevStats*);  \
   template cudaError_t polar_factors<R>(cudaStream_t, int, const cx<R>*, cx<R>*, cx<R>*);   \
   template cudaError_t sample_pick<R>(cudaStream_t, int, int, const cx<R>*, const cx<R>*,   \
                                       uint64_t, int, int, int, cx<R>*, uint8_t*, double*, int);

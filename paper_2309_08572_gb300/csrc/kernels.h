@@ -36,9 +36,19 @@ cudaError_t dual_rows(cudaStream_t st, int kk, int cols, const cx<R>* y, long ld
                       const double* w, cx<RO>* out);
 template <typename R>
 cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<R>* qm);
+// n eigenvalues w (descending); the total weight is the trace of wm (ntr x ntr)
 template <typename R>
-cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, double kcut,
-                         int kmax, int use_ppt, double* f, StepScalars* sc, DevStats* ds);
+cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, int ntr,
+                         double kcut, int kmax, int use_ppt, double* f, StepScalars* sc,
+                         DevStats* ds);
+// Pivoted Cholesky W ~ L L^+ of a Hermitian PSD matrix (n <= 1024, rmax <= 128); device
+// outputs: L (n x r, row stride lr), *rout = r, *resid = remaining diag max / tr W.
+template <typename R>
+cudaError_t pchol(cudaStream_t st, int n, const cx<R>* w, int rmax, double tol, cx<R>* L, int lr,
+                  int* rout, double* resid);
+// zs = z diag(s^-1/2) (r x r)
+template <typename R>
+cudaError_t lift(cudaStream_t st, int r, const cx<R>* z, const double* s, cx<R>* zs);
 template <typename R, typename RO>
 cudaError_t scale_vk(cudaStream_t st, int n, int kk, const cx<R>* v, long ldv, const double* f,
                      cx<RO>* out);
