@@ -300,7 +300,8 @@ def run_ours(args):
     g.profile(0)
     dom = max(range(3), key=lambda k: prof[k]["ms"])
     names = {0: "complex GEMM (cgemm_kernel)",
-             1: "Jacobi eigensolver (jacobi_smem_kernel / jacobi_coop_kernel)",
+             1: "eigensolver (jacobi_smem_kernel sweeps; mixed mode: FP32 sweeps + FP64 "
+                "refinement products)",
              2: "other kernels"}
 
     # timed region: K steps (each a batch of circuits run concurrently), events around

@@ -237,8 +237,9 @@ cudaError_t peig(mpdo_ctx* h, int n, const cx<R>* a, long lda, cx<R>* v, long ld
     // mixed mode: FP32 sweeps with FP64 refinement while the sweeps fit one CTA's shared
     // memory; larger problems take the FP64 solver
     if (h->mixed && n <= kMixedEigMax) {
-      e = heig_mixed(h->st, n, a, lda, v, ldv, w, floor, h->mixw, nullptr);
-      prof_end(h, 1, pi, 0.0);
+      double fl = 0.0;
+      e = heig_mixed(h->st, n, a, lda, v, ldv, w, floor, h->mixw, nullptr, &fl);
+      prof_end(h, 1, pi, fl);
       return e;
     }
   }
@@ -248,7 +249,7 @@ cudaError_t peig(mpdo_ctx* h, int n, const cx<R>* a, long lda, cx<R>* v, long ld
     int slot = h->prof_slot++;
     e = cudaMemcpyAsync(&h->prof_counts[slot], eigw<R>(h).counters + 3, sizeof(int),
                         cudaMemcpyDeviceToHost, h->st);
-    prof_end(h, 1, pi, 0.0, slot, 8.0 * 3 * 256 * (double)eig_padded_n(n));
+    prof_end(h, 1, pi, 0.0, slot, eig_flops_per_count(n, std::is_same<R, double>::value));
   } else {
     prof_end(h, 1, pi, 0.0);
   }

@@ -144,7 +144,11 @@ void mix_work_bind(MixWork& w, void* base, int n_cap) {
 }
 
 cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, double2* v, long ldv,
-                       double* w, double floor, MixWork& wk, int* levels_out) {
+                       double* w, double floor, MixWork& wk, int* levels_out,
+                       double* flops_out) {
+  double flops = 0.0;
+  auto gf = [&](int mm, int nn, int kk) { flops += 8.0 * mm * nn * (double)kk; };
+  int hcnt[4];
   if (n <= 0) return cudaSuccess;
   if (n > wk.n_cap) return cudaErrorInvalidValue;
   int m = n, off = 0, level = 0;
@@ -157,6 +161,8 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
     if (level > 0) {
       MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, wk.x, m, wk.t, m));
       MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, m, n, wk.x, m, wk.t, m, wk.s, m));
+      gf(n, m, n);
+      gf(m, m, n);
       B = wk.s;
       ldbm = m;
     }
@@ -168,6 +174,7 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
     } else {
       MPDO_CUDA_TRY((convert<float, double>(st, m, m, wk.y32, m, wk.ie, m)));
       MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, m, wk.x, m, wk.ie, m, wk.z, m));
+      gf(n, m, m);
     }
     for (int pass = 0; pass < kPasses; ++pass) {
       MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, wk.z, m, wk.t, m));
@@ -188,6 +195,10 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
                                                     wk.ie);
       MPDO_CUDA_TRY(cudaGetLastError());
       MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, m, wk.z, m, wk.ie, m, wk.z2, m));
+      gf(n, m, n);
+      gf(m, m, n);
+      gf(m, m, n);
+      gf(n, m, m);
       std::swap(wk.z, wk.z2);
     }
     // Rayleigh quotients of the refined vectors and the split of this level
@@ -197,8 +208,13 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
     count_launch();
     mix_scan_kernel<<<1, 1024, 0, st>>>(m, wk.s, wk.g, wk.lam, wk.scan);
     MPDO_CUDA_TRY(cudaGetLastError());
+    gf(n, m, n);
+    gf(m, m, n);
+    gf(m, m, n);
     MPDO_CUDA_TRY(cudaMemcpyAsync(hscan, wk.scan, sizeof(hscan), cudaMemcpyDeviceToHost, st));
+    MPDO_CUDA_TRY(cudaMemcpyAsync(hcnt, wk.ew.counters, sizeof(hcnt), cudaMemcpyDeviceToHost, st));
     MPDO_CUDA_TRY(cudaStreamSynchronize(st));
+    flops += hcnt[3] * eig_flops_per_count(m, false);
     int nl = (int)hscan[1];
     const bool last = (nl >= m) || level + 1 >= kMaxLevels || !(hscan[2] > floor * lam0) ||
                       nl == 0;
@@ -217,6 +233,7 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
     m = mr;
   }
   if (levels_out) *levels_out = level + 1;
+  if (flops_out) *flops_out = flops;
   return cudaSuccess;
 }
 

@@ -39,6 +39,7 @@ size_t eig_work_bytes(int n_cap);
 // padded size used by the eigensolver; each active pair-round of the block Jacobi does
 // 3 * 16 * 16 * padded_n complex multiply-adds (rows, columns and eigenvectors)
 int eig_padded_n(int n);
+double eig_flops_per_count(int n, bool fp64);
 template <typename R>
 void eig_work_bind(EigWork<R>& w, void* base, int n_cap);
 
@@ -62,7 +63,9 @@ void mix_work_bind(MixWork& w, void* base, int n_cap);
 // Eigenpairs of the FP64 Hermitian matrix a (n x n, row-major, lda), descending, resolved
 // down to floor * lambda_max: FP32 Jacobi levels with FP64 refinement.  Synchronises the
 // stream once per level.
+// *flops_out (may be NULL): executed flops (FP32 rotations plus FP64 products).
 cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, double2* v, long ldv,
-                       double* w, double floor, MixWork& wk, int* levels_out);
+                       double* w, double floor, MixWork& wk, int* levels_out,
+                       double* flops_out = nullptr);
 
 }  // namespace mpdo

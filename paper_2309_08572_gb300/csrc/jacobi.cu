@@ -357,6 +357,7 @@ __global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
   __syncthreads();
   const R atol = Tol<R>::abs * s_anorm;
   int sweep = 0;
+  int total_rot = 0;   // thread 0: rotations applied (pair-rounds with an active pair)
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
@@ -419,6 +420,7 @@ __global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
       }
       __syncthreads();
     }
+    if (tid == 0) total_rot += s_rot;
     if (s_rot == 0) { ++sweep; break; }
   }
   // eigenvalues = diagonal; sort descending (n <= 128)
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
   }
   if (tid == 0 && counters) {
     counters[2] = sweep;
-    counters[3] = 0;
+    counters[3] = total_rot;   // each rotates 2 rows and 2 columns of A and 2 columns of V
   }
 }
 
@@ -481,6 +483,16 @@ inline int padded_n(int n) {
 }  // namespace
 
 int eig_padded_n(int n) { return padded_n(n); }
+
+// Executed rotation flops per unit of counters[3] (8 real flops per complex element update):
+// the one-CTA kernel counts applied rotations (each updates 2 rows and 2 columns of A and 2
+// columns of V, n elements each: 6 n updates); the block kernel counts active pair-rounds
+// (3 x 16 x 16 x n_pad complex multiply-adds).
+double eig_flops_per_count(int n, bool fp64) {
+  const int smax = fp64 ? 84 : 118;
+  if (n <= smax) return 8.0 * 6.0 * (double)(n + (n & 1));
+  return 8.0 * 3 * 256 * (double)padded_n(n);
+}
 
 template <typename R>
 size_t eig_work_bytes(int n_cap) {
