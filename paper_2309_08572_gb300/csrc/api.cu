@@ -101,7 +101,7 @@ struct mpdo_ctx {
   // FP32 site tensors with FP64 Gram matrices and small-matrix arithmetic (cfg.gram_fp64)
   bool mixed = false;
   // inner eigenproblem through a pivoted Cholesky (see inner_eig)
-  void *wW32 = nullptr, *wL = nullptr, *wGs = nullptr, *wZ = nullptr;
+  void *wW32 = nullptr, *wL = nullptr, *wGs = nullptr, *wZ = nullptr, *wLg = nullptr;
   struct PcOut { int r; int pad; double resid; };
   PcOut* dpc = nullptr;
   PcOut* hpc = nullptr;       // pinned
@@ -292,9 +292,76 @@ cudaError_t pwide(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<f
 // reaches kInnerRmax columns above the tolerance falls back to the full solve.
 // Eigenvectors go to wVk (row stride nin); returns their count.
 constexpr int kInnerDirect = 32;
+
+// Stopping tolerance of the factor for a cut at `cut` of the largest eigenvalue: 1% of the
+// cut, but not below what the factor's precision resolves (FP64 ~1e-15 of the trace;
+// FP32 ~1e-7, used only in C64 mode whose cuts sit at 6e-7).
+inline double pc_tol(const mpdo_ctx* h, double cut) {
+  const double floor = (h->dbl || h->mixed) ? 1e-16 : 2e-7;
+  return std::max(0.01 * cut, floor);
+}
 constexpr double kInnerTol = 1e-7;
 constexpr double kInnerTol64 = 1e-14;
 constexpr int kInnerRmax = 128;
+
+// Eigenpairs of the PSD Gram g (n x n, Gram precision RM) through its pivoted Cholesky
+// factor g ~ L L^+ (stopping at tol * tr g) and one-sided Jacobi on L: eigenvectors to
+// v (row stride ldv), eigenvalues to w, descending (FP64 factor and rotations for FP64
+// Grams, FP32 for FP32 Grams).
+// *nvals = r on success (columns r..n-1 of v and w[r..n) zeroed when zero_tail), 0 when
+// the factor does not fit (rank above the shared-memory cap) and the caller must solve
+// otherwise.  One host synchronisation (the rank).
+template <typename RM>
+int pc_eig(mpdo_ctx* h, int n, const cx<RM>* g, cx<RM>* v, long ldv, double* w, double tol,
+           bool zero_tail, int* nvals) {
+  cudaStream_t st = h->st;
+  *nvals = 0;
+  if (n < 1 || n > 1024) return MPDO_OK;
+  const size_t rbytes = std::is_same<RM, double>::value ? 16 : 8;
+  int rcap = (int)std::min<size_t>(128, kOsjMaxSmem / (rbytes * (size_t)n));
+  rcap -= rcap & 1;
+  const int rmax = std::min(n, rcap);
+  if (rmax < 1) return MPDO_OK;
+  int pi = prof_begin(h, 1);
+  if constexpr (std::is_same<RM, double>::value) {
+    CK(pchol<double>(st, n, g, rmax, tol, static_cast<double2*>(h->wLg), kInnerRmax,
+                     &h->dpc->r, &h->dpc->resid));
+  } else {
+    CK(pchol<float>(st, n, g, rmax, tol, static_cast<float2*>(h->wLg), kInnerRmax, &h->dpc->r,
+                    &h->dpc->resid));
+  }
+  CK(cudaMemcpyAsync(h->hpc, h->dpc, sizeof(mpdo_ctx::PcOut), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int r = h->hpc->r;
+  if (r < 1 || (r >= rmax && r < n && h->hpc->resid > tol)) {
+    prof_end(h, 1, pi, 0.0);
+    prof_drain(h);
+    return MPDO_OK;
+  }
+  int* cnt = eigw<RM>(h).counters;
+  if constexpr (std::is_same<RM, double>::value) {
+    const double2* L = static_cast<const double2*>(h->wLg);
+    CK((osj<double, double, double>(st, n, r, L, kInnerRmax, v, (int)ldv, w, cnt, 0)));
+  } else {
+    const float2* L = static_cast<const float2*>(h->wLg);
+    CK((osj<float, float, float>(st, n, r, L, kInnerRmax, v, (int)ldv, w, cnt, 0)));
+  }
+  if (zero_tail && r < n) {
+    CK(cudaMemset2DAsync(v + r, ldv * sizeof(cx<RM>), 0, (n - r) * sizeof(cx<RM>), n, st));
+    CK(cudaMemsetAsync(w + r, 0, (n - r) * sizeof(double), st));
+  }
+  // executed flops: per rotation 3 dot products and 2 column updates of n complex entries
+  // (8 real flops each); the rotation count is read back with the profile
+  if (pi >= 0 && h->prof_slot < h->prof_nslots) {
+    int slot = h->prof_slot++;
+    CK(cudaMemcpyAsync(&h->prof_counts[slot], cnt + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+    prof_end(h, 1, pi, 0.0, slot, 8.0 * 5 * (double)n);
+  } else {
+    prof_end(h, 1, pi, 0.0);
+  }
+  *nvals = r;
+  return MPDO_OK;
+}
 
 template <typename RM>
 int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
@@ -302,6 +369,17 @@ int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
   cudaStream_t st = h->st;
   TM* W = static_cast<TM*>(h->wWK);
   TM* V = static_cast<TM*>(h->wVk);
+  if (h->dbl) {
+    // FP64 mode: factor + one-sided Jacobi when the rank fits; the Kraus tail below the
+    // tolerance is negligible for the cut and the PPT sums
+    int nv = 0;
+    int rc = pc_eig<RM>(h, nin, W, V, nin, h->wWv, kInnerTol64, false, &nv);
+    if (rc) return rc;
+    if (nv > 0) {
+      *nvals = nv;
+      return MPDO_OK;
+    }
+  }
   if (nin <= kInnerDirect) {
     CK(peig<RM>(h, nin, W, nin, V, nin, h->wWv, 1e-10));
     *nvals = nin;
@@ -405,13 +483,25 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   RM* wRs = static_cast<RM*>(h->wRs);
   RM* wIrs = static_cast<RM*>(h->wIrs);
 
+  int rc;
   // a2: Gram matrices of the two site tensors
   PO(swap12<T>(st, dl, 3, ki, dm, ai, wM));
   CK((pgram<RS, RM>(h, OP_C, OP_N, n3, n3, dl * ki, wM, n3, wM, n3, wGi, n3)));
   CK((pgram<RS, RM>(h, OP_N, OP_C, n3, n3, kj * dr, aj, (long)kj * dr, aj, (long)kj * dr, wGj,
                     n3)));
   // a3: left factor from the eigendecomposition of G_i (numerical rank by gtol)
-  CK(peig<RM>(h, n3, wGi, n3, wVg, n3, h->wSig, 0.1 * h->gtol));
+  {
+    int nv = 0;
+    // the factor route (FP64 factor and rotations) serves the FP64 mode; the mixed mode
+    // keeps its FP32-sweep solver (rotating an FP32 copy of the factor loses the small
+    // eigenvalues: the factor's rounding is relative to whole columns, not to eigen-
+    // directions), C64 the FP32 Jacobi solver
+    if (h->dbl) {
+      rc = pc_eig<RM>(h, n3, wGi, wVg, n3, h->wSig, pc_tol(h, h->gtol), true, &nv);
+      if (rc) return rc;
+    }
+    if (nv == 0) CK(peig<RM>(h, n3, wGi, n3, wVg, n3, h->wSig, 0.1 * h->gtol));
+  }
   PO(gram_mask<RM>(st, n3, h->wSig, h->gtol, wRs, wIrs, h->dsc));
   PO(gram_factor<RM>(st, n3, wVg, wRs, wIrs, wR, wVs, wVr));
   // a4/a5: Phi from the channel and G_j, then H = (I x R) Phi (I x R)^+
@@ -420,9 +510,16 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
                (long)n3 * n9, 3));
   CK(pgemm<RM>(h, OP_N, OP_C, n9, n3, n3, wX, n9, n3, wR, n3, 0, wH, n9, n3, 3));
   // a6: bond eigenpairs and cut
-  CK(peig<RM>(h, n9, wH, n9, wU, n9, h->wLam, 0.1 * h->htol));
+  {
+    int nv = 0;
+    if (h->dbl) {
+      rc = pc_eig<RM>(h, n9, wH, wU, n9, h->wLam, pc_tol(h, h->htol), true, &nv);
+      if (rc) return rc;
+    }
+    if (nv == 0) CK(peig<RM>(h, n9, wH, n9, wU, n9, h->wLam, 0.1 * h->htol));
+  }
   PO(bond_select<RM>(st, n9, h->wLam, wH, n9, h->htol, chi, h->dsc, h->dstats));
-  int rc = read_scalars(h);
+  rc = read_scalars(h);
   if (rc) return rc;
   const int keep = h->hsc->keep;
   // a7: split.  Vgen = (I x V sigma^-1/2) U_keep
@@ -1012,7 +1109,8 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   if ((rc = alloc_dev(hp, &h->eigmem, eb))) return rc;
   if (em == 16) eig_work_bind<double>(h->eig64, h->eigmem, ncap);
   else eig_work_bind<float>(h->eig32, h->eigmem, ncap);
-  if ((rc = alloc_dev(hp, &h->wL, (size_t)KM * kInnerRmax * em)) ||
+  if ((rc = alloc_dev(hp, &h->wLg, (size_t)std::max(n9, KM) * kInnerRmax * em)) ||
+      (rc = alloc_dev(hp, &h->wL, (size_t)KM * kInnerRmax * em)) ||
       (rc = B(&h->wGs, (size_t)kInnerRmax * kInnerRmax)) ||
       (rc = B(&h->wZ, (size_t)kInnerRmax * kInnerRmax)) ||
       (rc = alloc_dev(hp, (void**)&h->dpc, sizeof(mpdo_ctx::PcOut))))

@@ -40,54 +40,52 @@ constexpr double kGapPerDim = 100 * 6e-8;
 constexpr int kPasses = 2;
 constexpr int kMaxLevels = 8;
 
-// lam_i = S_ii / G_ii; out[0] = lam_max; out[1] = length of the leading run with
-// lam > tau lam_max; out[2] = max lam over the rest
-__global__ void mix_scan_kernel(int m, const double2* __restrict__ S,
-                                const double2* __restrict__ G, double* lam, double* out) {
-  __shared__ double red[1024];
-  const int tid = threadIdx.x;
+// One refinement step's scalars and correction, one CTA.  S = SG[:, 0:m], G = SG[:, m:2m]
+// (row stride 2m).  lam_i = S_ii / G_ii; scan[0] = lam_max, scan[1] = length of the leading
+// run with lam > kTau lam_max, scan[2] = max lam over the rest; IE = I + E (file comment).
+// lam0 <= 0: this is level 0 and lam_max is lam_0.
+__global__ void __launch_bounds__(1024) mix_refine_kernel(int m, int n,
+                                                          const double2* __restrict__ SG,
+                                                          double lam0, double* lam, double* scan,
+                                                          double2* IE) {
+  __shared__ double red[32];
+  __shared__ double s_lmax;
+  __shared__ int s_nl;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const long ld = 2L * m;
   double mx = -1e300;
   for (int i = tid; i < m; i += blockDim.x) {
-    double g = G[(long)i * m + i].x;
-    double l = g > 0 ? S[(long)i * m + i].x / g : 0.0;
+    double g = SG[(long)i * ld + m + i].x;
+    double l = g > 0 ? SG[(long)i * ld + i].x / g : 0.0;
     lam[i] = l;
     mx = fmax(mx, l);
   }
-  red[tid] = mx;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (tid < o) red[tid] = fmax(red[tid], red[tid + o]);
-    __syncthreads();
-  }
-  const double lmax = red[0];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[wid] = mx;
   __syncthreads();
   if (tid == 0) {
+    double v = -1e300;
+    for (int k = 0; k < nw; ++k) v = fmax(v, red[k]);
     int nl = 0;
-    while (nl < m && lam[nl] > kTau * lmax) ++nl;
+    while (nl < m && lam[nl] > kTau * v) ++nl;
     double rest = 0.0;
     for (int i = nl; i < m; ++i) rest = fmax(rest, lam[i]);
-    out[0] = lmax;
-    out[1] = (double)nl;
-    out[2] = rest;
+    scan[0] = v;
+    scan[1] = (double)nl;
+    scan[2] = rest;
+    s_lmax = v;
+    s_nl = nl;
   }
-}
-
-// IE = I + E (see the file comment)
-__global__ void mix_correction_kernel(int m, int n, const double2* __restrict__ S,
-                                      const double2* __restrict__ G,
-                                      const double* __restrict__ lam,
-                                      const double* __restrict__ scan, double lam0,
-                                      double2* IE) {
-  const double lmax = scan[0];
+  __syncthreads();
+  const double lmax = s_lmax;
+  const int nl = s_nl;
+  const double l0 = lam0 > 0 ? lam0 : lmax;
   // separated: above the FP32 resolution of this level and above the FP64 rounding of the
   // products with A (~n eps_64 lam_0), below which eigenvectors are not defined
-  const double sep = fmax(kGapPerDim * (m > 10 ? m : 10) * lmax, 100.0 * n * 1.1e-16 * lam0);
-  const int nl = (int)scan[1];
-  long total = (long)m * m;
-  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
-       e += (long)gridDim.x * blockDim.x) {
+  const double sep = fmax(kGapPerDim * (m > 10 ? m : 10) * lmax, 100.0 * n * 1.1e-16 * l0);
+  for (long e = tid; e < (long)m * m; e += blockDim.x) {
     int i = (int)(e / m), j = (int)(e % m);
-    double2 g = G[e];
+    double2 g = SG[(long)i * ld + m + j];
     double2 r;
     if (i == j) {
       r = make_double2(1.0 + 0.5 * (1.0 - g.x), 0.0);
@@ -95,8 +93,8 @@ __global__ void mix_correction_kernel(int m, int n, const double2* __restrict__ 
       double d = lam[j] - lam[i];
       bool resolved = (i < nl) || (j < nl);
       if (resolved && fabs(d) > sep) {
-        double2 s = S[e];
-        r = make_double2((s.x - lam[j] * g.x) / d, (s.y - lam[j] * g.y) / d);
+        double2 sv = SG[(long)i * ld + j];
+        r = make_double2((sv.x - lam[j] * g.x) / d, (sv.y - lam[j] * g.y) / d);
       } else {
         r = make_double2(-0.5 * g.x, -0.5 * g.y);
       }
@@ -115,7 +113,7 @@ cudaError_t gemm64(cudaStream_t st, int opa, int opb, int m, int n, int k, const
 
 size_t mix_work_bytes(int n_cap) {
   size_t sq = (size_t)n_cap * n_cap;
-  return 7 * sq * sizeof(double2) + 2 * sq * sizeof(float2) + 4 * (size_t)n_cap * 8 +
+  return 8 * sq * sizeof(double2) + 2 * sq * sizeof(float2) + 4 * (size_t)n_cap * 8 +
          eig_work_bytes<float>(n_cap) + 8 * 256;
 }
 
@@ -129,11 +127,9 @@ void mix_work_bind(MixWork& w, void* base, int n_cap) {
   };
   w.n_cap = n_cap;
   w.x = reinterpret_cast<double2*>(take(sq * 16));
-  w.z = reinterpret_cast<double2*>(take(sq * 16));
-  w.z2 = reinterpret_cast<double2*>(take(sq * 16));
-  w.t = reinterpret_cast<double2*>(take(sq * 16));
-  w.s = reinterpret_cast<double2*>(take(sq * 16));
-  w.g = reinterpret_cast<double2*>(take(sq * 16));
+  w.tz = reinterpret_cast<double2*>(take(2 * sq * 16));
+  w.tz2 = reinterpret_cast<double2*>(take(2 * sq * 16));
+  w.s = reinterpret_cast<double2*>(take(2 * sq * 16));
   w.ie = reinterpret_cast<double2*>(take(sq * 16));
   w.a32 = reinterpret_cast<float2*>(take(sq * 8));
   w.y32 = reinterpret_cast<float2*>(take(sq * 8));
@@ -154,13 +150,18 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
   int m = n, off = 0, level = 0;
   double lam0 = 0.0;
   double hscan[3];
+  // Z lives in the right half of tz ([T | Z], row stride 2m) so that S and G come from one
+  // product Z^+ [T | Z]
   for (;; ++level) {
+    const long l2 = 2L * m;
+    double2* T = wk.tz;
+    double2* Z = wk.tz + m;
     // B = X^+ A X (level 0: B = A), rounded to FP32 for the sweeps
     const double2* B = a;
     long ldbm = lda;
     if (level > 0) {
-      MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, wk.x, m, wk.t, m));
-      MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, m, n, wk.x, m, wk.t, m, wk.s, m));
+      MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, wk.x, m, T, l2));
+      MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, m, n, wk.x, m, T, l2, wk.s, m));
       gf(n, m, n);
       gf(m, m, n);
       B = wk.s;
@@ -170,57 +171,41 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
     MPDO_CUDA_TRY(heig<float>(st, m, wk.a32, m, wk.y32, m, wk.w32, wk.ew, 20));
     // Z = X Y
     if (level == 0) {
-      MPDO_CUDA_TRY((convert<float, double>(st, n, m, wk.y32, m, wk.z, m)));
+      MPDO_CUDA_TRY((convert<float, double>(st, n, m, wk.y32, m, Z, l2)));
     } else {
       MPDO_CUDA_TRY((convert<float, double>(st, m, m, wk.y32, m, wk.ie, m)));
-      MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, m, wk.x, m, wk.ie, m, wk.z, m));
+      MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, m, wk.x, m, wk.ie, m, Z, l2));
       gf(n, m, m);
     }
     for (int pass = 0; pass < kPasses; ++pass) {
-      MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, wk.z, m, wk.t, m));
-      MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, m, n, wk.z, m, wk.t, m, wk.s, m));
-      MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, m, n, wk.z, m, wk.z, m, wk.g, m));
-      count_launch(2);
-      mix_scan_kernel<<<1, 1024, 0, st>>>(m, wk.s, wk.g, wk.lam, wk.scan);
+      MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, Z, l2, T, l2));     // T = A Z
+      MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, 2 * m, n, Z, l2, T, l2, wk.s, l2));  // [S | G]
+      count_launch();
+      mix_refine_kernel<<<1, 1024, 0, st>>>(m, n, wk.s, level == 0 ? 0.0 : lam0, wk.lam,
+                                            wk.scan, wk.ie);
       MPDO_CUDA_TRY(cudaGetLastError());
-      long tot = (long)m * m;
-      int blocks = (int)std::min<long>((tot + 255) / 256, 4096);
-      if (level == 0 && pass == 0) {
-        // lam_0 (largest eigenvalue) for the absolute separation floor
-        MPDO_CUDA_TRY(cudaMemcpyAsync(hscan, wk.scan, sizeof(hscan), cudaMemcpyDeviceToHost, st));
-        MPDO_CUDA_TRY(cudaStreamSynchronize(st));
-        lam0 = hscan[0];
-      }
-      mix_correction_kernel<<<blocks, 256, 0, st>>>(m, n, wk.s, wk.g, wk.lam, wk.scan, lam0,
-                                                    wk.ie);
-      MPDO_CUDA_TRY(cudaGetLastError());
-      MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, m, wk.z, m, wk.ie, m, wk.z2, m));
+      double2* Z2 = wk.tz2 + m;
+      MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, m, Z, l2, wk.ie, m, Z2, l2));
       gf(n, m, n);
-      gf(m, m, n);
-      gf(m, m, n);
+      gf(m, 2 * m, n);
       gf(n, m, m);
-      std::swap(wk.z, wk.z2);
+      std::swap(wk.tz, wk.tz2);
+      T = wk.tz;
+      Z = wk.tz + m;
     }
-    // Rayleigh quotients of the refined vectors and the split of this level
-    MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, wk.z, m, wk.t, m));
-    MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, m, n, wk.z, m, wk.t, m, wk.s, m));
-    MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, m, n, wk.z, m, wk.z, m, wk.g, m));
-    count_launch();
-    mix_scan_kernel<<<1, 1024, 0, st>>>(m, wk.s, wk.g, wk.lam, wk.scan);
-    MPDO_CUDA_TRY(cudaGetLastError());
-    gf(n, m, n);
-    gf(m, m, n);
-    gf(m, m, n);
+    // the last pass's Rayleigh quotients (second-order accurate for the refined vectors)
+    // and the split of this level
     MPDO_CUDA_TRY(cudaMemcpyAsync(hscan, wk.scan, sizeof(hscan), cudaMemcpyDeviceToHost, st));
     MPDO_CUDA_TRY(cudaMemcpyAsync(hcnt, wk.ew.counters, sizeof(hcnt), cudaMemcpyDeviceToHost, st));
     MPDO_CUDA_TRY(cudaStreamSynchronize(st));
     flops += hcnt[3] * eig_flops_per_count(m, false);
+    if (level == 0) lam0 = hscan[0];
     int nl = (int)hscan[1];
     const bool last = (nl >= m) || level + 1 >= kMaxLevels || !(hscan[2] > floor * lam0) ||
                       nl == 0;
     const int take = last ? m : nl;
     // final columns and values of this level
-    MPDO_CUDA_TRY(cudaMemcpy2DAsync(v + off, ldv * sizeof(double2), wk.z, m * sizeof(double2),
+    MPDO_CUDA_TRY(cudaMemcpy2DAsync(v + off, ldv * sizeof(double2), Z, l2 * sizeof(double2),
                                     take * sizeof(double2), n, cudaMemcpyDeviceToDevice, st));
     MPDO_CUDA_TRY(cudaMemcpyAsync(w + off, wk.lam, take * sizeof(double),
                                   cudaMemcpyDeviceToDevice, st));
@@ -228,7 +213,7 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
     if (last) break;
     // the unresolved columns become the next basis
     const int mr = m - nl;
-    MPDO_CUDA_TRY(cudaMemcpy2DAsync(wk.x, mr * sizeof(double2), wk.z + nl, m * sizeof(double2),
+    MPDO_CUDA_TRY(cudaMemcpy2DAsync(wk.x, mr * sizeof(double2), Z + nl, l2 * sizeof(double2),
                                     mr * sizeof(double2), n, cudaMemcpyDeviceToDevice, st));
     m = mr;
   }

@@ -49,11 +49,20 @@ template <typename R>
 cudaError_t heig(cudaStream_t st, int n, const cx<R>* a, long lda, cx<R>* v, long ldv,
                  double* w, EigWork<R>& work, int max_sweeps);
 
+// One-sided Jacobi on the n x r factor L (row-major, ld lr; r <= 128) of W = L L^+, computed
+// in precision R in one CTA's shared memory (n * r * sizeof(cx<R>) <= kOsjMaxSmem, plus the
+// FP64 copy with finish64): U (n x r, ld ldu) = eigenvectors of W, w (r) = eigenvalues,
+// descending.  finish64 (R = float): FP64 sweeps after the FP32 ones.  counters[2..3] =
+// sweeps, rotations.
+constexpr size_t kOsjMaxSmem = 200 * 1024;
+template <typename RI, typename R, typename RO>
+cudaError_t osj(cudaStream_t st, int n, int r, const cx<RI>* L, int lr, cx<RO>* U, int ldu,
+                double* w, int* counters, int finish64);
+
 // Workspace of the mixed-precision eigensolver (capacity n_cap).
 struct MixWork {
   int n_cap = 0;
-  double2 *x = nullptr, *z = nullptr, *z2 = nullptr, *t = nullptr, *s = nullptr, *g = nullptr,
-          *ie = nullptr;
+  double2 *x = nullptr, *tz = nullptr, *tz2 = nullptr, *s = nullptr, *ie = nullptr;
   float2 *a32 = nullptr, *y32 = nullptr;
   double *lam = nullptr, *w32 = nullptr, *scan = nullptr;
   EigWork<float> ew;

@@ -643,3 +643,201 @@ extern "C" int mpdo_heig_noalloc(int prec, int n, void* a, void* v, double* w, i
   }
   return MPDO_OK;
 }
+
+// =======================================================================================
+// Eigenpairs of a Hermitian PSD matrix from its pivoted Cholesky factor W ~ L L^+:
+// one-sided (Hestenes) Jacobi on the columns of L.  Pairs of columns are rotated until
+// mutually orthogonal (|a_p^+ a_q| <= tol |a_p| |a_q|); then sigma_k = |a_k| and the unit
+// columns are the eigenvectors of L L^+ with eigenvalues sigma_k^2.  The rotations never
+// form a Gram matrix, so small eigenvalues keep their relative accuracy (Demmel and
+// Veselic): the factor's graded columns need no square of the precision.  One CTA; L lives
+// column-major in shared memory; warp w handles pair slots w, w + nw, ... of each round.
+namespace mpdo {
+namespace {
+
+template <typename R>
+struct OsjTol;
+template <> struct OsjTol<double> { static constexpr double v = 1e-14; };
+template <> struct OsjTol<float> { static constexpr double v = 2e-6; };
+
+// Sweeps over the column pairs of A (column-major, n x rp, precision of T) until no pair
+// is rotated; returns the rotations applied (thread 0).
+template <typename T>
+__device__ int osj_sweeps(T* A, int n, int rp, int max_sweeps, double tol, int* s_rot,
+                          int* sweeps_out) {
+  using R = decltype(T{}.x);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  int sweep = 0, total = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < rp - 1; ++round) {
+      for (int slot = warp; slot < rp / 2; slot += nw) {
+        int p, q;
+        tourney(round, slot, rp, p, q);
+        T* ap = A + (size_t)p * n;
+        T* aq = A + (size_t)q * n;
+        R al = 0, be = 0, gr = 0, gi = 0;
+        for (int i = lane; i < n; i += 32) {
+          T x = ap[i], y = aq[i];
+          al += x.x * x.x + x.y * x.y;
+          be += y.x * y.x + y.y * y.y;
+          gr += x.x * y.x + x.y * y.y;     // conj(x) y
+          gi += x.x * y.y - x.y * y.x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          gr += __shfl_xor_sync(0xffffffffu, gr, o);
+          gi += __shfl_xor_sync(0xffffffffu, gi, o);
+        }
+        const R ag = sqrt(gr * gr + gi * gi);
+        if (!(ag > (R)tol * sqrt(al * be)) || !(ag > 0)) continue;
+        // with b_q = conj(e) a_q (e = g/|g|) the pair's Gram is real: [[al, |g|], [|g|, be]]
+        const R zeta = (be - al) / (2 * ag);
+        const R t = (zeta >= 0 ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+        const R c = R(1) / sqrt(R(1) + t * t), s = c * t;
+        const R er = gr / ag, ei = gi / ag;   // e
+        for (int i = lane; i < n; i += 32) {
+          T x = ap[i], y = aq[i];
+          T b;   // conj(e) y
+          b.x = er * y.x + ei * y.y;
+          b.y = er * y.y - ei * y.x;
+          T xn, yn;
+          xn.x = c * x.x - s * b.x; xn.y = c * x.y - s * b.y;
+          yn.x = s * x.x + c * b.x; yn.y = s * x.y + c * b.y;
+          ap[i] = xn;
+          aq[i] = yn;
+        }
+        if (lane == 0) atomicAdd(s_rot, 1);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) total += *s_rot;
+    const int any = *s_rot;
+    __syncthreads();
+    if (any == 0) { ++sweep; break; }
+  }
+  *sweeps_out = sweep;
+  return total;
+}
+
+// Column norms, descending sort and output of the unit columns (A column-major n x rp).
+template <typename T, typename RO>
+__device__ void osj_output(const T* A, int n, int r, int rp, cx<RO>* U, int ldu, double* w,
+                           double* s_key, int* s_val) {
+  using R = decltype(T{}.x);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  int P = 2;
+  while (P < rp) P <<= 1;
+  for (int c = warp; c < P; c += nw) {
+    double nn = 0.0;
+    if (c < r) {
+      const T* ac = A + (size_t)c * n;
+      for (int i = lane; i < n; i += 32) nn += (double)ac[i].x * ac[i].x + (double)ac[i].y * ac[i].y;
+      for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    }
+    if (lane == 0) {
+      s_key[c] = (c < r && isfinite(nn)) ? nn : -1.0;
+      s_val[c] = c;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int c = tid; c < P; c += blockDim.x) {
+        int l = c ^ j;
+        if (l > c) {
+          bool desc = ((c & k) == 0);
+          double kc = s_key[c], kl = s_key[l];
+          if (desc ? (kc < kl) : (kc > kl)) {
+            s_key[c] = kl; s_key[l] = kc;
+            int t2 = s_val[c]; s_val[c] = s_val[l]; s_val[l] = t2;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int k = tid; k < r; k += blockDim.x) w[k] = s_key[k] > 0 ? s_key[k] : 0.0;
+  for (long e = tid; e < (long)n * r; e += blockDim.x) {
+    int i = (int)(e / r), k = (int)(e % r);
+    int col = s_val[k];
+    col = (col >= 0 && col < r) ? col : k;
+    double nk = s_key[k];
+    T x = A[(size_t)col * n + i];
+    R inv = nk > 0 ? (R)(1.0 / sqrt(nk)) : R(0);
+    U[(long)i * ldu + k] = mkc<RO>((RO)(x.x * inv), (RO)(x.y * inv));
+  }
+}
+
+// R: precision of the sweeps.  finish64 (R = float only): after the FP32 sweeps the
+// rotated columns are widened and the sweeps continue in FP64 (a few, from near
+// orthogonality), so the columns end orthogonal to FP64 precision; the FP32 phase's
+// rounding perturbs each direction by ~1e-7 relative, which mixed precision accepts.
+template <typename RI, typename R, typename RO>
+__global__ void __launch_bounds__(1024) osj_kernel(int n, int r, const cx<RI>* __restrict__ L,
+                                                   int lr, cx<RO>* U, int ldu, double* w,
+                                                   int max_sweeps, int finish64, int* counters) {
+  using T = cx<R>;
+  extern __shared__ __align__(16) unsigned char osj_raw[];
+  const int rp = r + (r & 1);
+  T* A = reinterpret_cast<T*>(osj_raw);          // column c at A + c * n
+  __shared__ int s_rot;
+  __shared__ double s_key[128];
+  __shared__ int s_val[128];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < n * rp; e += blockDim.x) {
+    int c = e / n, i = e - c * n;
+    cx<RI> x = (c < r) ? L[(long)i * lr + c] : mkc<RI>(0, 0);
+    A[e] = mkc<R>((R)x.x, (R)x.y);
+  }
+  __syncthreads();
+  int sweeps = 0, sweeps2 = 0;
+  int total = osj_sweeps<T>(A, n, rp, max_sweeps, OsjTol<R>::v, &s_rot, &sweeps);
+  if (finish64 && sizeof(R) == 4) {
+    // widen into the region after the FP32 columns (16-byte aligned)
+    double2* A2 = reinterpret_cast<double2*>(osj_raw + (((size_t)n * rp * sizeof(T) + 15) & ~(size_t)15));
+    for (int e = tid; e < n * rp; e += blockDim.x) A2[e] = make_double2((double)A[e].x, (double)A[e].y);
+    __syncthreads();
+    total += osj_sweeps<double2>(A2, n, rp, max_sweeps, OsjTol<double>::v, &s_rot, &sweeps2);
+    osj_output<double2, RO>(A2, n, r, rp, U, ldu, w, s_key, s_val);
+  } else {
+    osj_output<T, RO>(A, n, r, rp, U, ldu, w, s_key, s_val);
+  }
+  if (tid == 0 && counters) {
+    counters[2] = sweeps + sweeps2;
+    counters[3] = total;
+  }
+}
+
+}  // namespace
+
+template <typename RI, typename R, typename RO>
+cudaError_t osj(cudaStream_t st, int n, int r, const cx<RI>* L, int lr, cx<RO>* U, int ldu,
+                double* w, int* counters, int finish64) {
+  if (n < 1 || r < 1 || r > 128) return cudaErrorInvalidValue;
+  const int rp = r + (r & 1);
+  size_t sm = (size_t)n * rp * sizeof(cx<R>);
+  if (finish64 && sizeof(R) == 4) sm = ((sm + 15) & ~(size_t)15) + (size_t)n * rp * sizeof(double2);
+  if (sm > kOsjMaxSmem) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    MPDO_CUDA_TRY(cudaFuncSetAttribute(osj_kernel<RI, R, RO>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kOsjMaxSmem));
+    attr = true;
+  }
+  int thr = std::min(1024, std::max(64, (rp / 2) * 32));
+  count_launch();
+  osj_kernel<RI, R, RO><<<1, thr, sm, st>>>(n, r, L, lr, U, ldu, w, 30, finish64, counters);
+  return cudaGetLastError();
+}
+template cudaError_t osj<double, double, double>(cudaStream_t, int, int, const double2*, int,
+                                                 double2*, int, double*, int*, int);
+template cudaError_t osj<double, float, double>(cudaStream_t, int, int, const double2*, int,
+                                                double2*, int, double*, int*, int);
+template cudaError_t osj<float, float, float>(cudaStream_t, int, int, const float2*, int,
+                                              float2*, int, double*, int*, int);
+
+}  // namespace mpdo
