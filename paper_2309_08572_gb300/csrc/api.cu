@@ -1070,8 +1070,8 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   double sv = cfg->sv_cutoff > 0 ? cfg->sv_cutoff : 1e-14;
   h->htol = std::max(sv * sv, 10 * eps);
   // The left factor's rank cut: directions of G_i below gtol carry less than gtol of the
-  // block's weight each; in mixed mode they need not be resolved below 1% of the bond cut.
-  h->gtol = h->mixed ? std::max(10 * eps, 0.01 * h->htol) : 10 * eps;
+  // block's weight each; in mixed mode they need not be resolved below 10% of the bond cut.
+  h->gtol = h->mixed ? std::max(10 * eps, 0.1 * h->htol) : 10 * eps;
   double kc = cfg->kraus_cutoff > 0 ? cfg->kraus_cutoff : 1e-14;
   h->kcut = std::max(kc, std::sqrt(10 * eps));
   h->max_sweeps = (h->dbl || h->mixed) ? 30 : 20;

@@ -31,13 +31,13 @@ namespace {
 
 // FP32 sweeps give eigenvectors to ~m eps_32 lam_max / gap.  A refinement pass squares that
 // error only while it is small, so pairs are corrected only when their gap exceeds
-// 100 m eps_32 lam_max (error <= 1e-2, 1e-4 after one pass, 1e-8 after two); closer pairs
+// 100 m eps_32 lam_max (error <= 1e-2 at worst, ~1e-6 in practice, squared by the pass); closer pairs
 // stay a cluster (orthonormalised only: any basis of a cluster is an eigenbasis to within
 // the cluster's width).  Resolved eigenvalues lie above kTau lam_max, two decades per level,
 // so that neighbours in a geometric spectrum stay separated.
 constexpr double kTau = 1e-2;
 constexpr double kGapPerDim = 100 * 6e-8;
-constexpr int kPasses = 2;
+constexpr int kPasses = 1;
 constexpr int kMaxLevels = 8;
 
 // One refinement step's scalars and correction, one CTA.  S = SG[:, 0:m], G = SG[:, m:2m]
