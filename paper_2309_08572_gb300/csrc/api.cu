@@ -21,6 +21,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -100,8 +101,13 @@ struct mpdo_ctx {
   EigWork<float> eig32;
   // FP32 site tensors with FP64 Gram matrices and small-matrix arithmetic (cfg.gram_fp64)
   bool mixed = false;
+  // Waits for the host read-backs of the update: spinning (cudaStreamSynchronize) for one
+  // circuit; blocking on an event (the thread sleeps) while the batch executor runs many
+  // circuits, whose spinning host threads would otherwise take every core.
+  cudaEvent_t bev = nullptr;
+  bool block_sync = false;
   // inner eigenproblem through a pivoted Cholesky (see inner_eig)
-  void *wW32 = nullptr, *wL = nullptr, *wGs = nullptr, *wZ = nullptr, *wLg = nullptr;
+  void *wL = nullptr, *wGs = nullptr, *wZ = nullptr, *wLg = nullptr;
   struct PcOut { int r; int pad; double resid; };
   PcOut* dpc = nullptr;
   PcOut* hpc = nullptr;       // pinned
@@ -203,13 +209,28 @@ int alloc_dev(mpdo_ctx* h, void** p, size_t bytes) {
     cudaGetLastError();
     return fail(h, MPDO_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
   }
+  // no handle buffer ever starts with stale contents of earlier allocations
+  e = cudaMemset(*p, 0, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(*p);
+    return fail(h, MPDO_ERR_CUDA, "cudaMemset of a new buffer failed");
+  }
   h->allocs.push_back(*p);
   return MPDO_OK;
 }
 
+cudaError_t sync_stream(mpdo_ctx* h) {
+  if (h->block_sync && h->bev) {
+    cudaError_t e = cudaEventRecord(h->bev, h->st);
+    return e == cudaSuccess ? cudaEventSynchronize(h->bev) : e;
+  }
+  return cudaStreamSynchronize(h->st);
+}
+
 int read_scalars(mpdo_ctx* h) {
   CK(cudaMemcpyAsync(h->hsc, h->dsc, sizeof(StepScalars), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
+  CK(sync_stream(h));
   prof_drain(h);
   if (h->hsc->flags & 1) return fail(h, MPDO_ERR_NUMERIC, "zero or non-finite state in update");
   return MPDO_OK;
@@ -302,6 +323,7 @@ inline double pc_tol(const mpdo_ctx* h, double cut) {
 }
 constexpr double kInnerTol = 1e-7;
 constexpr double kInnerTol64 = 1e-14;
+constexpr double kInnerTolMixed = 1e-10;
 constexpr int kInnerRmax = 128;
 
 // Eigenpairs of the PSD Gram g (n x n, Gram precision RM) through its pivoted Cholesky
@@ -331,7 +353,7 @@ int pc_eig(mpdo_ctx* h, int n, const cx<RM>* g, cx<RM>* v, long ldv, double* w, 
                     &h->dpc->resid));
   }
   CK(cudaMemcpyAsync(h->hpc, h->dpc, sizeof(mpdo_ctx::PcOut), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream(h));
   const int r = h->hpc->r;
   if (r < 1 || (r >= rmax && r < n && h->hpc->resid > tol)) {
     prof_end(h, 1, pi, 0.0);
@@ -385,28 +407,24 @@ int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
     *nvals = nin;
     return MPDO_OK;
   }
-  // FP64 mode: FP64 factor down to 1e-14 of the trace; FP32 and mixed modes: FP32 factor
-  // down to its floor
-  const bool f64 = h->dbl;
-  const double tol = f64 ? kInnerTol64 : kInnerTol;
-  const int rmax = std::min(nin, kInnerRmax);
+  // FP64 and mixed modes: FP64 factor (down to 1e-14 resp. 1e-10 of the trace); C64: FP32
+  // factor down to its floor.  (An FP32 factor of the FP64 Gram in mixed mode resolved the
+  // kept Kraus directions only to ~1e-7 of the largest weight, which moved energies by
+  // up to 1e-5 where two weights at the cut were close.)
+  const double tol = h->dbl ? kInnerTol64 : h->mixed ? kInnerTolMixed : kInnerTol;
+  // mixed: keep L^+ L within the mixed solver's size
+  const int rmax = std::min(nin, h->mixed ? kMixedEigMax : kInnerRmax);
   int pi = prof_begin(h, 2);
   if constexpr (std::is_same<RM, double>::value) {
-    if (f64) {
-      CK(pchol<double>(st, nin, W, rmax, tol, static_cast<double2*>(h->wL), kInnerRmax,
-                       &h->dpc->r, &h->dpc->resid));
-    } else {
-      CK((convert<double, float>(st, nin, nin, W, nin, static_cast<float2*>(h->wW32), nin)));
-      CK(pchol<float>(st, nin, static_cast<const float2*>(h->wW32), rmax, tol,
-                      static_cast<float2*>(h->wL), kInnerRmax, &h->dpc->r, &h->dpc->resid));
-    }
+    CK(pchol<double>(st, nin, W, rmax, tol, static_cast<double2*>(h->wL), kInnerRmax,
+                     &h->dpc->r, &h->dpc->resid));
   } else {
     CK(pchol<float>(st, nin, W, rmax, tol, static_cast<float2*>(h->wL), kInnerRmax, &h->dpc->r,
                     &h->dpc->resid));
   }
   prof_end(h, 2, pi, 0.0);
   CK(cudaMemcpyAsync(h->hpc, h->dpc, sizeof(mpdo_ctx::PcOut), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream(h));
   prof_drain(h);
   const int r = h->hpc->r;
   if (r < 1 || (r >= rmax && h->hpc->resid > tol)) {
@@ -416,27 +434,11 @@ int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
   }
   TM* Gs = static_cast<TM*>(h->wGs);
   TM* Z = static_cast<TM*>(h->wZ);
-  if constexpr (std::is_same<RM, double>::value) {
-    if (f64) {
-      const double2* L = static_cast<const double2*>(h->wL);
-      CK(pgemm<double>(h, OP_C, OP_N, r, r, nin, L, kInnerRmax, 0, L, kInnerRmax, 0, Gs, r, 0, 1));
-      CK(peig<double>(h, r, Gs, r, Z, r, h->wWv, 1e-10));
-      PO(lift<double>(st, r, Z, h->wWv, Gs));
-      CK(pgemm<double>(h, OP_N, OP_N, nin, r, r, L, kInnerRmax, 0, Gs, r, 0, V, nin, 0, 1));
-    } else {
-      const float2* L = static_cast<const float2*>(h->wL);
-      CK((pgram<float, double>(h, OP_C, OP_N, r, r, nin, L, kInnerRmax, L, kInnerRmax, Gs, r)));
-      CK(peig<double>(h, r, Gs, r, Z, r, h->wWv, 1e-10));
-      PO(lift<double>(st, r, Z, h->wWv, Gs));
-      CK(pwide<double>(h, OP_N, OP_N, nin, r, r, L, kInnerRmax, 0, Gs, r, 0, V, nin, 0, 1));
-    }
-  } else {
-    const float2* L = static_cast<const float2*>(h->wL);
-    CK(pgemm<float>(h, OP_C, OP_N, r, r, nin, L, kInnerRmax, 0, L, kInnerRmax, 0, Gs, r, 0, 1));
-    CK(peig<float>(h, r, Gs, r, Z, r, h->wWv, 1e-10));
-    PO(lift<float>(st, r, Z, h->wWv, Gs));
-    CK(pgemm<float>(h, OP_N, OP_N, nin, r, r, L, kInnerRmax, 0, Gs, r, 0, V, nin, 0, 1));
-  }
+  const TM* L = static_cast<const TM*>(h->wL);
+  CK(pgemm<RM>(h, OP_C, OP_N, r, r, nin, L, kInnerRmax, 0, L, kInnerRmax, 0, Gs, r, 0, 1));
+  CK(peig<RM>(h, r, Gs, r, Z, r, h->wWv, 1e-10));
+  PO(lift<RM>(st, r, Z, h->wWv, Gs));
+  CK(pgemm<RM>(h, OP_N, OP_N, nin, r, r, L, kInnerRmax, 0, Gs, r, 0, V, nin, 0, 1));
   *nvals = r;
   return MPDO_OK;
 }
@@ -496,7 +498,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
     // keeps its FP32-sweep solver (rotating an FP32 copy of the factor loses the small
     // eigenvalues: the factor's rounding is relative to whole columns, not to eigen-
     // directions), C64 the FP32 Jacobi solver
-    if (h->dbl) {
+    if (h->dbl || (h->mixed && n3 > kMixedEigMax)) {
       rc = pc_eig<RM>(h, n3, wGi, wVg, n3, h->wSig, pc_tol(h, h->gtol), true, &nv);
       if (rc) return rc;
     }
@@ -512,7 +514,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   // a6: bond eigenpairs and cut
   {
     int nv = 0;
-    if (h->dbl) {
+    if (h->dbl || (h->mixed && n9 > kMixedEigMax)) {
       rc = pc_eig<RM>(h, n9, wH, wU, n9, h->wLam, pc_tol(h, h->htol), true, &nv);
       if (rc) return rc;
     }
@@ -878,6 +880,7 @@ int init_state(mpdo_ctx* h, const double* v) {
   std::fill(h->kd.begin(), h->kd.end(), 1);
   h->rev = false;
   h->centre = 0;
+  CK(cudaMemsetAsync(h->dsc, 0, sizeof(StepScalars), h->st));
   if (h->dbl)
     CK(product_state<double>(h->st, v, static_cast<double2*>(h->sites), (long)h->site_cap, h->n));
   else
@@ -945,7 +948,7 @@ int energy(mpdo_ctx* h, double J, double hx, double bz, double out[6]) {
   TD res[6];
   for (int a = 0; a < 6; ++a)
     CK(cudaMemcpyAsync(&res[a], ebuf[cur] + a * env, sizeof(TD), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  CK(sync_stream(h));
   prof_drain(h);
   for (int a = 0; a < 6; ++a) out[a] = res[a].x;
   return MPDO_OK;
@@ -1070,8 +1073,8 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   double sv = cfg->sv_cutoff > 0 ? cfg->sv_cutoff : 1e-14;
   h->htol = std::max(sv * sv, 10 * eps);
   // The left factor's rank cut: directions of G_i below gtol carry less than gtol of the
-  // block's weight each; in mixed mode they need not be resolved below 10% of the bond cut.
-  h->gtol = h->mixed ? std::max(10 * eps, 0.1 * h->htol) : 10 * eps;
+  // block's weight each; in mixed mode they need not be resolved below 1% of the bond cut.
+  h->gtol = h->mixed ? std::max(10 * eps, 0.01 * h->htol) : 10 * eps;
   double kc = cfg->kraus_cutoff > 0 ? cfg->kraus_cutoff : 1e-14;
   h->kcut = std::max(kc, std::sqrt(10 * eps));
   h->max_sweeps = (h->dbl || h->mixed) ? 30 : 20;
@@ -1115,8 +1118,11 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
       (rc = B(&h->wZ, (size_t)kInnerRmax * kInnerRmax)) ||
       (rc = alloc_dev(hp, (void**)&h->dpc, sizeof(mpdo_ctx::PcOut))))
     return rc;
-  // FP32 copy of an FP64 inner Gram for the pivoted Cholesky (FP64 and mixed modes)
-  if (em == 16 && (rc = alloc_dev(hp, &h->wW32, (size_t)KM * KM * 8))) return rc;
+  if (cudaEventCreateWithFlags(&h->bev, cudaEventBlockingSync | cudaEventDisableTiming) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    h->bev = nullptr;
+  }
   if (cudaMallocHost((void**)&h->hpc, sizeof(mpdo_ctx::PcOut)) != cudaSuccess) {
     cudaGetLastError();
     return fail(nullptr, MPDO_ERR_OOM, "pinned host allocation");
@@ -1124,6 +1130,9 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   if (h->mixed) {
     if ((rc = alloc_dev(hp, &h->mixmem, mix_work_bytes(ncap)))) return rc;
     mix_work_bind(h->mixw, h->mixmem, ncap);
+    // MPDO_NO_GRAPHS=1: launch the mixed eigensolver's levels directly (no CUDA graphs)
+    const char* ng = std::getenv("MPDO_NO_GRAPHS");
+    if (ng && ng[0] == '1') h->mixw.use_graphs = false;
   }
   if ((rc = alloc_dev(hp, (void**)&h->dsc, sizeof(StepScalars))) ||
       (rc = alloc_dev(hp, (void**)&h->dstats, sizeof(DevStats))))
@@ -1255,15 +1264,22 @@ int mpdo_batch_run(int n_handles, mpdo_t* handles, int n_circuits, const mpdo_ci
   std::atomic<int> next{0};
   std::vector<int> st(n_circuits, MPDO_OK);
   std::vector<std::string> msg(n_circuits);
+  // MPDO_SPIN_SYNC=1 keeps spinning waits in the executor too
+  const char* spin = std::getenv("MPDO_SPIN_SYNC");
+  const bool blocking = n_handles > 2 && !(spin && spin[0] == '1');
   auto worker = [&](int k) {
     mpdo_t h = handles[k];
     cudaSetDevice(h->device);
+    h->block_sync = blocking;
+    h->mixw.block_ev = blocking ? h->bev : nullptr;
     for (;;) {
       int i = next.fetch_add(1);
       if (i >= n_circuits) break;
       st[i] = run_circuit(h, circuits[i], out + 4 * (size_t)i);
       if (st[i]) msg[i] = h->err;
     }
+    h->block_sync = false;
+    h->mixw.block_ev = nullptr;
   };
   const int nt = std::min(n_handles, std::max(1, n_circuits));
   std::vector<std::thread> pool;
@@ -1333,6 +1349,8 @@ int mpdo_destroy(mpdo_t h) {
   if (!h) return MPDO_OK;
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
+  mix_work_release(h->mixw);
+  if (h->bev) cudaEventDestroy(h->bev);
   for (void* p : h->allocs) cudaFree(p);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   if (h->prof_counts) cudaFreeHost(h->prof_counts);
@@ -1406,6 +1424,7 @@ int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, 
     int lv = 0;
     cudaError_t e2 = heig_mixed(st, n, (const double2*)a, n, (double2*)v, n, w, 1e-14, mw, &lv);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    mix_work_release(mw);
     cudaFree(mm);
     if (e2 != cudaSuccess) return fail(nullptr, MPDO_ERR_CUDA, cudaGetErrorString(e2));
     if (sweeps) *sweeps = lv;

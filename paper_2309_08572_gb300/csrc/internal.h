@@ -60,15 +60,22 @@ cudaError_t osj(cudaStream_t st, int n, int r, const cx<RI>* L, int lr, cx<RO>* 
                 double* w, int* counters, int finish64);
 
 // Workspace of the mixed-precision eigensolver (capacity n_cap).
+struct MixGraphs;   // captured level sequences (eigmix.cu)
 struct MixWork {
   int n_cap = 0;
   double2 *x = nullptr, *tz = nullptr, *tz2 = nullptr, *s = nullptr, *ie = nullptr;
   float2 *a32 = nullptr, *y32 = nullptr;
   double *lam = nullptr, *w32 = nullptr, *scan = nullptr;
   EigWork<float> ew;
+  MixGraphs* graphs = nullptr;   // created on first use; freed by mix_work_release
+  bool use_graphs = true;
+  cudaEvent_t block_ev = nullptr; // when set, level read-backs wait on it (blocking sync)
+  double* hpin = nullptr;         // pinned host landing area of the read-backs (lazy)
 };
 size_t mix_work_bytes(int n_cap);
 void mix_work_bind(MixWork& w, void* base, int n_cap);
+// Destroys the captured graphs (the device workspace itself belongs to the caller).
+void mix_work_release(MixWork& w);
 // Eigenpairs of the FP64 Hermitian matrix a (n x n, row-major, lda), descending, resolved
 // down to floor * lambda_max: FP32 Jacobi levels with FP64 refinement.  Synchronises the
 // stream once per level.

@@ -85,14 +85,20 @@ __global__ void __launch_bounds__(JT) jacobi_coop_kernel(int np, int nblk, cx<R>
   __shared__ R s_anorm;
   const int tid = threadIdx.x;
 
-  // |A| scale for the absolute rotation floor: sum of |diag| (block reduction)
+  // |A| scale for the absolute rotation floor: sum of |diag|, reduced in a fixed order so
+  // that every CTA (and every run) uses the same threshold
   {
+    __shared__ R wpart[JT / 32];
     R part = 0;
     for (int i = tid; i < np; i += JT) part += fabs(ap[(long)i * np + i].x);
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (tid == 0) s_anorm = 0;
+    if ((tid & 31) == 0) wpart[tid >> 5] = part;
     __syncthreads();
-    if ((tid & 31) == 0) atomicAdd(&s_anorm, part);
+    if (tid == 0) {
+      R t = 0;
+      for (int k = 0; k < JT / 32; ++k) t += wpart[k];
+      s_anorm = t;
+    }
   }
   __syncthreads();
   const R atol = Tol<R>::abs * s_anorm;
@@ -421,7 +427,11 @@ __global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
       __syncthreads();
     }
     if (tid == 0) total_rot += s_rot;
-    if (s_rot == 0) { ++sweep; break; }
+    // every thread reads the count before thread 0 resets it for the next sweep (a thread
+    // that read the reset value would leave the loop alone and break the block barriers)
+    const int rotated = s_rot;
+    __syncthreads();
+    if (rotated == 0) { ++sweep; break; }
   }
   // eigenvalues = diagonal; sort descending (n <= 128)
   __shared__ int s_nan;

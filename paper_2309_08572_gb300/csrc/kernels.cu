@@ -104,7 +104,8 @@ __global__ void gram_mask_kernel(int n, const double* __restrict__ sig, double g
   __syncthreads();
   if (threadIdx.x == 0) {
     sc->rank_g = cnt;
-    if (bad) sc->flags |= 1;
+    // first flag write of an update: starts the update's flags afresh
+    sc->flags = bad ? 1 : 0;
   }
 }
 

@@ -197,6 +197,36 @@ def test_batch_executor_matches_oracle_fp64(lib):
         m.close()
 
 
+def test_batch_executor_mixed_repeatable(lib):
+    """Mixed precision through the executor: a pool reused for a second batch, and the
+    same circuits one at a time, give identical results (no state carried between
+    circuits on a handle), within the mixed tolerances of the oracle."""
+    base = synth.chain40()
+    circs = []
+    for j, n in enumerate([8, 11, 9, 12, 10, 7]):
+        a, b = synth._angles(synth.rng_for(700 + j), 2)
+        c = synth.scaled(base, n_sites=n, chi_max=32, k_max=6)
+        c.alpha, c.beta = a, b
+        circs.append(c)
+    pool = [lib.Mpdo(12, 32, 6, m_max=25, prec="c64", gram_fp64=True, sv_cutoff=1e-4,
+                     own_stream=True) for _ in range(3)]
+    descs = []
+    for c in circs:
+        dls = [pool[0].upload_layer(layer) for layer in lib.circuit_layers(c)]
+        descs.append(dict(n_sites=c.n_sites, chi_max=c.chi_max, k_max=c.k_max, layers=dls,
+                          J=c.J, hx=c.hx, b=c.bz))
+    out = lib.batch_run(pool, descs)
+    out2 = lib.batch_run(pool, descs[::-1])[::-1]
+    out3 = lib.batch_run(pool[:1], descs)
+    assert np.array_equal(out, out2) and np.array_equal(out, out3)
+    for c, row in zip(circs[:2], out[:2]):
+        _, r = _oracle(c, sv_cutoff=1e-4)
+        for j, key in enumerate(("e_raw", "e_succ", "p_succ", "trace")):
+            assert _rel(row[j], r[key]) < MIXED_TOL[key], (c.n_sites, key, row[j], r[key])
+    for m in pool:
+        m.close()
+
+
 def test_batch512_sample_through_executor(lib):
     """The batched workload (512 circuits, N ~ U{20..100}, chi in {32,64,128}, K=8,
     p in {1,2}, log-uniform rates): 24 of its circuits run concurrently in complex64 on a
