@@ -6,7 +6,7 @@ chi = 256, K = 16, Rydberg decay 0.005 and dephasing 0.005 per block, crosstalk 
 0.01 rad, post-promotion 0.01 rad, seeded angles (seed 3).  One step = one full circuit:
 reset to |+>^N, the 3 layers (297 two-site updates: Gram contractions, Jacobi
 eigensolves, split, Kraus truncation with PPT) and the TFIM energy / success probability.
-One step runs a batch of such circuits (--batch, default 16, seeded angle draws)
+One step runs a batch of such circuits (--batch, default 32, seeded angle draws)
 concurrently through the library's batch executor (one CUDA stream and host thread per
 circuit in flight); the single-circuit latency is reported beside it.
 
@@ -458,7 +458,7 @@ def main():
                     help="skip the plain FP64 single-circuit comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--batch", type=int, default=16,
+    ap.add_argument("--batch", type=int, default=32,
                     help="circuits per step, run concurrently by the batch executor")
     ap.add_argument("--workload", choices=["chain100", "chain40"], default="chain100",
                     help="chain40 (N=40, p=2, chi=64, K=8) is the small profiling case")
