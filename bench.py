@@ -379,6 +379,9 @@ def run_ours(args):
         peak = alu_peak_tflops(prec, smax)
         roof.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
+                     "traffic_note": "not a per-launch constant of this class (sizes vary); one "
+                                     "ncu capture of a level solve (n=24) read 36.6 KB and "
+                                     "wrote 0 B of DRAM: the solves live in shared memory",
                      "flops_per_launch": dprof["flops"] / max(1, dprof["launches"]),
                      "peak_note": f"CUDA-core {'FP64' if prec == 'fp64' else 'FP32'} FMA peak from "
                                   f"unit counts (152 SMs x {'2' if prec == 'fp64' else '128'} FMA/clk "
