@@ -31,6 +31,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -447,6 +449,68 @@ def run_ours(args):
     return 0
 
 
+def run_batch512(args):
+    """The batched workload: 512 circuits (N ~ U{20..100}, chi in {32,64,128}, K = 8,
+    p in {1,2}, log-uniform rates, seed 4) per step through the executor, mixed precision
+    at the same bond cut; value = site-updates/s over all of them."""
+    import torch
+    import paper_2309_08572_gb300 as lib
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    sv = bond_cut(args)
+    circs = synth.batch512()
+    host_layers = [lib.circuit_layers(ci) for ci in circs]
+    m_max = max(k.shape[0] for L in host_layers for layer in L for _, k in layer)
+    n_cap = max(ci.n_sites for ci in circs)
+    chi_cap = max(ci.chi_max for ci in circs)
+    k_cap = max(ci.k_max for ci in circs)
+    lprec = "fp64" if args.prec == "fp64" else "c64"
+    pool = [lib.Mpdo(n_cap, chi_cap, k_cap, m_max=m_max, prec=lprec, own_stream=True,
+                     gram_fp64=(args.prec == "mixed"), sv_cutoff=sv)
+            for _ in range(args.batch)]
+    dls = [[pool[0].upload_layer(layer) for layer in L] for L in host_layers]
+    descs = [dict(n_sites=ci.n_sites, chi_max=ci.chi_max, k_max=ci.k_max, layers=d, J=ci.J,
+                  hx=ci.hx, b=ci.bz) for ci, d in zip(circs, dls)]
+    updates = sum(ci.p * (ci.n_sites - 1) for ci in circs)
+    for _ in range(args.warmup):
+        lib.batch_run(pool, descs)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = lib.batch_run(pool, descs)
+        torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ck = clocks.stop()
+    total_ms = sum(times)
+    line = {"metric": METRIC, "value": args.steps * updates / (total_ms / 1e3),
+            "unit": "site-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "c64": "f32", "mixed": "f32+f64"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": "batch512: 512 circuits, N ~ U{20..100}, chi in {32,64,128}, "
+                                   "K=8, p in {1,2}, decay/dephasing log-U[1e-4,1e-2], seed 4",
+                       "updates_per_step": updates, "precision": PREC_DESC[args.prec],
+                       "bond_cut": f"s > {sv:g} s_max" if sv else "numerical floor",
+                       "pool": f"{args.batch} handles (one stream each) sized N=100, chi=128, K=8",
+                       "l2": "inputs far larger than L2 across the step"},
+            "energy_evals_per_s": args.steps * len(circs) / (total_ms / 1e3),
+            "finite": bool(np.all(np.isfinite(out))), "clocks": ck}
+    print(json.dumps(line), flush=True)
+    for d in dls:
+        for dl in d:
+            pool[0].free_uploaded(dl)
+    for m in pool:
+        m.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,7 +527,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--batch", type=int, default=32,
                     help="circuits per step, run concurrently by the batch executor")
-    ap.add_argument("--workload", choices=["chain100", "chain40"], default="chain100",
+    ap.add_argument("--workload", choices=["chain100", "chain40", "batch512"], default="chain100",
                     help="chain40 (N=40, p=2, chi=64, K=8) is the small profiling case")
     args = ap.parse_args()
     global WORKLOAD
@@ -472,6 +536,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch512":
+        return run_batch512(args)
     return run_ours(args)
 
 

@@ -47,8 +47,8 @@ enum {
  *  MPDO_C64  : complex64 state, FP32 GEMMs (FP32 accumulation), FP32 Jacobi;
  *              cutoff, PPT and trace renormalisation in FP64 scalars.  With
  *              mpdo_config.gram_fp64 = 1 the Grams and the small matrices are FP64.
- *  MPDO_TF32X3, MPDO_BF16X3 : as MPDO_C64 with the large contractions on the
- *              tensor cores in split precision (3 products per real product). */
+ *  MPDO_TF32X3, MPDO_BF16X3 : reserved for tensor-core split-precision contractions;
+ *              not built: mpdo_create rejects them with MPDO_ERR_ARG. */
 typedef enum { MPDO_FP64 = 0, MPDO_C64 = 1, MPDO_TF32X3 = 2, MPDO_BF16X3 = 3 } mpdo_prec;
 
 typedef struct mpdo_ctx* mpdo_t;   /* opaque; the library owns all its device memory */
