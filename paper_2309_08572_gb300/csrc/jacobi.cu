@@ -537,10 +537,7 @@ cudaError_t heig(cudaStream_t st, int n, const cx<R>* a, long lda, cx<R>* v, lon
       attr_set = true;
     }
     count_launch();
-    // small problems: one or a few warps (a round's two block barriers then cost little;
-    // with one thread per element they dominated, ncu: barrier the top stall at n = 24)
-    int thr = np2 <= 32 ? 32 : np2 <= 64 ? 128
-                        : std::min(SJ_THREADS, std::max(64, ((np2 / 2) * np2 + 31) / 32 * 32));
+    int thr = std::min(SJ_THREADS, std::max(64, ((np2 / 2) * np2 + 31) / 32 * 32));
     jacobi_smem_kernel<R><<<1, thr, sm, st>>>(n, np2, a, lda, v, ldv, w, work.counters,
                                               max_sweeps);
     return cudaGetLastError();

@@ -3,6 +3,7 @@ training by the library's MLP kernels, angle proposals from its input gradient, 
 re-scoring of every proposal by the engine.  The gain over the method without the network:
 with the same number of engine evaluations, the proposals reach a lower energy than random
 angle draws (a bounded version of the 100k-sample workload: short chains, 4000 samples)."""
+import dataclasses
 import math
 
 import numpy as np
@@ -69,6 +70,20 @@ def test_surrogate_proposals_beat_random_draws(lib):
     print("surrogate best E/N", e_prop.min(), "random best E/N", e_rand.min(),
           "final train loss", losses[-1])
     assert e_prop.min() < e_rand.min()
+    # the workload's target: proposals for N = 100, p = 2, re-scored by the MPDO at chi = 128
+    # (mixed precision); the network saw only 8-12-atom chains, so this is transfer
+    big = dataclasses.replace(target, n_sites=100, chi_max=128, k_max=8)
+    pool100 = [lib.Mpdo(100, 128, 8, m_max=25, prec="c64", gram_fp64=True, sv_cutoff=1e-4,
+                        own_stream=True) for _ in range(8)]
+    theta100 = sg.propose(net, big, p, n_starts=64, steps=200, lr=0.05, seed=4)
+    e100 = sg.simulate([sg.with_angles(big, t[:p], t[p:]) for t in theta100[:4]], pool100)[:, 0]
+    r100 = sg.simulate([dataclasses.replace(big, alpha=list(rng.uniform(0, math.pi, p)),
+                                            beta=list(rng.uniform(0, math.pi, p)))
+                        for _ in range(4)], pool100)[:, 0]
+    print("N=100 chi=128: surrogate best E/N", e100.min(), "random mean E/N", r100.mean())
+    assert np.all(np.isfinite(e100)) and e100.min() < r100.mean()
+    for m in pool100:
+        m.close()
     net.close()
     for m in pool:
         m.close()
