@@ -385,17 +385,53 @@ int pc_eig(mpdo_ctx* h, int n, const cx<RM>* g, cx<RM>* v, long ldv, double* w, 
   return MPDO_OK;
 }
 
+// Eigenpairs of the PSD Gram g (n x n) through a pivoted Cholesky factor g ~ L L^+
+// (stopping at tol * tr g, at most rmax columns; FP64 factor for FP64 Grams, FP32 for
+// FP32 Grams) and the eigenpairs of the r x r matrix L^+ L (solved down to floor of its
+// largest), lifted as u = L z / sqrt(s): eigenvectors to v (row stride ldv), eigenvalues
+// to w, descending.  *nvals = r, or 0 when the factor needs more than rmax columns (the
+// caller solves the full problem).  zero_tail: columns r..n-1 of v and w[r..n) zeroed.
 template <typename RM>
-int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
+int lift_eig(mpdo_ctx* h, int n, const cx<RM>* g, cx<RM>* v, long ldv, double* w, double tol,
+             int rmax, double floor, bool zero_tail, int* nvals) {
   using TM = cx<RM>;
   cudaStream_t st = h->st;
-  TM* W = static_cast<TM*>(h->wWK);
-  TM* V = static_cast<TM*>(h->wVk);
+  *nvals = 0;
+  rmax = std::min(rmax, n);
+  if (n < 1 || n > 1024 || rmax < 1) return MPDO_OK;
+  TM* L = static_cast<TM*>(h->wLg);
+  int pi = prof_begin(h, 2);
+  CK(pchol<RM>(st, n, g, rmax, tol, L, kInnerRmax, &h->dpc->r, &h->dpc->resid));
+  prof_end(h, 2, pi, 0.0);
+  CK(cudaMemcpyAsync(h->hpc, h->dpc, sizeof(mpdo_ctx::PcOut), cudaMemcpyDeviceToHost, st));
+  CK(sync_stream(h));
+  prof_drain(h);
+  const int r = h->hpc->r;
+  if (r < 1 || (r >= rmax && r < n && h->hpc->resid > tol)) return MPDO_OK;
+  TM* Gs = static_cast<TM*>(h->wGs);
+  TM* Z = static_cast<TM*>(h->wZ);
+  CK(pgemm<RM>(h, OP_C, OP_N, r, r, n, L, kInnerRmax, 0, L, kInnerRmax, 0, Gs, r, 0, 1));
+  CK(peig<RM>(h, r, Gs, r, Z, r, w, floor));
+  PO(lift<RM>(st, r, Z, w, Gs));
+  CK(pgemm<RM>(h, OP_N, OP_N, n, r, r, L, kInnerRmax, 0, Gs, r, 0, v, ldv, 0, 1));
+  if (zero_tail && r < n) {
+    CK(cudaMemset2DAsync(v + r, ldv * sizeof(TM), 0, (n - r) * sizeof(TM), n, st));
+    CK(cudaMemsetAsync(w + r, 0, (n - r) * sizeof(double), st));
+  }
+  *nvals = r;
+  return MPDO_OK;
+}
+
+template <typename RM>
+int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
+  cx<RM>* W = static_cast<cx<RM>*>(h->wWK);
+  cx<RM>* V = static_cast<cx<RM>*>(h->wVk);
+  int rc;
   if (h->dbl) {
     // FP64 mode: factor + one-sided Jacobi when the rank fits; the Kraus tail below the
     // tolerance is negligible for the cut and the PPT sums
     int nv = 0;
-    int rc = pc_eig<RM>(h, nin, W, V, nin, h->wWv, kInnerTol64, false, &nv);
+    rc = pc_eig<RM>(h, nin, W, V, nin, h->wWv, kInnerTol64, false, &nv);
     if (rc) return rc;
     if (nv > 0) {
       *nvals = nv;
@@ -410,36 +446,18 @@ int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
   // FP64 and mixed modes: FP64 factor (down to 1e-14 resp. 1e-10 of the trace); C64: FP32
   // factor down to its floor.  (An FP32 factor of the FP64 Gram in mixed mode resolved the
   // kept Kraus directions only to ~1e-7 of the largest weight, which moved energies by
-  // up to 1e-5 where two weights at the cut were close.)
+  // up to 1e-5 where two weights at the cut were close.)  Mixed: L^+ L stays within the
+  // mixed solver's size.
   const double tol = h->dbl ? kInnerTol64 : h->mixed ? kInnerTolMixed : kInnerTol;
-  // mixed: keep L^+ L within the mixed solver's size
-  const int rmax = std::min(nin, h->mixed ? kMixedEigMax : kInnerRmax);
-  int pi = prof_begin(h, 2);
-  if constexpr (std::is_same<RM, double>::value) {
-    CK(pchol<double>(st, nin, W, rmax, tol, static_cast<double2*>(h->wL), kInnerRmax,
-                     &h->dpc->r, &h->dpc->resid));
-  } else {
-    CK(pchol<float>(st, nin, W, rmax, tol, static_cast<float2*>(h->wL), kInnerRmax, &h->dpc->r,
-                    &h->dpc->resid));
-  }
-  prof_end(h, 2, pi, 0.0);
-  CK(cudaMemcpyAsync(h->hpc, h->dpc, sizeof(mpdo_ctx::PcOut), cudaMemcpyDeviceToHost, st));
-  CK(sync_stream(h));
-  prof_drain(h);
-  const int r = h->hpc->r;
-  if (r < 1 || (r >= rmax && h->hpc->resid > tol)) {
+  int nv = 0;
+  rc = lift_eig<RM>(h, nin, W, V, nin, h->wWv, tol, h->mixed ? kMixedEigMax : kInnerRmax, 1e-10,
+                    false, &nv);
+  if (rc) return rc;
+  if (nv == 0) {
     CK(peig<RM>(h, nin, W, nin, V, nin, h->wWv, 1e-10));
-    *nvals = nin;
-    return MPDO_OK;
+    nv = nin;
   }
-  TM* Gs = static_cast<TM*>(h->wGs);
-  TM* Z = static_cast<TM*>(h->wZ);
-  const TM* L = static_cast<const TM*>(h->wL);
-  CK(pgemm<RM>(h, OP_C, OP_N, r, r, nin, L, kInnerRmax, 0, L, kInnerRmax, 0, Gs, r, 0, 1));
-  CK(peig<RM>(h, r, Gs, r, Z, r, h->wWv, 1e-10));
-  PO(lift<RM>(st, r, Z, h->wWv, Gs));
-  CK(pgemm<RM>(h, OP_N, OP_N, nin, r, r, L, kInnerRmax, 0, Gs, r, 0, V, nin, 0, 1));
-  *nvals = r;
+  *nvals = nv;
   return MPDO_OK;
 }
 
@@ -494,11 +512,16 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   // a3: left factor from the eigendecomposition of G_i (numerical rank by gtol)
   {
     int nv = 0;
-    // the factor route (FP64 factor and rotations) serves the FP64 mode; the mixed mode
-    // keeps its FP32-sweep solver (rotating an FP32 copy of the factor loses the small
-    // eigenvalues: the factor's rounding is relative to whole columns, not to eigen-
-    // directions), C64 the FP32 Jacobi solver
-    if (h->dbl || (h->mixed && n3 > kMixedEigMax)) {
+    // FP64 mode: FP64 factor + one-sided Jacobi.  Mixed: FP64 factor and the mixed solver
+    // on L^+ L (rank r instead of 3D; rotating an FP32 copy of the factor instead loses the
+    // small eigenvalues: its rounding is relative to whole columns, not to eigen-
+    // directions), the factor route on larger ranks.  C64: the FP32 Jacobi solver.
+    if (h->mixed) {
+      rc = lift_eig<RM>(h, n3, wGi, wVg, n3, h->wSig, pc_tol(h, h->gtol), kMixedEigMax,
+                        0.1 * h->gtol, true, &nv);
+      if (rc) return rc;
+    }
+    if (nv == 0 && (h->dbl || (h->mixed && n3 > kMixedEigMax))) {
       rc = pc_eig<RM>(h, n3, wGi, wVg, n3, h->wSig, pc_tol(h, h->gtol), true, &nv);
       if (rc) return rc;
     }
@@ -514,7 +537,12 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   // a6: bond eigenpairs and cut
   {
     int nv = 0;
-    if (h->dbl || (h->mixed && n9 > kMixedEigMax)) {
+    if (h->mixed) {
+      rc = lift_eig<RM>(h, n9, wH, wU, n9, h->wLam, pc_tol(h, h->htol), kMixedEigMax,
+                        0.1 * h->htol, true, &nv);
+      if (rc) return rc;
+    }
+    if (nv == 0 && (h->dbl || (h->mixed && n9 > kMixedEigMax))) {
       rc = pc_eig<RM>(h, n9, wH, wU, n9, h->wLam, pc_tol(h, h->htol), true, &nv);
       if (rc) return rc;
     }
