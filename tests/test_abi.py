@@ -65,3 +65,21 @@ def test_invalid_arguments_are_rejected_without_gpu(pkg):
         pkg.build_block_channel(0.1, -1.0, 0.0)
     with pytest.raises(pkg.MpdoError):
         pkg.build_block_channel(float("nan"), 0.0, 0.0)
+
+
+def test_create_argument_checks_without_gpu(pkg):
+    """mpdo_create validates sizes before any CUDA call: oversized m_max*k_max is
+    ERR_ARG; the smoke circuit's sizes pass validation and fail only on the missing GPU."""
+    import ctypes as C
+    import __graft_entry__ as g
+
+    def create(k_max, m_max):
+        cfg = pkg.Config(6, 3, 729, k_max, m_max, pkg.PREC["fp64"], 0.0, 0.0, 1, None, 0)
+        h = C.c_void_p(None)
+        rc = pkg.LIB.mpdo_create(C.byref(cfg), None, C.byref(h))
+        if rc == 0:
+            pkg.LIB.mpdo_destroy(h)
+        return rc
+
+    assert create(64, 25) == -1
+    assert create(g.SMOKE_K_MAX, g.SMOKE_M_MAX) != -1
