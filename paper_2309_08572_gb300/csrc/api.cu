@@ -1447,6 +1447,12 @@ int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, 
     // mixed-precision solver on an FP64 matrix (resolved down to 1e-14 of the largest)
     void* mm = nullptr;
     if (cudaMalloc(&mm, mix_work_bytes(n)) != cudaSuccess) { cudaGetLastError(); return fail(nullptr, MPDO_ERR_OOM, "heig work"); }
+    // the solver's CTA ticket starts at zero
+    if (cudaMemsetAsync(mm, 0, mix_work_bytes(n), st) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(mm);
+      return fail(nullptr, MPDO_ERR_CUDA, "heig work clear");
+    }
     MixWork mw;
     mix_work_bind(mw, mm, n);
     int lv = 0;

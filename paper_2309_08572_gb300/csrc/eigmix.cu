@@ -40,14 +40,19 @@ constexpr double kTau = 1e-2;
 constexpr double kGapPerDim = 100 * 6e-8;
 constexpr int kMaxLevels = 8;
 
-// One refinement step's scalars and correction, one CTA.  S = SG[:, 0:m], G = SG[:, m:2m]
-// (row stride 2m).  lam_i = S_ii / G_ii; scan[0] = lam_max, scan[1] = length of the leading
-// run with lam > kTau lam_max, scan[2] = max lam over the rest; IE = I + E (file comment).
-// lam0 <= 0: this is level 0 and lam_max is lam_0.
-__global__ void __launch_bounds__(1024) mix_refine_kernel(int m, int n,
-                                                          const double2* __restrict__ SG,
-                                                          int level0, double* lam, double* scan,
-                                                          double2* IE) {
+// Level scalars in wk.scan: [0] lam_max of the pass, [1] nl = length of the leading run
+// with lam > kTau lam_max, [2] largest lam after that run, [3] lam_max of level 0's last
+// pass, [4] lam_max of level 0's first pass (lam_0 of the separation floor), [5] Jacobi
+// rotations of the level, [6] 1 when this level is the last, [7] columns it emits.
+constexpr int kScan = 8;
+
+// One refinement step's scalars and correction, run by one CTA.  S = SG[:, 0:m],
+// G = SG[:, m:2m] (row stride 2m), written by other CTAs of the same launch (read through
+// L2).  lam_i = S_ii / G_ii; IE = I + E (file comment).  The final pass also decides
+// whether the level is the last one.
+__device__ void refine_step(int m, int n, const double2* SG, int level0, int final_pass,
+                            int level, double floor, const int* rot, double* lam, double* scan,
+                            double2* IE) {
   __shared__ double red[32];
   __shared__ double s_lmax;
   __shared__ int s_nl;
@@ -55,8 +60,8 @@ __global__ void __launch_bounds__(1024) mix_refine_kernel(int m, int n,
   const long ld = 2L * m;
   double mx = -1e300;
   for (int i = tid; i < m; i += blockDim.x) {
-    double g = SG[(long)i * ld + m + i].x;
-    double l = g > 0 ? SG[(long)i * ld + i].x / g : 0.0;
+    double g = __ldcg(&SG[(long)i * ld + m + i].x);
+    double l = g > 0 ? __ldcg(&SG[(long)i * ld + i].x) / g : 0.0;
     lam[i] = l;
     mx = fmax(mx, l);
   }
@@ -74,6 +79,15 @@ __global__ void __launch_bounds__(1024) mix_refine_kernel(int m, int n,
     scan[1] = (double)nl;
     scan[2] = rest;
     if (level0) scan[4] = v;   // lam_0, kept for the later levels
+    if (final_pass) {
+      if (level == 0) scan[3] = v;
+      const double top = scan[3];
+      const bool last = (nl >= m) || (level + 1 >= kMaxLevels) || !(rest > floor * top) ||
+                        nl == 0;
+      scan[5] = rot ? (double)rot[3] : 0.0;
+      scan[6] = last ? 1.0 : 0.0;
+      scan[7] = last ? (double)m : (double)nl;
+    }
     s_lmax = v;
     s_nl = nl;
   }
@@ -86,7 +100,7 @@ __global__ void __launch_bounds__(1024) mix_refine_kernel(int m, int n,
   const double sep = fmax(kGapPerDim * (m > 10 ? m : 10) * lmax, 100.0 * n * 1.1e-16 * l0);
   for (long e = tid; e < (long)m * m; e += blockDim.x) {
     int i = (int)(e / m), j = (int)(e % m);
-    double2 g = SG[(long)i * ld + m + j];
+    double2 g = __ldcg(&SG[(long)i * ld + m + j]);
     double2 r;
     if (i == j) {
       r = make_double2(1.0 + 0.5 * (1.0 - g.x), 0.0);
@@ -94,7 +108,7 @@ __global__ void __launch_bounds__(1024) mix_refine_kernel(int m, int n,
       double d = lam[j] - lam[i];
       bool resolved = (i < nl) || (j < nl);
       if (resolved && fabs(d) > sep) {
-        double2 sv = SG[(long)i * ld + j];
+        double2 sv = __ldcg(&SG[(long)i * ld + j]);
         r = make_double2((sv.x - lam[j] * g.x) / d, (sv.y - lam[j] * g.y) / d);
       } else {
         r = make_double2(-0.5 * g.x, -0.5 * g.y);
@@ -102,6 +116,85 @@ __global__ void __launch_bounds__(1024) mix_refine_kernel(int m, int n,
     }
     IE[e] = r;
   }
+}
+
+constexpr int RT = 16;   // output tile of the fused products (one element per thread)
+
+// [S | G] = Z^+ [T | Z] (m x 2m, row stride 2m) from TZ = [T | Z] (n x 2m, row stride 2m),
+// then the refinement step, run by the CTA that finishes last (a ticket counter in global
+// memory; no CTA waits on another).  The ticket returns to 0 for the next launch.
+__global__ void __launch_bounds__(RT * RT) sg_refine_kernel(
+    int m, int n, const double2* __restrict__ TZ, double2* SG, int level0, int final_pass,
+    int level, double floor, const int* rot, double* lam, double* scan, double2* IE,
+    unsigned int* ticket) {
+  __shared__ double2 As[RT][RT + 1];   // [k][i]
+  __shared__ double2 Bs[RT][RT + 1];   // [k][j]
+  __shared__ int s_last;
+  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT;
+  const int i0 = blockIdx.y * RT, j0 = blockIdx.x * RT;
+  const long ld = 2L * m;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < n; k0 += RT) {
+    const int k = k0 + ty;
+    double2 za = make_double2(0.0, 0.0), tb = make_double2(0.0, 0.0);
+    if (k < n && i0 + tx < m) za = cconj(TZ[(long)k * ld + m + i0 + tx]);
+    if (k < n && j0 + tx < 2 * m) tb = TZ[(long)k * ld + j0 + tx];
+    As[ty][tx] = za;
+    Bs[ty][tx] = tb;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < RT; ++kk) cfma(acc, As[kk][ty], Bs[kk][tx]);
+    __syncthreads();
+  }
+  if (i0 + ty < m && j0 + tx < 2 * m) SG[(long)(i0 + ty) * ld + j0 + tx] = acc;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int total = gridDim.x * gridDim.y;
+    s_last = (atomicAdd(ticket, 1u) == total - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  refine_step(m, n, SG, level0, final_pass, level, floor, rot, lam, scan, IE);
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// The level's last product Z' = Z (I + E) (Z: n x m, row stride ldz), routed by the level's
+// scalars: columns j < take go to v[:, off + j] (with w[off + j] = lam_j); when the level is
+// not the last, columns j >= nl go to the next basis x[:, j - nl] (row stride m - nl).
+__global__ void __launch_bounds__(RT * RT) level_out_kernel(
+    int n, int m, const double2* __restrict__ Z, long ldz, const double2* __restrict__ IE,
+    const double* scan, const double* lam, double2* v, long ldv, double* w, int off,
+    double2* x) {
+  __shared__ double2 As[RT][RT + 1];   // [k][row]
+  __shared__ double2 Bs[RT][RT + 1];   // [k][col]
+  const int tx = threadIdx.x % RT, ty = threadIdx.x / RT;
+  const int r0 = blockIdx.y * RT, j0 = blockIdx.x * RT;
+  const bool last = scan[6] != 0.0;
+  const int nl = (int)scan[1];
+  const int take = last ? m : nl;
+  const int mr = m - nl;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < m; k0 += RT) {
+    double2 za = make_double2(0.0, 0.0), eb = make_double2(0.0, 0.0);
+    if (r0 + ty < n && k0 + tx < m) za = Z[(long)(r0 + ty) * ldz + k0 + tx];
+    if (k0 + ty < m && j0 + tx < m) eb = IE[(long)(k0 + ty) * m + j0 + tx];
+    As[tx][ty] = za;
+    Bs[ty][tx] = eb;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < RT; ++kk) cfma(acc, As[kk][ty], Bs[kk][tx]);
+    __syncthreads();
+  }
+  const int r = r0 + ty, j = j0 + tx;
+  if (r < n && j < m) {
+    if (j < take)
+      v[(long)r * ldv + off + j] = acc;
+    else if (!last && j >= nl)
+      x[(long)r * mr + (j - nl)] = acc;
+  }
+  if (blockIdx.y == 0 && ty == 0 && j < take) w[off + j] = lam[j];
 }
 
 cudaError_t gemm64(cudaStream_t st, int opa, int opb, int m, int n, int k, const double2* A,
@@ -112,21 +205,33 @@ cudaError_t gemm64(cudaStream_t st, int opa, int opb, int m, int n, int k, const
 
 }  // namespace
 
-// One captured graph per (input matrix, n, m, level 0 or not): the launches of a level up
-// to its host read-back run as one graph launch instead of ~12 kernel launches.
+// One captured graph per level shape: (input matrix, n, m, level, outputs, floor).  The
+// launches of a level and its read-back run as one graph launch instead of ~8.
 struct MixKey {
   const void* a;
   long lda;
-  int n, m, lev0;
+  int n, m, level;
+  const void* v;
+  long ldv;
+  const void* w;
+  double floor;
   bool operator==(const MixKey& o) const {
-    return a == o.a && lda == o.lda && n == o.n && m == o.m && lev0 == o.lev0;
+    return a == o.a && lda == o.lda && n == o.n && m == o.m && level == o.level && v == o.v &&
+           ldv == o.ldv && w == o.w && floor == o.floor;
   }
 };
 struct MixKeyHash {
   size_t operator()(const MixKey& k) const {
+    auto mix = [](size_t h, size_t x) {
+      return h ^ (x + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2));
+    };
     size_t h = std::hash<const void*>()(k.a);
-    h ^= std::hash<long>()(k.lda) + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
-    h ^= std::hash<long>()(((long)k.n << 32) ^ ((long)k.m << 1) ^ k.lev0) + (h << 6) + (h >> 2);
+    h = mix(h, std::hash<long>()(k.lda));
+    h = mix(h, std::hash<long>()(((long)k.n << 32) ^ ((long)k.m << 8) ^ k.level));
+    h = mix(h, std::hash<const void*>()(k.v));
+    h = mix(h, std::hash<long>()(k.ldv));
+    h = mix(h, std::hash<const void*>()(k.w));
+    h = mix(h, std::hash<double>()(k.floor));
     return h;
   }
 };
@@ -146,7 +251,7 @@ void mix_work_release(MixWork& w) {
 size_t mix_work_bytes(int n_cap) {
   size_t sq = (size_t)n_cap * n_cap;
   return 8 * sq * sizeof(double2) + 2 * sq * sizeof(float2) + 4 * (size_t)n_cap * 8 +
-         eig_work_bytes<float>(n_cap) + 8 * 256;
+         eig_work_bytes<float>(n_cap) + 10 * 256;
 }
 
 void mix_work_bind(MixWork& w, void* base, int n_cap) {
@@ -167,20 +272,35 @@ void mix_work_bind(MixWork& w, void* base, int n_cap) {
   w.y32 = reinterpret_cast<float2*>(take(sq * 8));
   w.lam = reinterpret_cast<double*>(take((size_t)n_cap * 8));
   w.w32 = reinterpret_cast<double*>(take((size_t)n_cap * 8));
-  w.scan = reinterpret_cast<double*>(take(64));
+  w.scan = reinterpret_cast<double*>(take(kScan * sizeof(double)));
+  w.ticket = reinterpret_cast<unsigned int*>(take(64));
   eig_work_bind<float>(w.ew, take(eig_work_bytes<float>(n_cap)), n_cap);
 }
 
 namespace {
 constexpr int kPasses = 2;
-inline double2* mix_result(MixWork& wk, int m) { return ((kPasses & 1) ? wk.tz2 : wk.tz) + m; }
 
-// The launches of one level up to the read-back (no host synchronisation inside).
-// Level 0 reads B = A; later levels project on the basis in wk.x.  Refined vectors end in
-// the right half of tz2 ([T | Z] layout, row stride 2m).
-cudaError_t enqueue_level(cudaStream_t st, int n, int m, bool lev0, const double2* a, long lda,
-                          MixWork& wk, double& flops) {
-  auto gf = [&](int mm, int nn, int kk) { flops += 8.0 * mm * nn * (double)kk; };
+// Floating-point work of one level's products (8 real flops per complex multiply-add).
+double level_flops(int n, int m, bool lev0) {
+  auto g = [](int a, int b, int c) { return 8.0 * a * b * (double)c; };
+  double f = 0.0;
+  if (!lev0) f += g(n, m, n) + g(m, m, n) + g(n, m, m);   // X^+ A X and Z = X Y
+  f += g(n, m, n);                                          // T = A Z
+  for (int pass = 0; pass < kPasses; ++pass) {
+    f += g(m, 2 * m, n);                                    // [S | G]
+    f += (pass + 1 < kPasses) ? 2 * g(n, m, m) : g(n, m, m); // [T | Z] (I + E) or Z (I + E)
+  }
+  return f;
+}
+
+// The launches of one level, ending with the copy of its scalars to the pinned host area
+// (no host synchronisation inside, so a level can be captured as one graph).  Level 0 reads
+// B = A; later levels project on the basis in wk.x, which the level's last product replaces
+// with the unresolved columns.  The refinement carries T along: after a pass,
+// [T | Z] <- [T | Z] (I + E) = [A Z' | Z'], so A enters only the first product.
+cudaError_t enqueue_level(cudaStream_t st, int n, int m, int level, const double2* a, long lda,
+                          double2* v, long ldv, double* w, double floor, MixWork& wk) {
+  const bool lev0 = (level == 0);
   const long l2 = 2L * m;
   double2* T = wk.tz;
   double2* Z = wk.tz + m;
@@ -189,40 +309,52 @@ cudaError_t enqueue_level(cudaStream_t st, int n, int m, bool lev0, const double
   if (!lev0) {
     MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, wk.x, m, T, l2));
     MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, m, n, wk.x, m, T, l2, wk.s, m));
-    gf(n, m, n);
-    gf(m, m, n);
     B = wk.s;
     ldbm = m;
   }
-  MPDO_CUDA_TRY((convert<double, float>(st, m, m, B, ldbm, wk.a32, m)));
-  MPDO_CUDA_TRY(heig<float>(st, m, wk.a32, m, wk.y32, m, wk.w32, wk.ew, 20));
-  if (lev0) {
-    MPDO_CUDA_TRY((convert<float, double>(st, n, m, wk.y32, m, Z, l2)));
+  if (m <= kSmemJacobiMaxF32) {
+    // the FP32 sweeps read the FP64 matrix and write the vectors in the precision needed
+    if (lev0) {
+      MPDO_CUDA_TRY((heig_smem_f32<double, double>(st, m, B, ldbm, Z, l2, wk.w32,
+                                                   wk.ew.counters, 20)));
+    } else {
+      MPDO_CUDA_TRY((heig_smem_f32<double, float>(st, m, B, ldbm, wk.y32, m, wk.w32,
+                                                  wk.ew.counters, 20)));
+      MPDO_CUDA_TRY(cgemm_dx(st, OP_N, OP_N, n, m, m, wk.x, m, 0, wk.y32, m, 0, Z, l2, 0, 1));
+    }
   } else {
-    MPDO_CUDA_TRY((convert<float, double>(st, m, m, wk.y32, m, wk.ie, m)));
-    MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, m, wk.x, m, wk.ie, m, Z, l2));
-    gf(n, m, m);
+    MPDO_CUDA_TRY((convert<double, float>(st, m, m, B, ldbm, wk.a32, m)));
+    MPDO_CUDA_TRY(heig<float>(st, m, wk.a32, m, wk.y32, m, wk.w32, wk.ew, 20));
+    if (lev0)
+      MPDO_CUDA_TRY((convert<float, double>(st, n, m, wk.y32, m, Z, l2)));
+    else
+      MPDO_CUDA_TRY(cgemm_dx(st, OP_N, OP_N, n, m, m, wk.x, m, 0, wk.y32, m, 0, Z, l2, 0, 1));
   }
-  // refinement passes: T = A Z, [S | G] = Z^+ [T | Z], I + E, Z' = Z (I + E); the buffers
-  // alternate between tz and tz2, so the result lies in mix_result(wk, m)
+  MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, Z, l2, T, l2));
   double2* cur = wk.tz;
   double2* nxt = wk.tz2;
+  const dim3 gsg((2 * m + RT - 1) / RT, (m + RT - 1) / RT);
   for (int pass = 0; pass < kPasses; ++pass) {
-    double2* Tc = cur;
-    double2* Zc = cur + m;
-    MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, n, a, lda, Zc, l2, Tc, l2));
-    MPDO_CUDA_TRY(gemm64(st, OP_C, OP_N, m, 2 * m, n, Zc, l2, Tc, l2, wk.s, l2));
+    const int final_pass = (pass + 1 == kPasses);
     count_launch();
-    mix_refine_kernel<<<1, 1024, 0, st>>>(m, n, wk.s, (lev0 && pass == 0) ? 1 : 0, wk.lam,
-                                          wk.scan, wk.ie);
+    sg_refine_kernel<<<gsg, RT * RT, 0, st>>>(m, n, cur, wk.s, (lev0 && pass == 0) ? 1 : 0,
+                                              final_pass, level, floor, wk.ew.counters, wk.lam,
+                                              wk.scan, wk.ie, wk.ticket);
     MPDO_CUDA_TRY(cudaGetLastError());
-    MPDO_CUDA_TRY(gemm64(st, OP_N, OP_N, n, m, m, Zc, l2, wk.ie, m, nxt + m, l2));
-    gf(n, m, n);
-    gf(m, 2 * m, n);
-    gf(n, m, m);
-    std::swap(cur, nxt);
+    if (!final_pass) {
+      // [T | Z] (I + E): two products sharing the right factor (batch of 2, offset m)
+      MPDO_CUDA_TRY(cgemm<double>(st, OP_N, OP_N, n, m, m, cur, l2, m, wk.ie, m, 0, nxt, l2, m,
+                                  2, make_double2(1, 0), make_double2(0, 0)));
+      std::swap(cur, nxt);
+    } else {
+      count_launch();
+      const dim3 gout((m + RT - 1) / RT, (n + RT - 1) / RT);
+      level_out_kernel<<<gout, RT * RT, 0, st>>>(n, m, cur + m, l2, wk.ie, wk.scan, wk.lam, v,
+                                                 ldv, w, n - m, wk.x);
+      MPDO_CUDA_TRY(cudaGetLastError());
+    }
   }
-  return cudaSuccess;
+  return cudaMemcpyAsync(wk.hpin, wk.scan, kScan * sizeof(double), cudaMemcpyDeviceToHost, st);
 }
 }  // namespace
 
@@ -232,37 +364,40 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
   double flops = 0.0;
   if (n <= 0) return cudaSuccess;
   if (n > wk.n_cap) return cudaErrorInvalidValue;
-  if (!wk.hpin) MPDO_CUDA_TRY(cudaMallocHost((void**)&wk.hpin, 8 * sizeof(double)));
-  double* hscan = wk.hpin;                          // [0..2]
-  int* hcnt = reinterpret_cast<int*>(wk.hpin + 4);  // [0..3]
-  int m = n, off = 0, level = 0;
-  double lam0 = 0.0;
+  if (!wk.hpin) MPDO_CUDA_TRY(cudaMallocHost((void**)&wk.hpin, kScan * sizeof(double)));
+  const double* hscan = wk.hpin;
+  int m = n, level = 0;
   for (;; ++level) {
-    const long l2 = 2L * m;
-    const bool lev0 = (level == 0);
     // graphs only for one-CTA sweeps (m <= 118) on a capturable stream
     bool launched = false;
-    double lflops = 0.0;
-    if (wk.use_graphs && m <= 118 && st != 0 && st != cudaStreamLegacy &&
+    if (wk.use_graphs && m <= kSmemJacobiMaxF32 && st != 0 && st != cudaStreamLegacy &&
         st != cudaStreamPerThread) {
       if (!wk.graphs) wk.graphs = new MixGraphs();
-      MixKey key{a, lda, n, m, lev0 ? 1 : 0};
+      MixKey key{a, lda, n, m, level, v, ldv, w, floor};
       auto it = wk.graphs->map.find(key);
       if (it == wk.graphs->map.end()) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          cudaError_t e2 = enqueue_level(st, n, m, lev0, a, lda, wk, lflops);
+          cudaError_t e2 = enqueue_level(st, n, m, level, a, lda, v, ldv, w, floor, wk);
           e = cudaStreamEndCapture(st, &g);
           if (e2 != cudaSuccess) e = e2;
+          // kernel nodes of the graph (the capture counted them without launching them)
           size_t nodes = 0;
           if (e == cudaSuccess) e = cudaGraphGetNodes(g, nullptr, &nodes);
-          // the capture counted its kernels without launching them
-          count_launch(-(long long)nodes);
+          std::vector<cudaGraphNode_t> list(nodes);
+          if (e == cudaSuccess && nodes) e = cudaGraphGetNodes(g, list.data(), &nodes);
+          int kernels = 0;
+          for (size_t q = 0; e == cudaSuccess && q < nodes; ++q) {
+            cudaGraphNodeType ty;
+            e = cudaGraphNodeGetType(list[q], &ty);
+            if (e == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+          }
+          count_launch(-(long long)kernels);
           cudaGraphExec_t ex = nullptr;
           if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
           if (g) cudaGraphDestroy(g);
-          if (e == cudaSuccess) it = wk.graphs->map.emplace(key, std::make_pair(ex, (int)nodes)).first;
+          if (e == cudaSuccess) it = wk.graphs->map.emplace(key, std::make_pair(ex, kernels)).first;
         }
         if (e != cudaSuccess) {
           cudaGetLastError();
@@ -275,44 +410,18 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
         launched = true;
       }
     }
-    if (!launched) MPDO_CUDA_TRY(enqueue_level(st, n, m, lev0, a, lda, wk, lflops));
-    // flops of the level's products (same count whether captured or not)
-    {
-      auto gfl = [&](int mm, int nn, int kk) { flops += 8.0 * mm * nn * (double)kk; };
-      if (!lev0) { gfl(n, m, n); gfl(m, m, n); gfl(n, m, m); }
-      for (int pass = 0; pass < kPasses; ++pass) {
-        gfl(n, m, n);
-        gfl(m, 2 * m, n);
-        gfl(n, m, m);
-      }
-    }
-    double2* Z = mix_result(wk, m);   // refined vectors
-    MPDO_CUDA_TRY(cudaMemcpyAsync(hscan, wk.scan, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MPDO_CUDA_TRY(cudaMemcpyAsync(hcnt, wk.ew.counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (!launched) MPDO_CUDA_TRY(enqueue_level(st, n, m, level, a, lda, v, ldv, w, floor, wk));
     if (wk.block_ev) {
       MPDO_CUDA_TRY(cudaEventRecord(wk.block_ev, st));
       MPDO_CUDA_TRY(cudaEventSynchronize(wk.block_ev));
     } else {
       MPDO_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    flops += hcnt[3] * eig_flops_per_count(m, false);
-    if (level == 0) lam0 = hscan[0];
-    int nl = (int)hscan[1];
-    const bool last = (nl >= m) || level + 1 >= kMaxLevels || !(hscan[2] > floor * lam0) ||
-                      nl == 0;
-    const int take = last ? m : nl;
-    // final columns and values of this level
-    MPDO_CUDA_TRY(cudaMemcpy2DAsync(v + off, ldv * sizeof(double2), Z, l2 * sizeof(double2),
-                                    take * sizeof(double2), n, cudaMemcpyDeviceToDevice, st));
-    MPDO_CUDA_TRY(cudaMemcpyAsync(w + off, wk.lam, take * sizeof(double),
-                                  cudaMemcpyDeviceToDevice, st));
-    off += take;
-    if (last) break;
-    // the unresolved columns become the next basis
-    const int mr = m - nl;
-    MPDO_CUDA_TRY(cudaMemcpy2DAsync(wk.x, mr * sizeof(double2), Z + nl, l2 * sizeof(double2),
-                                    mr * sizeof(double2), n, cudaMemcpyDeviceToDevice, st));
-    m = mr;
+    flops += level_flops(n, m, level == 0) + hscan[5] * eig_flops_per_count(m, false);
+    const int nl = (int)hscan[1];
+    // the device decided (scan[6]); the bounds below only guard the host loop
+    if (hscan[6] != 0.0 || nl <= 0 || nl >= m || level + 1 >= kMaxLevels) break;
+    m -= nl;
   }
   if (levels_out) *levels_out = level + 1;
   if (flops_out) *flops_out = flops;

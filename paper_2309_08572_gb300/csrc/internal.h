@@ -49,6 +49,13 @@ template <typename R>
 cudaError_t heig(cudaStream_t st, int n, const cx<R>* a, long lda, cx<R>* v, long ldv,
                  double* w, EigWork<R>& work, int max_sweeps);
 
+// One-CTA FP32 Jacobi solve (n <= kSmemJacobiMaxF32) of a Hermitian matrix of precision RI
+// (rounded to FP32 on load), eigenvectors written in precision RO; w, counters as for heig.
+constexpr int kSmemJacobiMaxF32 = 118;
+template <typename RI, typename RO>
+cudaError_t heig_smem_f32(cudaStream_t st, int n, const cx<RI>* a, long lda, cx<RO>* v, long ldv,
+                          double* w, int* counters, int max_sweeps);
+
 // One-sided Jacobi on the n x r factor L (row-major, ld lr; r <= 128) of W = L L^+, computed
 // in precision R in one CTA's shared memory (n * r * sizeof(cx<R>) <= kOsjMaxSmem, plus the
 // FP64 copy with finish64): U (n x r, ld ldu) = eigenvectors of W, w (r) = eigenvalues,
@@ -66,6 +73,7 @@ struct MixWork {
   double2 *x = nullptr, *tz = nullptr, *tz2 = nullptr, *s = nullptr, *ie = nullptr;
   float2 *a32 = nullptr, *y32 = nullptr;
   double *lam = nullptr, *w32 = nullptr, *scan = nullptr;
+  unsigned int* ticket = nullptr;   // CTA ticket of the fused refinement (0 between launches)
   EigWork<float> ew;
   MixGraphs* graphs = nullptr;   // created on first use; freed by mix_work_release
   bool use_graphs = true;

@@ -325,12 +325,14 @@ __global__ void eig_finalize_kernel(int n, int np, const cx<R>* __restrict__ ap,
 // phase factored out): rotation parameters, then one pass over the 2x2 blocks of A (row
 // and column rotation together) and the columns of V, with a block barrier after each.  Rotations act on A itself (two-sided),
 // so eigenvectors are accurate to eps |A| / gap.  Used for n <= smem_jacobi_max<R>().
+// The input (precision RI) is rounded to R on load and the eigenvectors are written in
+// precision RO, so a solve of an FP64 matrix in FP32 sweeps needs no conversion launches.
 constexpr int SJ_THREADS = 1024;
 
-template <typename R>
+template <typename R, typename RI, typename RO>
 __global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
-                                                                 const cx<R>* __restrict__ a,
-                                                                 long lda, cx<R>* v, long ldv,
+                                                                 const cx<RI>* __restrict__ a,
+                                                                 long lda, cx<RO>* v, long ldv,
                                                                  double* w, int* counters,
                                                                  int max_sweeps) {
   using T = cx<R>;
@@ -349,7 +351,12 @@ __global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
   const int half = np / 2;
   for (int e = tid; e < np * np; e += nthr) {
     int i = e / np, j = e % np;
-    A[e] = (i < n && j < n) ? a[(long)i * lda + j] : mkc<R>(0, 0);
+    T z = mkc<R>(0, 0);
+    if (i < n && j < n) {
+      const cx<RI> t = a[(long)i * lda + j];
+      z = mkc<R>((R)t.x, (R)t.y);
+    }
+    A[e] = z;
     V[e] = mkc<R>(i == j ? 1 : 0, 0);
   }
   if (tid == 0) s_anorm = 0;
@@ -472,7 +479,8 @@ __global__ void __launch_bounds__(SJ_THREADS) jacobi_smem_kernel(int n, int np,
     int i = e / n, k = e % n;
     int col = s_val[k];
     col = (col >= 0 && col < n) ? col : k;
-    v[(long)i * ldv + k] = V[(size_t)i * np + col];
+    const T t = V[(size_t)i * np + col];
+    v[(long)i * ldv + k] = mkc<RO>((RO)t.x, (RO)t.y);
   }
   if (tid == 0 && counters) {
     counters[2] = sweep;
@@ -490,7 +498,37 @@ inline int padded_n(int n) {
   return nblk * JW;
 }
 
+template <typename R, typename RI, typename RO>
+cudaError_t smem_jacobi_launch(cudaStream_t st, int n, const cx<RI>* a, long lda, cx<RO>* v,
+                               long ldv, double* w, int* counters, int max_sweeps) {
+  const int np2 = n + (n & 1);
+  const size_t sm = 2ull * np2 * np2 * sizeof(cx<R>);
+  const int smax = smem_jacobi_max<R>() + (smem_jacobi_max<R>() & 1);
+  // once per instantiation (a thread-safe static initialiser)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      jacobi_smem_kernel<R, RI, RO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(2ull * smax * smax * sizeof(cx<R>)));
+  MPDO_CUDA_TRY(attr);
+  count_launch();
+  const int thr = std::min(SJ_THREADS, std::max(64, ((np2 / 2) * np2 + 31) / 32 * 32));
+  jacobi_smem_kernel<R, RI, RO><<<1, thr, sm, st>>>(n, np2, a, lda, v, ldv, w, counters,
+                                                    max_sweeps);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+template <typename RI, typename RO>
+cudaError_t heig_smem_f32(cudaStream_t st, int n, const cx<RI>* a, long lda, cx<RO>* v, long ldv,
+                          double* w, int* counters, int max_sweeps) {
+  if (n <= 0) return cudaSuccess;
+  if (n > kSmemJacobiMaxF32) return cudaErrorInvalidValue;
+  return smem_jacobi_launch<float, RI, RO>(st, n, a, lda, v, ldv, w, counters, max_sweeps);
+}
+template cudaError_t heig_smem_f32<double, double>(cudaStream_t, int, const double2*, long,
+                                                   double2*, long, double*, int*, int);
+template cudaError_t heig_smem_f32<double, float>(cudaStream_t, int, const double2*, long,
+                                                  float2*, long, double*, int*, int);
 
 int eig_padded_n(int n) { return padded_n(n); }
 
@@ -524,24 +562,8 @@ cudaError_t heig(cudaStream_t st, int n, const cx<R>* a, long lda, cx<R>* v, lon
                  double* w, EigWork<R>& work, int max_sweeps) {
   if (n <= 0) return cudaSuccess;
   if (n > work.n_cap) return cudaErrorInvalidValue;
-  if (n <= smem_jacobi_max<R>()) {
-    int np2 = n + (n & 1);
-    size_t sm = 2ull * np2 * np2 * sizeof(cx<R>);
-    static bool attr_set = false;
-    if (!attr_set) {
-      MPDO_CUDA_TRY(cudaFuncSetAttribute(jacobi_smem_kernel<R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2ull * 118 * 118 * sizeof(float2) > 2ull * 84 * 84 * sizeof(double2)
-                                                   ? 2ull * 118 * 118 * sizeof(float2)
-                                                   : 2ull * 84 * 84 * sizeof(double2))));
-      attr_set = true;
-    }
-    count_launch();
-    int thr = std::min(SJ_THREADS, std::max(64, ((np2 / 2) * np2 + 31) / 32 * 32));
-    jacobi_smem_kernel<R><<<1, thr, sm, st>>>(n, np2, a, lda, v, ldv, w, work.counters,
-                                              max_sweeps);
-    return cudaGetLastError();
-  }
+  if (n <= smem_jacobi_max<R>())
+    return smem_jacobi_launch<R, R, R>(st, n, a, lda, v, ldv, w, work.counters, max_sweeps);
   int np = padded_n(n);
   int nblk = np / JW;
   long total = (long)np * np;
