@@ -35,6 +35,10 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The batch executor runs one stream per circuit in flight; with the default 8 hardware
+# work queues, streams share queues and wait on each other's launches.  Read when the
+# CUDA context is created, so it is set before torch initialises CUDA.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import synth  # noqa: E402
 

@@ -153,7 +153,10 @@ int mpdo_reconfigure(mpdo_t h, int n_sites, int chi_max, int k_max, int use_ppt,
  * device-resident layers in order (each must have been uploaded by a handle of the same
  * precision on the same device) and evaluates the TFIM energy; out[4i..4i+3] = e_raw,
  * e_success, success_prob, trace; status[i] (may be NULL) = its return code.  The pool
- * handles must be distinct and not used by other threads during the call. */
+ * handles must be distinct and not used by other threads during the call.  The driver
+ * maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware queues (default 8); with more
+ * handles than queues, streams that share a queue wait on each other's launches, so set
+ * it (up to 32) in the environment before the process creates its CUDA context. */
 typedef struct {
   int n_sites, chi_max, k_max, use_ppt;
   int n_layers;
