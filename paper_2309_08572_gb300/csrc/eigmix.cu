@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(RT * RT) sg_refine_kernel(
 __global__ void __launch_bounds__(RT * RT) level_out_kernel(
     int n, int m, const double2* __restrict__ Z, long ldz, const double2* __restrict__ IE,
     const double* scan, const double* lam, double2* v, long ldv, double* w, int off,
-    double2* x) {
+    double2* x, double* hscan) {
   __shared__ double2 As[RT][RT + 1];   // [k][row]
   __shared__ double2 Bs[RT][RT + 1];   // [k][col]
   const int tx = threadIdx.x % RT, ty = threadIdx.x / RT;
@@ -195,6 +195,11 @@ __global__ void __launch_bounds__(RT * RT) level_out_kernel(
       x[(long)r * mr + (j - nl)] = acc;
   }
   if (blockIdx.y == 0 && ty == 0 && j < take) w[off + j] = lam[j];
+  // the level's scalars, straight into the mapped host area (no copy launch)
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < kScan) {
+    hscan[threadIdx.x] = scan[threadIdx.x];
+    __threadfence_system();
+  }
 }
 
 cudaError_t gemm64(cudaStream_t st, int opa, int opb, int m, int n, int k, const double2* A,
@@ -206,7 +211,8 @@ cudaError_t gemm64(cudaStream_t st, int opa, int opb, int m, int n, int k, const
 }  // namespace
 
 // One captured graph per level shape: (input matrix, n, m, level, outputs, floor).  The
-// launches of a level and its read-back run as one graph launch instead of ~8.
+// launches of a level run as one graph launch instead of ~8; its scalars reach the host
+// through mapped pinned memory, written by the level's last kernel.
 struct MixKey {
   const void* a;
   long lda;
@@ -242,6 +248,7 @@ struct MixGraphs {
 void mix_work_release(MixWork& w) {
   if (w.hpin) cudaFreeHost(w.hpin);
   w.hpin = nullptr;
+  w.hpin_dev = nullptr;
   if (!w.graphs) return;
   for (auto& kv : w.graphs->map) cudaGraphExecDestroy(kv.second.first);
   delete w.graphs;
@@ -293,8 +300,8 @@ double level_flops(int n, int m, bool lev0) {
   return f;
 }
 
-// The launches of one level, ending with the copy of its scalars to the pinned host area
-// (no host synchronisation inside, so a level can be captured as one graph).  Level 0 reads
+// The launches of one level; its last kernel also writes the level's scalars to the mapped
+// host area (no host synchronisation inside, so a level can be captured as one graph).  Level 0 reads
 // B = A; later levels project on the basis in wk.x, which the level's last product replaces
 // with the unresolved columns.  The refinement carries T along: after a pass,
 // [T | Z] <- [T | Z] (I + E) = [A Z' | Z'], so A enters only the first product.
@@ -350,11 +357,11 @@ cudaError_t enqueue_level(cudaStream_t st, int n, int m, int level, const double
       count_launch();
       const dim3 gout((m + RT - 1) / RT, (n + RT - 1) / RT);
       level_out_kernel<<<gout, RT * RT, 0, st>>>(n, m, cur + m, l2, wk.ie, wk.scan, wk.lam, v,
-                                                 ldv, w, n - m, wk.x);
+                                                 ldv, w, n - m, wk.x, wk.hpin_dev);
       MPDO_CUDA_TRY(cudaGetLastError());
     }
   }
-  return cudaMemcpyAsync(wk.hpin, wk.scan, kScan * sizeof(double), cudaMemcpyDeviceToHost, st);
+  return cudaSuccess;
 }
 }  // namespace
 
@@ -364,7 +371,10 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
   double flops = 0.0;
   if (n <= 0) return cudaSuccess;
   if (n > wk.n_cap) return cudaErrorInvalidValue;
-  if (!wk.hpin) MPDO_CUDA_TRY(cudaMallocHost((void**)&wk.hpin, kScan * sizeof(double)));
+  if (!wk.hpin) {
+    MPDO_CUDA_TRY(cudaHostAlloc((void**)&wk.hpin, kScan * sizeof(double), cudaHostAllocMapped));
+    MPDO_CUDA_TRY(cudaHostGetDevicePointer((void**)&wk.hpin_dev, wk.hpin, 0));
+  }
   const double* hscan = wk.hpin;
   int m = n, level = 0;
   for (;; ++level) {

@@ -78,7 +78,8 @@ struct MixWork {
   MixGraphs* graphs = nullptr;   // created on first use; freed by mix_work_release
   bool use_graphs = true;
   cudaEvent_t block_ev = nullptr; // when set, level read-backs wait on it (blocking sync)
-  double* hpin = nullptr;         // pinned host landing area of the read-backs (lazy)
+  double* hpin = nullptr;         // mapped pinned host area of the level scalars (lazy)
+  double* hpin_dev = nullptr;     // its device address
 };
 size_t mix_work_bytes(int n_cap);
 void mix_work_bind(MixWork& w, void* base, int n_cap);
