@@ -22,9 +22,13 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace mpdo {
 
@@ -122,23 +126,31 @@ constexpr int RT = 16;   // output tile of the fused products (one element per t
 
 // [S | G] = Z^+ [T | Z] (m x 2m, row stride 2m) from TZ = [T | Z] (n x 2m, row stride 2m),
 // then the refinement step, run by the CTA that finishes last (a ticket counter in global
-// memory; no CTA waits on another).  The ticket returns to 0 for the next launch.
+// memory; no CTA waits on another).  The ticket returns to 0 for the next launch.  FP64
+// runs at 2 FMA per clock per SM, so each output tile's K loop (over n) is split over the
+// CTAs of a thread-block cluster (dims (splits, 1, 1)); the partial sums meet in rank 0
+// through distributed shared memory, added in rank order.
 __global__ void __launch_bounds__(RT * RT) sg_refine_kernel(
     int m, int n, const double2* __restrict__ TZ, double2* SG, int level0, int final_pass,
     int level, double floor, const int* rot, double* lam, double* scan, double2* IE,
-    unsigned int* ticket) {
+    unsigned int* ticket, int splits) {
   __shared__ double2 As[RT][RT + 1];   // [k][i]
   __shared__ double2 Bs[RT][RT + 1];   // [k][j]
+  __shared__ double2 part[RT * RT];
   __shared__ int s_last;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int s = (int)cluster.block_rank();
   const int tx = threadIdx.x % RT, ty = threadIdx.x / RT;
-  const int i0 = blockIdx.y * RT, j0 = blockIdx.x * RT;
+  const int i0 = blockIdx.y * RT, j0 = (blockIdx.x / splits) * RT;
   const long ld = 2L * m;
+  const int kc = ((n + splits * RT - 1) / (splits * RT)) * RT;
+  const int kb = s * kc, ke = min(n, kb + kc);
   double2 acc = make_double2(0.0, 0.0);
-  for (int k0 = 0; k0 < n; k0 += RT) {
+  for (int k0 = kb; k0 < ke; k0 += RT) {
     const int k = k0 + ty;
     double2 za = make_double2(0.0, 0.0), tb = make_double2(0.0, 0.0);
-    if (k < n && i0 + tx < m) za = cconj(TZ[(long)k * ld + m + i0 + tx]);
-    if (k < n && j0 + tx < 2 * m) tb = TZ[(long)k * ld + j0 + tx];
+    if (k < ke && i0 + tx < m) za = cconj(TZ[(long)k * ld + m + i0 + tx]);
+    if (k < ke && j0 + tx < 2 * m) tb = TZ[(long)k * ld + j0 + tx];
     As[ty][tx] = za;
     Bs[ty][tx] = tb;
     __syncthreads();
@@ -146,11 +158,19 @@ __global__ void __launch_bounds__(RT * RT) sg_refine_kernel(
     for (int kk = 0; kk < RT; ++kk) cfma(acc, As[kk][ty], Bs[kk][tx]);
     __syncthreads();
   }
-  if (i0 + ty < m && j0 + tx < 2 * m) SG[(long)(i0 + ty) * ld + j0 + tx] = acc;
+  part[threadIdx.x] = acc;
+  cluster.sync();
+  if (s == 0) {
+    double2 sum = part[threadIdx.x];
+    for (int q = 1; q < splits; ++q) sum = cadd(sum, cluster.map_shared_rank(part, q)[threadIdx.x]);
+    if (i0 + ty < m && j0 + tx < 2 * m) SG[(long)(i0 + ty) * ld + j0 + tx] = sum;
+  }
+  cluster.sync();   // rank 0 has read every partial before the cluster leaves
+  if (s != 0) return;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int total = gridDim.x * gridDim.y;
+    const unsigned int total = (gridDim.x / splits) * gridDim.y;
     s_last = (atomicAdd(ticket, 1u) == total - 1);
   }
   __syncthreads();
@@ -158,6 +178,14 @@ __global__ void __launch_bounds__(RT * RT) sg_refine_kernel(
   __threadfence();
   refine_step(m, n, SG, level0, final_pass, level, floor, rot, lam, scan, IE);
   if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// K slices of a small FP64 product: enough to bring the CTAs towards one per SM, each
+// slice at least 32 long, at most 8 (portable cluster size).
+inline int split_count(long tiles, int K) {
+  int s = 1;
+  while (s < 8 && tiles * (2 * s) <= 152 && K >= 32 * (2 * s)) s *= 2;
+  return s;
 }
 
 // The level's last product Z' = Z (I + E) (Z: n x m, row stride ldz), routed by the level's
@@ -341,13 +369,27 @@ cudaError_t enqueue_level(cudaStream_t st, int n, int m, int level, const double
   double2* cur = wk.tz;
   double2* nxt = wk.tz2;
   const dim3 gsg((2 * m + RT - 1) / RT, (m + RT - 1) / RT);
+  const int splits = split_count((long)gsg.x * gsg.y, n);
   for (int pass = 0; pass < kPasses; ++pass) {
     const int final_pass = (pass + 1 == kPasses);
     count_launch();
-    sg_refine_kernel<<<gsg, RT * RT, 0, st>>>(m, n, cur, wk.s, (lev0 && pass == 0) ? 1 : 0,
-                                              final_pass, level, floor, wk.ew.counters, wk.lam,
-                                              wk.scan, wk.ie, wk.ticket);
-    MPDO_CUDA_TRY(cudaGetLastError());
+    {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(gsg.x * splits, gsg.y);
+      cfg.blockDim = dim3(RT * RT);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = splits;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      MPDO_CUDA_TRY(cudaLaunchKernelEx(&cfg, sg_refine_kernel, m, n, (const double2*)cur, wk.s,
+                                       (lev0 && pass == 0) ? 1 : 0, final_pass, level, floor,
+                                       (const int*)wk.ew.counters, wk.lam, wk.scan, wk.ie,
+                                       wk.ticket, splits));
+    }
     if (!final_pass) {
       // [T | Z] (I + E): two products sharing the right factor (batch of 2, offset m)
       MPDO_CUDA_TRY(cgemm<double>(st, OP_N, OP_N, n, m, m, cur, l2, m, wk.ie, m, 0, nxt, l2, m,

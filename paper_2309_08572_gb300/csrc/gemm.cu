@@ -2,8 +2,12 @@
 // C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b]; op in {N, T, C (conj-transpose),
 // R (conj, no transpose)}.  Used by every contraction of the update for the FP64 and
 // C64 modes and for the unit tests of the other GEMM paths.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace mpdo {
 
@@ -141,6 +145,78 @@ __global__ void __launch_bounds__(ST * ST) cgemm_small_kernel(
     *p = v;
   }
 }
+
+// Split-K form of the 16 x 16 tile kernel for FP64 products with few output tiles and a
+// long K: FP64 runs at 2 FMA per clock per SM, so one tile's K loop is spread over the
+// CTAs of a thread-block cluster (cluster dims (splits, 1, 1): CTA rank s takes the s-th
+// K slice).  The partial sums meet in rank 0's registers through distributed shared
+// memory, added in rank order, so the result does not depend on scheduling.
+template <typename RA, typename RB, typename R>
+__global__ void __launch_bounds__(ST * ST) cgemm_small_split_kernel(
+    int M, int N, int K, const cx<RA>* __restrict__ A, long sam, long sak, long sab, int conja,
+    const cx<RB>* __restrict__ B, long sbk, long sbn, long sbb, int conjb, cx<R>* C, long scm,
+    long scn, long scb, cx<R> alpha, cx<R> beta, int use_beta, int splits) {
+  using T = cx<R>;
+  __shared__ T As[ST][ST + 1];
+  __shared__ T Bs[ST][ST + 1];
+  __shared__ T part[ST * ST];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int s = (int)cluster.block_rank();
+  const int tx = threadIdx.x % ST, ty = threadIdx.x / ST;
+  const int m0 = blockIdx.y * ST, n0 = (blockIdx.x / splits) * ST;
+  const long bz = blockIdx.z;
+  A += bz * sab;
+  B += bz * sbb;
+  C += bz * scb;
+  // K slices: whole multiples of ST, rank order
+  const int kc = ((K + splits * ST - 1) / (splits * ST)) * ST;
+  const int kb = s * kc, ke = min(K, kb + kc);
+  T acc = mkc<R>(0, 0);
+  for (int k0 = kb; k0 < ke; k0 += ST) {
+    {
+      int gm = m0 + ty, gk = k0 + tx;
+      T v = mkc<R>(0, 0);
+      if (gm < M && gk < ke) {
+        cx<RA> t = A[gm * sam + gk * sak];
+        v = mkc<R>((R)t.x, conja ? -(R)t.y : (R)t.y);
+      }
+      As[tx][ty] = v;
+      int gk2 = k0 + ty, gn = n0 + tx;
+      T u = mkc<R>(0, 0);
+      if (gn < N && gk2 < ke) {
+        cx<RB> t = B[gk2 * sbk + gn * sbn];
+        u = mkc<R>((R)t.x, conjb ? -(R)t.y : (R)t.y);
+      }
+      Bs[ty][tx] = u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < ST; ++kk) cfma(acc, As[kk][ty], Bs[kk][tx]);
+    __syncthreads();
+  }
+  part[threadIdx.x] = acc;
+  cluster.sync();
+  if (s == 0) {
+    T sum = part[threadIdx.x];
+    for (int q = 1; q < splits; ++q) sum = cadd(sum, cluster.map_shared_rank(part, q)[threadIdx.x]);
+    const int gm = m0 + ty, gn = n0 + tx;
+    if (gm < M && gn < N) {
+      T v = cmul(alpha, sum);
+      T* p = C + gm * scm + gn * scn;
+      if (use_beta) v = cadd(v, cmul(beta, *p));
+      *p = v;
+    }
+  }
+  cluster.sync();   // rank 0 has read every partial before the cluster leaves
+}
+
+// Number of K slices for a small-tile FP64 product: enough to bring the tiles of the grid
+// towards one per SM, each slice at least 32 long, at most 8 (portable cluster size).
+inline int split_count(long tiles, int K) {
+  int s = 1;
+  while (s < 8 && tiles * (2 * s) <= 152 && K >= 32 * (2 * s)) s *= 2;
+  return s;
+}
 }  // namespace
 
 template <typename RA, typename RB, typename R>
@@ -161,6 +237,30 @@ cudaError_t cgemm_impl(cudaStream_t st, int opa, int opb, int m, int n, int k, c
   for (int b0 = 0; b0 < batch; b0 += 65535) {
     int nb = batch - b0 < 65535 ? batch - b0 : 65535;
     count_launch();
+    if (small && sizeof(R) == 8) {
+      const long tiles = (long)((n + ST - 1) / ST) * ((m + ST - 1) / ST) * nb;
+      const int splits = split_count(tiles, k);
+      if (splits > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(((n + ST - 1) / ST) * splits, (m + ST - 1) / ST, nb);
+        cfg.blockDim = dim3(ST * ST);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = splits;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(
+            &cfg, cgemm_small_split_kernel<RA, RB, R>, m, n, k, A + (long)b0 * sa, sam, sak, sa,
+            conja, B + (long)b0 * sb, sbk, sbn, sb, conjb, C + (long)b0 * sc, (long)ldc, 1L, sc,
+            alpha, beta, use_beta, splits);
+        if (e != cudaSuccess) return e;
+        continue;
+      }
+    }
     if (small) {
       dim3 g2((n + ST - 1) / ST, (m + ST - 1) / ST, nb);
       cgemm_small_kernel<RA, RB, R><<<g2, ST * ST, 0, st>>>(
