@@ -1,7 +1,13 @@
 // Elementwise and small kernels of the MPDO update, observables and sampling.
 // Every kernel here is memory- or latency-bound; the contractions are in gemm.cu.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace mpdo {
 namespace {
@@ -449,27 +455,39 @@ __global__ void dual_rows_kernel(int kk, int cols, const cx<R>* __restrict__ y, 
   }
 }
 
-// Pivoted Cholesky of the Hermitian PSD n x n matrix w (precision R, n <= 1024, one CTA):
-// W ~ L L^+ with L n x r (row-major, row stride lr), greedy diagonal pivoting, stopping once
-// the largest remaining diagonal is <= tol * tr W or after rmax (<= 128) columns.
+// Pivoted Cholesky of the Hermitian PSD n x n matrix w (precision R, n <= 1024): W ~ L L^+
+// with L n x r (row-major, row stride lr), greedy diagonal pivoting, stopping once the
+// largest remaining diagonal is <= tol * tr W or after rmax (<= 128) columns.
 // *rout = r; *resid = largest remaining diagonal / tr W.
+// The rows are shared out over the CTAs of a thread-block cluster (row i belongs to rank
+// i mod S; FP64 runs at 2 FMA per clock per SM, so the column updates want several SMs).
+// Per column, one cluster barrier: each CTA posts its best remaining diagonal in shared
+// memory (two slots, alternating by column, so a slot is rewritten only after every CTA
+// has passed the next barrier), then every CTA reads all posts through distributed shared
+// memory and takes the same pivot.  Sums and the pivot choice follow rank order, so the
+// factor does not depend on scheduling.
 template <typename R>
 __global__ void __launch_bounds__(1024) pchol_kernel(int n, const cx<R>* __restrict__ w,
                                                      int rmax, double tol, cx<R>* L, int lr,
                                                      int* rout, double* resid) {
   using T = cx<R>;
-  __shared__ double d[1024];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int S = (int)cluster.num_blocks(), c = (int)cluster.block_rank();
+  __shared__ double d[1024];        // remaining diagonal of this CTA's rows (local index)
   __shared__ double rv[32];
   __shared__ int ri[32];
   __shared__ T lp[128];
-  __shared__ int s_p;
-  __shared__ double s_dp, s_tr;
+  __shared__ double post_v[2];      // this CTA's best remaining diagonal, by column parity
+  __shared__ int post_i[2];
+  __shared__ double post_tr;        // this CTA's share of the trace
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int nloc = (n - c + S - 1) / S;   // rows c, c + S, ...
   double tp = 0.0;
-  for (int i = tid; i < n; i += blockDim.x) {
+  for (int li = tid; li < nloc; li += blockDim.x) {
+    const int i = c + li * S;
     double v = (double)w[(long)i * n + i].x;
-    d[i] = v > 0 ? v : 0.0;
-    tp += d[i];
+    d[li] = v > 0 ? v : 0.0;
+    tp += d[li];
   }
   for (int o = 16; o > 0; o >>= 1) tp += __shfl_xor_sync(0xffffffffu, tp, o);
   if (lane == 0) rv[wid] = tp;
@@ -477,16 +495,19 @@ __global__ void __launch_bounds__(1024) pchol_kernel(int n, const cx<R>* __restr
   if (tid == 0) {
     double t = 0;
     for (int k = 0; k < nw; ++k) t += rv[k];
-    s_tr = t;
+    post_tr = t;
   }
-  __syncthreads();
+  cluster.sync();
+  double tr = 0.0;
+  for (int q = 0; q < S; ++q) tr += *cluster.map_shared_rank(&post_tr, q);
   int r = 0;
   double last = 0.0;
   for (int j = 0; j < rmax; ++j) {
+    const int par = j & 1;
     double bv = -1.0;
     int bi = -1;
-    for (int i = tid; i < n; i += blockDim.x)
-      if (d[i] > bv) { bv = d[i]; bi = i; }
+    for (int li = tid; li < nloc; li += blockDim.x)
+      if (d[li] > bv) { bv = d[li]; bi = c + li * S; }
     for (int o = 16; o > 0; o >>= 1) {
       double ov = __shfl_xor_sync(0xffffffffu, bv, o);
       int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -498,23 +519,29 @@ __global__ void __launch_bounds__(1024) pchol_kernel(int n, const cx<R>* __restr
       double b = -1.0;
       int p = -1;
       for (int k = 0; k < nw; ++k)
-        if (rv[k] > b) { b = rv[k]; p = ri[k]; }
-      s_dp = b;
-      s_p = p;
+        if (rv[k] > b || (rv[k] == b && ri[k] >= 0 && (p < 0 || ri[k] < p))) { b = rv[k]; p = ri[k]; }
+      post_v[par] = b;
+      post_i[par] = p;
     }
-    __syncthreads();
-    const double dp = s_dp;
-    const int p = s_p;
+    cluster.sync();   // posts of column j complete; columns < j of L visible
+    double dp = -1.0;
+    int p = -1;
+    for (int q = 0; q < S; ++q) {
+      const double v = cluster.map_shared_rank(post_v, q)[par];
+      const int i = cluster.map_shared_rank(post_i, q)[par];
+      if (v > dp || (v == dp && i >= 0 && (p < 0 || i < p))) { dp = v; p = i; }
+    }
     last = dp;
-    if (!(dp > tol * s_tr) || p < 0) break;
-    for (int k = tid; k < j; k += blockDim.x) lp[k] = L[(long)p * lr + k];
+    if (!(dp > tol * tr) || p < 0) break;
+    for (int k = tid; k < j; k += blockDim.x) lp[k] = __ldcg(&L[(long)p * lr + k]);
     __syncthreads();
     const R inv = (R)(1.0 / sqrt(dp));
-    for (int i = tid; i < n; i += blockDim.x) {
+    for (int li = tid; li < nloc; li += blockDim.x) {
+      const int i = c + li * S;
       T acc = w[(long)i * n + p];
-      const T* li = L + (long)i * lr;
+      const T* lrow = L + (long)i * lr;
       for (int k = 0; k < j; ++k) {
-        T a = li[k], b = lp[k];
+        T a = lrow[k], b = lp[k];
         // acc -= a * conj(b)
         acc.x -= a.x * b.x + a.y * b.y;
         acc.y -= a.y * b.x - a.x * b.y;
@@ -522,22 +549,34 @@ __global__ void __launch_bounds__(1024) pchol_kernel(int n, const cx<R>* __restr
       T lij = mkc<R>(acc.x * inv, acc.y * inv);
       if (i == p) lij = mkc<R>((R)sqrt(dp), R(0));
       L[(long)i * lr + j] = lij;
-      double nd = (i == p) ? 0.0 : d[i] - ((double)lij.x * lij.x + (double)lij.y * lij.y);
-      d[i] = nd > 0 ? nd : 0.0;
+      double nd = (i == p) ? 0.0 : d[li] - ((double)lij.x * lij.x + (double)lij.y * lij.y);
+      d[li] = nd > 0 ? nd : 0.0;
     }
     __syncthreads();
     r = j + 1;
     last = 0.0;
   }
-  if (tid == 0) {
-    if (r == rmax) {
-      double b = 0.0;
-      for (int i = 0; i < n; ++i) b = fmax(b, d[i]);
-      last = b;
+  if (r == rmax) {
+    // largest remaining diagonal over the cluster (posted in the free slot)
+    double b = 0.0;
+    for (int li = tid; li < nloc; li += blockDim.x) b = fmax(b, d[li]);
+    for (int o = 16; o > 0; o >>= 1) b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if (lane == 0) rv[wid] = b;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int k = 0; k < nw; ++k) t = fmax(t, rv[k]);
+      post_v[rmax & 1] = t;
     }
-    *rout = r;
-    *resid = s_tr > 0 ? last / s_tr : 0.0;
+    cluster.sync();
+    last = 0.0;
+    for (int q = 0; q < S; ++q) last = fmax(last, cluster.map_shared_rank(post_v, q)[rmax & 1]);
   }
+  if (c == 0 && tid == 0) {
+    *rout = r;
+    *resid = tr > 0 ? last / tr : 0.0;
+  }
+  cluster.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 // zs[i][c] = z[i][c] / sqrt(s_c) (0 where s_c <= 0): eigenvectors of L L^+ from those of L^+ L
@@ -701,9 +740,23 @@ template <typename R>
 cudaError_t pchol(cudaStream_t st, int n, const cx<R>* w, int rmax, double tol, cx<R>* L, int lr,
                   int* rout, double* resid) {
   if (n < 1 || n > 1024 || rmax < 1 || rmax > 128) return cudaErrorInvalidValue;
+  // cluster of S CTAs, at least 32 rows each, at most 8 (portable cluster size)
+  const int S = std::min(8, std::max(1, n / 32));
+  const int rows = (n + S - 1) / S;
+  const int threads = std::min(1024, std::max(64, (rows + 31) / 32 * 32));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(S);
+  cfg.blockDim = dim3(threads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = S;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
   count_launch();
-  pchol_kernel<R><<<1, 1024, 0, st>>>(n, w, rmax, tol, L, lr, rout, resid);
-  return cudaGetLastError();
+  return cudaLaunchKernelEx(&cfg, pchol_kernel<R>, n, w, rmax, tol, L, lr, rout, resid);
 }
 template cudaError_t pchol<float>(cudaStream_t, int, const float2*, int, double, float2*, int,
                                   int*, double*);
