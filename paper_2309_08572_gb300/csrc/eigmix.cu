@@ -181,10 +181,10 @@ __global__ void __launch_bounds__(RT * RT) sg_refine_kernel(
 }
 
 // K slices of a small FP64 product: enough to bring the CTAs towards one per SM, each
-// slice at least 32 long, at most 8 (portable cluster size).
+// slice at least 16 long (one tile step), at most 8 (portable cluster size).
 inline int split_count(long tiles, int K) {
   int s = 1;
-  while (s < 8 && tiles * (2 * s) <= 152 && K >= 32 * (2 * s)) s *= 2;
+  while (s < 8 && tiles * (2 * s) <= 152 && K >= 16 * (2 * s)) s *= 2;
   return s;
 }
 

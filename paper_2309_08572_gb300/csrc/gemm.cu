@@ -211,10 +211,11 @@ __global__ void __launch_bounds__(ST * ST) cgemm_small_split_kernel(
 }
 
 // Number of K slices for a small-tile FP64 product: enough to bring the tiles of the grid
-// towards one per SM, each slice at least 32 long, at most 8 (portable cluster size).
+// towards one per SM, each slice at least 16 long (one tile step), at most 8 (portable
+// cluster size).
 inline int split_count(long tiles, int K) {
   int s = 1;
-  while (s < 8 && tiles * (2 * s) <= 152 && K >= 32 * (2 * s)) s *= 2;
+  while (s < 8 && tiles * (2 * s) <= 152 && K >= 16 * (2 * s)) s *= 2;
   return s;
 }
 }  // namespace
