@@ -11,8 +11,9 @@ concurrently through the library's batch executor (one CUDA stream and host thre
 circuit in flight); the single-circuit latency is reported beside it.
 
 value  = two-site updates per second, whole job (all ranks), device-resident inputs.
-e2e    = the same metric through the host-buffer API (ops uploaded every step, energies
-         read back), wall clock.
+e2e    = the same metric through the host-buffer API (mpdo_batch_run_host: every step
+         each worker converts its circuit's ops, copies them from pinned host memory and
+         runs them; energies read back), wall clock.
 Also reported: QAOA energy evaluations per second, the roofline of the dominant kernel
 class, the CPU oracle on a bounded sample (cpu_baseline), SM clocks during the timed
 region, and the kernel launch count.
@@ -353,19 +354,17 @@ def run_ours(args):
         h2d = sum(sum((2 * k.shape[0] * 81 * 8 + 2 * 729 * 16) for _, k in layer)
                   for L in host_layers for layer in L)
     d2h = args.batch * (4 * 8 + updates * 2 * STEP_SCALARS_BYTES + c.p * DEV_STATS_BYTES)
+    # the circuits' ops in host memory, in the C ABI's layout (marshalled once, untimed)
+    hosts = [lib.HostCircuit(ci.n_sites, ci.chi_max, ci.k_max, L, J=ci.J, hx=ci.hx, b=ci.bz)
+             for ci, L in zip(circs, host_layers)]
     torch.cuda.synchronize()
     te = []
     for _ in range(max(1, args.steps)):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        fresh = [[pool[0].upload_layer(layer) for layer in L] for L in host_layers]
-        dd = [dict(dsc, layers=f) for dsc, f in zip(descs, fresh)]
-        lib.batch_run(pool, dd)
+        lib.batch_run_host(pool, hosts)
         te.append(time.perf_counter() - t0)
-        for f in fresh:
-            for dl in f:
-                pool[0].free_uploaded(dl)
     e2e_ms = 1e3 * sum(te)
     if dist:
         t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)

@@ -166,6 +166,21 @@ typedef struct {
 int mpdo_batch_run(int n_handles, mpdo_t* handles, int n_circuits, const mpdo_circuit* circuits,
                    double* out, int* status);
 
+/* The same executor for circuits given as host layers (as for mpdo_apply_layer): each
+ * worker converts its circuit's layers and copies them into its handle's staging buffer
+ * on the handle's stream, layer by layer, so one circuit's uploads overlap the other
+ * circuits' kernels.  Inputs are read only during the call; errors as for
+ * mpdo_batch_run (an invalid or non-finite op fails its circuit with MPDO_ERR_ARG or
+ * MPDO_ERR_NUMERIC). */
+typedef struct {
+  int n_sites, chi_max, k_max, use_ppt;
+  int n_layers;
+  const mpdo_layer* layers;   /* host layers, n_layers of them */
+  double J, hx, b;
+} mpdo_circuit_host;
+int mpdo_batch_run_host(int n_handles, mpdo_t* handles, int n_circuits,
+                        const mpdo_circuit_host* circuits, double* out, int* status);
+
 /* Current bond dimensions (host int[N-1]), inner dimensions (host int[N]) and centre. */
 int mpdo_get_dims(mpdo_t h, int* bond_dims, int* kraus_dims, int* centre);
 

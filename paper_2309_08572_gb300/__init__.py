@@ -50,6 +50,12 @@ class CircuitDesc(C.Structure):
                 ("J", C.c_double), ("hx", C.c_double), ("b", C.c_double)]
 
 
+class CircuitHostDesc(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("chi_max", C.c_int), ("k_max", C.c_int),
+                ("use_ppt", C.c_int), ("n_layers", C.c_int), ("layers", C.POINTER(Layer)),
+                ("J", C.c_double), ("hx", C.c_double), ("b", C.c_double)]
+
+
 class TruncStats(C.Structure):
     _fields_ = [("disc_bond_w", C.c_double), ("disc_kraus_w", C.c_double),
                 ("ppt_theta_min", C.c_double), ("ppt_infeasible", C.c_int),
@@ -80,6 +86,7 @@ def _load():
         "mpdo_get_dims": (I, [VP, P(I), P(I), P(I)]),
         "mpdo_reconfigure": (I, [VP, I, I, I, I, P(D)]),
         "mpdo_batch_run": (I, [I, P(VP), I, P(CircuitDesc), P(D), P(I)]),
+        "mpdo_batch_run_host": (I, [I, P(VP), I, P(CircuitHostDesc), P(D), P(I)]),
         "mpdo_get_site": (I, [VP, I, P(D), S, P(I)]),
         "mpdo_destroy": (I, [VP]),
         "mpdo_last_error": (C.c_char_p, [VP]),
@@ -347,6 +354,35 @@ def batch_run(pool: Sequence["Mpdo"], circuits: Sequence[dict]) -> np.ndarray:
     status = np.zeros(len(circuits), dtype=np.int32)
     rc = LIB.mpdo_batch_run(len(pool), handles, len(circuits), descs, _dptr(out),
                             status.ctypes.data_as(C.POINTER(C.c_int)))
+    if rc != 0:
+        bad = [(i, int(x)) for i, x in enumerate(status) if x]
+        msg = LIB.mpdo_last_error(None)
+        raise MpdoError(rc, f"{msg.decode() if msg else ''}; failed circuits {bad[:8]}")
+    return out
+
+
+class HostCircuit:
+    """A circuit's layers marshalled once into the C ABI's host layout (host memory), for
+    batch_run_host: n_sites, chi_max, k_max, layers (op lists as for Mpdo.apply_layer),
+    use_ppt, J, hx, b."""
+
+    def __init__(self, n_sites: int, chi_max: int, k_max: int, layers, use_ppt: bool = True,
+                 J: float = 1.0, hx: float = 1.0, b: float = 0.0):
+        self._args = [_LayerArgs(ops) for ops in layers]
+        self._layers = (Layer * max(1, len(self._args)))(*[a.layer for a in self._args])
+        self.desc = CircuitHostDesc(n_sites, chi_max, k_max, int(use_ppt), len(self._args),
+                                    self._layers, J, hx, b)
+
+
+def batch_run_host(pool: Sequence["Mpdo"], circuits: Sequence[HostCircuit]) -> np.ndarray:
+    """batch_run for circuits held in host memory: each worker uploads its circuit's layers
+    on its own stream.  Returns an (n, 4) array of e_raw, e_succ, p_succ, trace."""
+    handles = (C.c_void_p * len(pool))(*[m._h.value for m in pool])
+    descs = (CircuitHostDesc * max(1, len(circuits)))(*[c.desc for c in circuits])
+    out = np.zeros((len(circuits), 4))
+    status = np.zeros(len(circuits), dtype=np.int32)
+    rc = LIB.mpdo_batch_run_host(len(pool), handles, len(circuits), descs, _dptr(out),
+                                 status.ctypes.data_as(C.POINTER(C.c_int)))
     if rc != 0:
         bad = [(i, int(x)) for i, x in enumerate(status) if x]
         msg = LIB.mpdo_last_error(None)

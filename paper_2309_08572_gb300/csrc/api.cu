@@ -122,6 +122,8 @@ struct mpdo_ctx {
   // staging for host layers
   mpdo_dlayer_s staged;
   size_t staged_cap = 0;
+  unsigned char* hstage = nullptr;   // pinned host staging of staged layers
+  size_t hstage_cap = 0;
   // lazily allocated observable buffers
   void* obs = nullptr;
   size_t obs_bytes = 0;
@@ -761,8 +763,27 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
     }
     total = (total + 255) & ~(size_t)255;
   }
-  // host staging buffer of the converted data
-  std::vector<unsigned char> host(total + 256);
+  // host staging buffer of the converted data: the handle's pinned buffer for staged
+  // layers (reused; the copy below completes before the next layer is prepared)
+  std::vector<unsigned char> tmp;
+  unsigned char* hbuf = nullptr;
+  if (staged) {
+    if (h->hstage_cap < total + 256) {
+      if (h->hstage) cudaFreeHost(h->hstage);
+      h->hstage = nullptr;
+      h->hstage_cap = 0;
+      if (cudaMallocHost((void**)&h->hstage, total + 256) != cudaSuccess) {
+        cudaGetLastError();
+        h->hstage = nullptr;
+        return fail(h, MPDO_ERR_OOM, "pinned layer staging");
+      }
+      h->hstage_cap = total + 256;
+    }
+    hbuf = h->hstage;
+  } else {
+    tmp.resize(total + 256);
+    hbuf = tmp.data();
+  }
   dl->ops.clear();
   size_t off = 0;
   for (int k = 0; k < layer->n_ops; ++k) {
@@ -811,10 +832,10 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
       for (int a = 0; a < parts[p].n; ++a) {
         zc v = parts[p].p[a];
         if (parts[p].dbl) {
-          double* dst = reinterpret_cast<double*>(host.data() + off) + 2 * a;
+          double* dst = reinterpret_cast<double*>(hbuf + off) + 2 * a;
           dst[0] = v.real(); dst[1] = v.imag();
         } else {
-          float* dst = reinterpret_cast<float*>(host.data() + off) + 2 * a;
+          float* dst = reinterpret_cast<float*>(hbuf + off) + 2 * a;
           dst[0] = (float)v.real(); dst[1] = (float)v.imag();
         }
       }
@@ -843,7 +864,7 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
     if (ce != cudaSuccess) { cudaGetLastError(); return fail(h, MPDO_ERR_OOM, "layer upload"); }
     dl->mem = dev;
   }
-  CK(cudaMemcpyAsync(dev, host.data(), total, cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(dev, hbuf, total, cudaMemcpyHostToDevice, h->st));
   CK(cudaStreamSynchronize(h->st));  // host buffer is freed on return
   char* base = static_cast<char*>(dev);
   for (DevOp& d : dl->ops) {
@@ -1278,10 +1299,31 @@ int run_circuit(mpdo_t h, const mpdo_circuit& c, double* out) {
   }
   return mpdo_expect_energy(h, c.J, c.hx, c.b, out, out + 1, out + 2, out + 3);
 }
-}  // namespace
 
-int mpdo_batch_run(int n_handles, mpdo_t* handles, int n_circuits, const mpdo_circuit* circuits,
-                   double* out, int* status) {
+// The host-layer form: each layer is prepared (converted, channel partial traces formed)
+// and copied into the handle's staging buffer on its own stream, so the uploads of one
+// circuit overlap the kernels of the others.
+int run_circuit_host(mpdo_t h, const mpdo_circuit_host& c, double* out) {
+  int rc = mpdo_reconfigure(h, c.n_sites, c.chi_max, c.k_max, c.use_ppt, nullptr);
+  if (rc) return rc;
+  if (c.n_layers > 0 && !c.layers) return fail(h, MPDO_ERR_ARG, "null layer list in circuit");
+  for (int l = 0; l < c.n_layers; ++l) {
+    rc = prepare_layer(h, &c.layers[l], &h->staged, true);
+    if (rc) return rc;
+    rc = run_ops(h, h->staged.ops, nullptr, h->chi, h->kmax, h->use_ppt);
+    if (rc) return rc;
+  }
+  return mpdo_expect_energy(h, c.J, c.hx, c.b, out, out + 1, out + 2, out + 3);
+}
+
+// Shared driver of the batch executors: one host thread per pool handle, circuits taken
+// from a shared queue in index order.
+}  // namespace
+}  // extern "C"
+namespace {
+template <typename Circ, typename Run>
+int batch_drive(int n_handles, mpdo_t* handles, int n_circuits, const Circ* circuits,
+                double* out, int* status, Run run) {
   if (n_handles < 1 || !handles || n_circuits < 0 || (n_circuits > 0 && (!circuits || !out)))
     return fail(nullptr, MPDO_ERR_ARG, "bad batch arguments");
   for (int k = 0; k < n_handles; ++k)
@@ -1303,7 +1345,7 @@ int mpdo_batch_run(int n_handles, mpdo_t* handles, int n_circuits, const mpdo_ci
     for (;;) {
       int i = next.fetch_add(1);
       if (i >= n_circuits) break;
-      st[i] = run_circuit(h, circuits[i], out + 4 * (size_t)i);
+      st[i] = run(h, circuits[i], out + 4 * (size_t)i);
       if (st[i]) msg[i] = h->err;
     }
     h->block_sync = false;
@@ -1324,6 +1366,18 @@ int mpdo_batch_run(int n_handles, mpdo_t* handles, int n_circuits, const mpdo_ci
       if (st[i]) { g_err = "batch: circuit " + std::to_string(i) + ": " + msg[i]; break; }
   }
   return first;
+}
+}  // namespace
+extern "C" {
+
+int mpdo_batch_run(int n_handles, mpdo_t* handles, int n_circuits, const mpdo_circuit* circuits,
+                   double* out, int* status) {
+  return batch_drive(n_handles, handles, n_circuits, circuits, out, status, run_circuit);
+}
+
+int mpdo_batch_run_host(int n_handles, mpdo_t* handles, int n_circuits,
+                        const mpdo_circuit_host* circuits, double* out, int* status) {
+  return batch_drive(n_handles, handles, n_circuits, circuits, out, status, run_circuit_host);
 }
 
 int mpdo_get_dims(mpdo_t h, int* bond_dims, int* kraus_dims, int* centre) {
@@ -1383,6 +1437,7 @@ int mpdo_destroy(mpdo_t h) {
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   if (h->prof_counts) cudaFreeHost(h->prof_counts);
   if (h->staged.mem) cudaFree(h->staged.mem);
+  if (h->hstage) cudaFreeHost(h->hstage);
   if (h->obs) cudaFree(h->obs);
   if (h->hsc) cudaFreeHost(h->hsc);
   if (h->hstats) cudaFreeHost(h->hstats);

@@ -219,6 +219,10 @@ def test_batch_executor_mixed_repeatable(lib):
     out2 = lib.batch_run(pool, descs[::-1])[::-1]
     out3 = lib.batch_run(pool[:1], descs)
     assert np.array_equal(out, out2) and np.array_equal(out, out3)
+    # the host-layer executor uploads the same ops on each worker's stream: same results
+    hosts = [lib.HostCircuit(c.n_sites, c.chi_max, c.k_max, lib.circuit_layers(c), J=c.J,
+                             hx=c.hx, b=c.bz) for c in circs]
+    assert np.array_equal(out, lib.batch_run_host(pool, hosts))
     for c, row in zip(circs[:2], out[:2]):
         _, r = _oracle(c, sv_cutoff=1e-4)
         for j, key in enumerate(("e_raw", "e_succ", "p_succ", "trace")):
