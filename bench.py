@@ -480,6 +480,7 @@ def run_batch512(args):
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     times = []
+    launches0 = lib.kernel_launches()
     for _ in range(args.steps):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -490,8 +491,20 @@ def run_batch512(args):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    launches = lib.kernel_launches() - launches0
     ck = clocks.stop()
     total_ms = sum(times)
+    # end to end: the circuits' ops from host memory through the host-layer executor
+    hosts = [lib.HostCircuit(ci.n_sites, ci.chi_max, ci.k_max, L, J=ci.J, hx=ci.hx, b=ci.bz)
+             for ci, L in zip(circs, host_layers)]
+    te = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lib.batch_run_host(pool, hosts)
+        te.append(time.perf_counter() - t0)
+    h2d = sum(sum((2 * k.shape[0] * 81 * (16 if args.prec == "fp64" else 8) + 2 * 729 * 16)
+                  for _, k in layer) for L in host_layers for layer in L)
     line = {"metric": METRIC, "value": args.steps * updates / (total_ms / 1e3),
             "unit": "site-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -504,6 +517,11 @@ def run_batch512(args):
                        "pool": f"{args.batch} handles (one stream each) sized N=100, chi=128, K=8",
                        "l2": "inputs far larger than L2 across the step"},
             "energy_evals_per_s": args.steps * len(circs) / (total_ms / 1e3),
+            "e2e": {"value": len(te) * updates / sum(te), "unit": "site-updates/s",
+                    "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": len(circs) * 4 * 8 + updates * 2 * STEP_SCALARS_BYTES
+                    + sum(ci.p for ci in circs) * DEV_STATS_BYTES},
+            "gpu_launches": launches,
             "finite": bool(np.all(np.isfinite(out))), "clocks": ck}
     print(json.dumps(line), flush=True)
     for d in dls:
