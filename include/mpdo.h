@@ -218,6 +218,36 @@ int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double beta, double 
                           double bd, double eta, int* sites, int* ms, double* out,
                           size_t cap);
 
+/* Gate model G1: the pulse-level CZ channel (Sec. II, Eqs. LME_Hamiltonian,
+ * LME_Single_Site, LME; Fig. 1 caption; integrated into one channel as in Sec. III.A).
+ * Two atoms under H_p = H_1 (x) I + I (x) H_2 + B|rr><rr|, H_i = Omega(t)/2 (|r><1| + h.c.)
+ * + Delta|r><r|, Omega(t) = omega_max [exp(-(t - T/2)^2/u^2) - a]/(1 - a), u = width*T,
+ * a = exp(-(T/2u)^2); times in us, frequencies angular (rad/us).  The one-atom dissipators
+ * (decay with branching b0, b1 into the qubit levels, the rest to dark states; dephasing,
+ * linear-rate reading) run at gamma/T, i.e. gamma is per pulse.  n_steps equal steps,
+ * each N(tau/2) U_k N(tau/2) with U_k = exp(-i tau H_p(midpoint)) and N the closed-form
+ * noise of both atoms; then each atom gets diag(1, e^{-i phi_1}, 1), phi_1 the |01> phase
+ * of the noiseless pulse.  superop: host complex128 [81][81] on the two-atom row-major
+ * vec((a,b),(a',b')); *phi1, *infidelity (may be NULL): phi_1 and 1 - the average gate
+ * fidelity of the corrected noiseless pulse against CZ on the qubit subspace.  Host only
+ * (no GPU); cost ~n_steps * 4e5 complex multiply-adds.  MPDO_ERR_ARG for n_steps outside
+ * 1..1e6, T or width <= 0 or negative rates; MPDO_ERR_NUMERIC for non-finite input. */
+typedef struct {
+  double T, omega_max, delta, blockade, width;
+} mpdo_pulse;
+int mpdo_build_cz_pulse(const mpdo_pulse* pulse, double gamma_diss, double gamma_deph,
+                        double b0, double b1, int n_steps, double* superop, double* phi1,
+                        double* infidelity);
+
+/* The QAOA layer of mpdo_build_qaoa_layer with every CZ of the ZZ blocks replaced by the
+ * channel cz_superop (host complex128 [81][81], e.g. from mpdo_build_cz_pulse): block =
+ * (I(x)Had) CZ (I(x)Had Rz(J alpha) Had) CZ (I(x)Had) as superoperators, the crosstalk phase
+ * exp(-i xtalk_phase n_r(x)n_r) first; no post-promotion and no separate noise unit (the
+ * pulse carries both).  Outputs as for mpdo_build_qaoa_layer. */
+int mpdo_build_qaoa_layer_cz(int n_sites, int k, double alpha, double beta, double J,
+                             double bz, const double* cz_superop, double xtalk_phase,
+                             double eta, int* sites, int* ms, double* out, size_t cap);
+
 /* Instrumentation.
  * mpdo_kernel_launches: number of CUDA kernels this library has launched in the process.
  * mpdo_profile: time kernel launches of the selected classes on handle h with CUDA events

@@ -10,8 +10,11 @@ citing the passage it follows:
   ops.py          local operators, the G0 gate/noise channels, block composition,
                   Choi <-> Kraus (Sec. II Eqs. LME_Hamiltonian..LME, Sec. IV Eqs.
                   HZ_block_representation / HZ_representation, post-promotion Sec. IV.A)
+  pulse.py        gate model G1: the Gaussian-pulse CZ integrated from the two-atom
+                  Lindbladian (Sec. II Eqs. LME_Hamiltonian, LME_Single_Site, LME; Fig. 1;
+                  Sec. III.A), its phase correction and the G1 ZZ block
   qaoa.py         QAOA layer construction on the TFIM (Sec. IV Eqs. tfim_hamiltonian,
-                  tfim_model)
+                  tfim_model), G0 and G1
   dense.py        exact dense density-matrix simulation (rho in C^{d^N x d^N})
   ppt.py          purity-preserving truncation (Sec. III.D Eqs. xiformula, ppt; App. B)
   mpdo.py         the MPDO two-site update: contract, SVD, truncate, Kraus truncation

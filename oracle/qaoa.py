@@ -40,10 +40,28 @@ def layer_ops(c, k: int) -> List[Tuple[int, list]]:
     return [(i, both if i == 0 else mid) for i in range(n - 2, -1, -1)]
 
 
-def circuit_ops(c) -> List[Tuple[int, list]]:
+def layer_ops_cz(c, k: int, s_cz: np.ndarray) -> List[Tuple[int, list]]:
+    """Layer k in gate model G1: every CZ of the ZZ blocks is the channel s_cz (81 x 81, e.g.
+    the pulse CZ of oracle.pulse); crosstalk as in G0, no post-promotion and no separate
+    noise unit (the pulse carries both)."""
+    from . import pulse
+    n = c.n_sites
+    a, b = c.alpha[k], c.beta[k]
+    v = site_gate(a, b, c.J, c.bz)
+    blk = lambda **kw: pulse.g1_block_channel(c.J * a, s_cz, c.xtalk_phase, **kw)
+    both = blk(post_left=v, post_right=v)
+    if k % 2 == 0:                                   # left -> right
+        mid = blk(post_left=v)
+        return [(i, both if i == n - 2 else mid) for i in range(n - 1)]
+    mid = blk(post_right=v)
+    return [(i, both if i == 0 else mid) for i in range(n - 2, -1, -1)]
+
+
+def circuit_ops(c, s_cz=None) -> List[Tuple[int, list]]:
+    """All ops of the circuit; gate model G0, or G1 with the CZ channel s_cz."""
     out = []
     for k in range(c.p):
-        out.extend(layer_ops(c, k))
+        out.extend(layer_ops(c, k) if s_cz is None else layer_ops_cz(c, k, s_cz))
     return out
 
 

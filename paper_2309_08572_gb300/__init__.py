@@ -50,6 +50,17 @@ class CircuitDesc(C.Structure):
                 ("J", C.c_double), ("hx", C.c_double), ("b", C.c_double)]
 
 
+class Pulse(C.Structure):
+    """Gaussian pulse of the G1 CZ: times in us, angular frequencies in rad/us."""
+    _fields_ = [("T", C.c_double), ("omega_max", C.c_double), ("delta", C.c_double),
+                ("blockade", C.c_double), ("width", C.c_double)]
+
+
+# Fig. 1 (d, e): T = 2.165 us, Omega_max = 17 MHz, Delta = -14.7 MHz, B = 60 MHz (x 2 pi)
+GAUSSIAN_CZ = dict(T=2.165, omega_max=2 * np.pi * 17.0, delta=2 * np.pi * -14.7,
+                   blockade=2 * np.pi * 60.0, width=0.1)
+
+
 class CircuitHostDesc(C.Structure):
     _fields_ = [("n_sites", C.c_int), ("chi_max", C.c_int), ("k_max", C.c_int),
                 ("use_ppt", C.c_int), ("n_layers", C.c_int), ("layers", C.POINTER(Layer)),
@@ -91,6 +102,9 @@ def _load():
         "mpdo_destroy": (I, [VP]),
         "mpdo_last_error": (C.c_char_p, [VP]),
         "mpdo_build_block_channel": (I, [D, D, D, D, D, D, D, D, P(D), P(D), D, P(D), I, P(I)]),
+        "mpdo_build_cz_pulse": (I, [P(Pulse), D, D, D, D, I, P(D), P(D), P(D)]),
+        "mpdo_build_qaoa_layer_cz": (I, [I, I, D, D, D, D, P(D), D, D, P(I), P(I), P(D),
+                                         C.c_size_t]),
         "mpdo_build_qaoa_layer": (I, [I, I, D, D, D, D, D, D, D, D, D, D, D, D, P(I), P(I),
                                       P(D), S]),
         "mpdo_kernel_launches": (C.c_longlong, []),
@@ -177,6 +191,42 @@ def build_qaoa_layer(n_sites: int, k: int, alpha: float, beta: float, J: float =
                                    xtalk_phase, delta_pp, b0, b1, bd, eta,
                                    sites.ctypes.data_as(C.POINTER(C.c_int)),
                                    ms.ctypes.data_as(C.POINTER(C.c_int)), _dptr(out), cap)
+    _check(rc)
+    flat = out.view(complex).reshape(-1)
+    ops, off = [], 0
+    for s, m in zip(sites, ms):
+        ops.append((int(s), flat[off: off + m * 81].reshape(m, 9, 9).copy()))
+        off += m * 81
+    return ops
+
+
+def build_cz_pulse(gamma_diss: float = 0.0, gamma_deph: float = 0.0, b0: float = 1 / 16,
+                   b1: float = 1 / 16, n_steps: int = 2000, pulse: Optional[dict] = None):
+    """Pulse-level CZ channel (gate model G1, host builder): (superoperator (81, 81),
+    phi_1, noiseless average-gate infidelity).  pulse: dict of Pulse fields (default the
+    Gaussian CZ of Fig. 1)."""
+    p = Pulse(**(pulse or GAUSSIAN_CZ))
+    out = np.zeros((81 * 81, 2))
+    phi1, infid = C.c_double(0.0), C.c_double(0.0)
+    _check(LIB.mpdo_build_cz_pulse(C.byref(p), gamma_diss, gamma_deph, b0, b1, n_steps,
+                                   _dptr(out), C.byref(phi1), C.byref(infid)))
+    return out.view(complex).reshape(81, 81).copy(), phi1.value, infid.value
+
+
+def build_qaoa_layer_cz(n_sites: int, k: int, alpha: float, beta: float, cz_superop,
+                        J: float = 1.0, bz: float = 0.0, xtalk_phase: float = 0.0,
+                        eta: float = 1e-15):
+    """Ordered two-site ops of QAOA layer k with every CZ replaced by cz_superop (81 x 81)."""
+    nops = n_sites - 1
+    sites = np.zeros(nops, dtype=np.int32)
+    ms = np.zeros(nops, dtype=np.int32)
+    cap = nops * 81 * 81
+    out = np.zeros((cap, 2))
+    scz = np.ascontiguousarray(np.asarray(cz_superop, dtype=complex).reshape(81, 81)).view(float)
+    rc = LIB.mpdo_build_qaoa_layer_cz(n_sites, k, alpha, beta, J, bz, _dptr(scz.reshape(-1)),
+                                      xtalk_phase, eta,
+                                      sites.ctypes.data_as(C.POINTER(C.c_int)),
+                                      ms.ctypes.data_as(C.POINTER(C.c_int)), _dptr(out), cap)
     _check(rc)
     flat = out.view(complex).reshape(-1)
     ops, off = [], 0

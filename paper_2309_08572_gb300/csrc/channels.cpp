@@ -232,6 +232,130 @@ int block_channel(double angle_zz, double gd, double gp, double phi, double dpp,
   return kraus_from_superop(s, 9, eta, kraus);
 }
 
+// ------------------------------------------------------------------ gate model G1
+// Pulse-level CZ (Sec. II): two atoms under H_p(t) = H_1 (x) I + I (x) H_2 + B |rr><rr|,
+// H_i = Omega(t)/2 (|r><1| + h.c.) + Delta |r><r|, Gaussian Omega of Fig. 1 (offset to start
+// and end at 0), with the one-atom dissipators of Eq. LME at rates gamma / T (gamma per
+// pulse).  The pulse is integrated into one channel (Sec. III.A) by n equal steps, each
+//   N(tau/2) (U_k (x) conj U_k) N(tau/2),  U_k = exp(-i tau H_p(t_k)), t_k the midpoint,
+// with N the closed-form one-atom noise on both atoms (exact for a constant generator)
+// and H_p exponentiated whole (Jacobi eigendecomposition of the 9 x 9 matrix).  Each atom
+// then gets diag(1, e^{-i phi_1}, 1), phi_1 the |01> phase of the noiseless pulse, which
+// turns the pulse into a CZ when phi_11 - 2 phi_1 = pi.
+double gaussian_omega(double t, const mpdo_pulse& p) {
+  const double u = p.width * p.T, t0 = 0.5 * p.T;
+  const double a = std::exp(-(t0 / u) * (t0 / u));
+  const double x = (t - t0) / u;
+  return p.omega_max * (std::exp(-x * x) - a) / (1.0 - a);
+}
+
+Mat pulse_hamiltonian(double om, const mpdo_pulse& p) {
+  Mat h1 = op3({0, 0, 0, 0, 0, 0.5 * om, 0, 0.5 * om, p.delta});
+  Mat h = kron(h1, 3, eye(3), 3);
+  Mat h2 = kron(eye(3), 3, h1, 3);
+  for (int i = 0; i < 81; ++i) h[i] += h2[i];
+  h[8 * 9 + 8] += p.blockade;   // |rr><rr|
+  return h;
+}
+
+// s <- (u (x) conj u) s on two-atom superoperators: every column is a 9 x 9 matrix X over
+// ((a,b),(a',b')) and becomes u X u^+.
+void apply_unitary(Mat& s, const Mat& u) {
+  Mat x(81), y(81);
+  for (int c = 0; c < 81; ++c) {
+    for (int i = 0; i < 81; ++i) x[i] = s[i * 81 + c];
+    for (int i = 0; i < 9; ++i)
+      for (int j = 0; j < 9; ++j) {
+        zc acc = 0.0;
+        for (int k = 0; k < 9; ++k) acc += u[i * 9 + k] * x[k * 9 + j];
+        y[i * 9 + j] = acc;
+      }
+    for (int i = 0; i < 9; ++i)
+      for (int j = 0; j < 9; ++j) {
+        zc acc = 0.0;
+        for (int k = 0; k < 9; ++k) acc += y[i * 9 + k] * std::conj(u[j * 9 + k]);
+        s[(i * 9 + j) * 81 + c] = acc;
+      }
+  }
+}
+
+// s <- (n1 on atom `site`) s, n1 a one-atom superoperator (9 x 9 on (a,a')), applied through
+// its nonzero entries.
+void apply_one_atom(Mat& s, const Mat& n1, int site) {
+  struct Nz { int r, c; zc v; };
+  std::vector<Nz> nz;
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c)
+      if (n1[r * 9 + c] != 0.0) nz.push_back({r, c, n1[r * 9 + c]});
+  Mat out(81 * 81, 0.0);
+  for (const Nz& e : nz) {
+    const int a = e.r / 3, ap = e.r % 3, c = e.c / 3, cp = e.c % 3;
+    for (int o = 0; o < 3; ++o)
+      for (int op = 0; op < 3; ++op) {
+        // the other atom's indices o (ket) and op (bra) are untouched
+        const int rin = site == 0 ? (c * 3 + o) * 9 + (cp * 3 + op) : (o * 3 + c) * 9 + (op * 3 + cp);
+        const int rout = site == 0 ? (a * 3 + o) * 9 + (ap * 3 + op) : (o * 3 + a) * 9 + (op * 3 + ap);
+        for (int col = 0; col < 81; ++col) out[rout * 81 + col] += e.v * s[rin * 81 + col];
+      }
+  }
+  s.swap(out);
+}
+
+int cz_pulse(const mpdo_pulse& p, double gd, double gp, double b0, double b1, int n_steps,
+             Mat& s, double& phi1, double& infid) {
+  const double tau = p.T / n_steps;
+  // noiseless pulse and its phase correction
+  Mat u = eye(9);
+  std::vector<Mat> steps(n_steps);
+  for (int k = 0; k < n_steps; ++k) {
+    steps[k] = expmh(tau, pulse_hamiltonian(gaussian_omega((k + 0.5) * tau, p), p), 9);
+    u = matmul(steps[k], u, 9);
+  }
+  phi1 = std::arg(u[1 * 9 + 1]) - std::arg(u[0]);
+  Mat c1 = op3({1, 0, 0, 0, std::exp(zc(0, -phi1)), 0, 0, 0, 1});
+  Mat cc = kron(c1, 3, c1, 3);
+  Mat uc = matmul(cc, u, 9);
+  const int q[4] = {0, 1, 3, 4};
+  zc tr = 0.0;
+  for (int i = 0; i < 4; ++i) tr += (i == 3 ? -1.0 : 1.0) * uc[q[i] * 9 + q[i]];
+  infid = 1.0 - (std::norm(tr) + 4.0) / 20.0;
+  // the noisy channel
+  const Mat nh = noise_superop(gd * 0.5 * tau / p.T, gp * 0.5 * tau / p.T, b0, b1);
+  s = eye(81);
+  for (int k = 0; k < n_steps; ++k) {
+    apply_one_atom(s, nh, 0);
+    apply_one_atom(s, nh, 1);
+    apply_unitary(s, steps[k]);
+    apply_one_atom(s, nh, 0);
+    apply_one_atom(s, nh, 1);
+  }
+  apply_unitary(s, cc);
+  for (zc v : s)
+    if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return MPDO_ERR_NUMERIC;
+  return MPDO_OK;
+}
+
+// The ZZ block with each CZ replaced by the channel s_cz (81 x 81): superoperator products
+// of (I (x) Had) s_cz (I (x) Had Rz Had) s_cz (I (x) Had), crosstalk phase first, optional
+// one-site unitaries after; Kraus set from the Choi matrix.
+int block_channel_cz(double angle_zz, const Mat& s_cz, double phi, const Mat* post_l,
+                     const Mat* post_r, double eta, std::vector<Mat>& kraus) {
+  Mat had2 = kron(eye(3), 3, hadq(), 3);
+  Mat rz = kron(eye(3), 3, expmh(angle_zz, zq(), 3), 3);
+  Mat mid = matmul(matmul(had2, rz, 9), had2, 9);
+  Mat s = unitary_superop(had2, 9);
+  s = matmul(s_cz, s, 81);
+  s = matmul(unitary_superop(mid, 9), s, 81);
+  s = matmul(s_cz, s, 81);
+  s = matmul(unitary_superop(had2, 9), s, 81);
+  if (phi != 0.0) s = matmul(s, unitary_superop(expmh(phi, kron(nr(), 3, nr(), 3), 9), 9), 81);
+  if (post_l || post_r) {
+    Mat v = kron(post_l ? *post_l : eye(3), 3, post_r ? *post_r : eye(3), 3);
+    s = matmul(unitary_superop(v, 9), s, 81);
+  }
+  return kraus_from_superop(s, 9, eta, kraus);
+}
+
 bool finite_all(std::initializer_list<double> xs) {
   for (double x : xs)
     if (!std::isfinite(x)) return false;
@@ -288,6 +412,67 @@ extern "C" int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double be
   const bool ltr = (k % 2 == 0);
   rc = block_channel(J * alpha, gamma_diss, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd,
                      ltr ? &v : nullptr, ltr ? nullptr : &v, eta, mid);
+  if (rc) return rc;
+  size_t off = 0;
+  for (int q = 0; q < n_sites - 1; ++q) {
+    int i = ltr ? q : n_sites - 2 - q;
+    bool last = ltr ? (i == n_sites - 2) : (i == 0);
+    const std::vector<Mat>& ch = last ? both : mid;
+    sites[q] = i;
+    ms[q] = (int)ch.size();
+    if (off + ch.size() * 81 > cap) return MPDO_ERR_ARG;
+    for (const Mat& e : ch)
+      for (int a = 0; a < 81; ++a) {
+        out[2 * off] = e[a].real();
+        out[2 * off + 1] = e[a].imag();
+        ++off;
+      }
+  }
+  return MPDO_OK;
+}
+
+extern "C" int mpdo_build_cz_pulse(const mpdo_pulse* pulse, double gamma_diss,
+                                   double gamma_deph, double b0, double b1, int n_steps,
+                                   double* superop, double* phi1, double* infidelity) {
+  if (!pulse || !superop || n_steps < 1 || n_steps > 1000000) return MPDO_ERR_ARG;
+  if (!finite_all({pulse->T, pulse->omega_max, pulse->delta, pulse->blockade, pulse->width,
+                   gamma_diss, gamma_deph, b0, b1}))
+    return MPDO_ERR_NUMERIC;
+  if (!(pulse->T > 0) || !(pulse->width > 0) || gamma_diss < 0 || gamma_deph < 0 || b0 < 0 ||
+      b1 < 0)
+    return MPDO_ERR_ARG;
+  Mat s;
+  double ph = 0, inf = 0;
+  int rc = cz_pulse(*pulse, gamma_diss, gamma_deph, b0, b1, n_steps, s, ph, inf);
+  if (rc) return rc;
+  for (int i = 0; i < 81 * 81; ++i) {
+    superop[2 * i] = s[i].real();
+    superop[2 * i + 1] = s[i].imag();
+  }
+  if (phi1) *phi1 = ph;
+  if (infidelity) *infidelity = inf;
+  return MPDO_OK;
+}
+
+extern "C" int mpdo_build_qaoa_layer_cz(int n_sites, int k, double alpha, double beta, double J,
+                                        double bz, const double* cz_superop, double xtalk_phase,
+                                        double eta, int* sites, int* ms, double* out,
+                                        size_t cap) {
+  if (n_sites < 2 || k < 0 || !cz_superop || !sites || !ms || !out) return MPDO_ERR_ARG;
+  if (!finite_all({alpha, beta, J, bz, xtalk_phase, eta})) return MPDO_ERR_NUMERIC;
+  Mat scz(81 * 81);
+  for (int i = 0; i < 81 * 81; ++i) {
+    scz[i] = zc(cz_superop[2 * i], cz_superop[2 * i + 1]);
+    if (!std::isfinite(scz[i].real()) || !std::isfinite(scz[i].imag())) return MPDO_ERR_NUMERIC;
+  }
+  // one-site gate exp(-i beta S^x) exp(-i b J alpha S^z), folded after the last block
+  Mat v = matmul(expmh(beta, xq(), 3), expmh(bz * J * alpha, zq(), 3), 3);
+  std::vector<Mat> both, mid;
+  int rc = block_channel_cz(J * alpha, scz, xtalk_phase, &v, &v, eta, both);
+  if (rc) return rc;
+  const bool ltr = (k % 2 == 0);
+  rc = block_channel_cz(J * alpha, scz, xtalk_phase, ltr ? &v : nullptr, ltr ? nullptr : &v,
+                        eta, mid);
   if (rc) return rc;
   size_t off = 0;
   for (int q = 0; q < n_sites - 1; ++q) {

@@ -83,3 +83,44 @@ def test_create_argument_checks_without_gpu(pkg):
 
     assert create(64, 25) == -1
     assert create(g.SMOKE_K_MAX, g.SMOKE_M_MAX) != -1
+
+
+@pytest.mark.parametrize("args", [
+    dict(gamma_diss=0.0, gamma_deph=0.0, b0=1 / 16, b1=1 / 16, n_steps=200),
+    dict(gamma_diss=0.05, gamma_deph=0.02, b0=1 / 16, b1=1 / 16, n_steps=300),
+    dict(gamma_diss=0.3, gamma_deph=0.1, b0=0.4, b1=0.6, n_steps=150),
+])
+def test_cz_pulse_matches_oracle(pkg, args):
+    """Gate model G1: the library's pulse CZ (closed-form dissipators, structured products)
+    against the oracle's (matrix exponentials of the dissipator generator, dense products)."""
+    from oracle import pulse as opulse
+    s_lib, phi_lib, inf_lib = pkg.build_cz_pulse(**args)
+    bd = 1.0 - args["b0"] - args["b1"]
+    s_or, phi_or = opulse.cz_superop(args["gamma_diss"], args["gamma_deph"], args["b0"],
+                                     args["b1"], bd, args["n_steps"])
+    assert np.abs(s_lib - s_or).max() < 1e-11
+    assert abs(phi_lib - phi_or) < 1e-12
+    u = opulse.pulse_unitary(args["n_steps"])
+    assert abs(inf_lib - opulse.average_cz_infidelity(u)) < 1e-12
+
+
+def test_qaoa_layer_cz_ops_match_oracle(pkg):
+    from oracle import pulse as opulse
+    s_cz, _ = opulse.cz_superop(0.02, 0.01, 1 / 16, 1 / 16, 7 / 8, 200)
+    c = synth.scaled(synth.chain40(), n_sites=6)
+    for k in range(c.p):
+        lib = pkg.build_qaoa_layer_cz(c.n_sites, k, c.alpha[k], c.beta[k], s_cz, c.J, c.bz,
+                                      c.xtalk_phase)
+        orc = oqaoa.layer_ops_cz(c, k, s_cz)
+        assert [s for s, _ in lib] == [s for s, _ in orc]
+        for (_, a), (_, b) in zip(lib, orc):
+            assert np.abs(oops.superop(a) - oops.superop(b)).max() < 1e-12
+
+
+def test_cz_pulse_rejects_bad_arguments(pkg):
+    with pytest.raises(pkg.MpdoError):
+        pkg.build_cz_pulse(n_steps=0)
+    with pytest.raises(pkg.MpdoError):
+        pkg.build_cz_pulse(gamma_diss=-1.0, n_steps=10)
+    with pytest.raises(pkg.MpdoError):
+        pkg.build_cz_pulse(n_steps=10, pulse=dict(pkg.GAUSSIAN_CZ, T=float("nan")))

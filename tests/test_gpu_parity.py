@@ -256,3 +256,27 @@ def test_batch512_sample_through_executor(lib):
             assert _rel(out[i][j], r[key]) < TOL["c64"], (i, key, out[i][j], r[key])
     for m in pool:
         m.close()
+
+
+def test_g1_pulse_circuit_matches_oracle(lib):
+    """Gate model G1: blocks built from the pulse-level CZ (63 Kraus operators each) by the
+    library's host builder, run through the CUDA path in FP64, against the oracle MPDO on the
+    oracle's own G1 ops (its pulse integration and block composition); the inner index is
+    cut at K = 16 with PPT on both sides (swapping the two op sets moves the oracle's
+    energies by 4e-13, so the cut is well conditioned)."""
+    from oracle import pulse as opulse
+    c = synth.scaled(synth.chain40(), n_sites=7, chi_max=64, k_max=16)
+    s_lib, _, _ = lib.build_cz_pulse(c.gamma_diss, c.gamma_deph, c.b0, c.b1, n_steps=300)
+    s_or, _ = opulse.cz_superop(c.gamma_diss, c.gamma_deph, c.b0, c.b1, c.bd, 300)
+    g = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=63, prec="fp64")
+    for k in range(c.p):
+        g.apply_layer(lib.build_qaoa_layer_cz(c.n_sites, k, c.alpha[k], c.beta[k], s_lib, c.J,
+                                              c.bz, c.xtalk_phase))
+    e = g.expect_energy(c.J, c.hx, c.bz)
+    g.close()
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max)
+    for i, kr in oqaoa.circuit_ops(c, s_or):
+        m.apply_two_site(i, kr)
+    r = oobs.expect_energy(m, c.J, c.hx, c.bz)
+    for key in r:
+        assert _rel(e[key], r[key]) < 1e-9, (key, e[key], r[key])

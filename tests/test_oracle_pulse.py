@@ -1,0 +1,97 @@
+"""Pins of the pulse-level CZ oracle (gate model G1, oracle/pulse.py) to what the paper
+and the mathematics fix: the closed form without drive, channel properties, the CZ phase
+condition of the Gaussian pulse at B = 2 pi x 60 MHz (Sec. II, Fig. 1 d), the coherent
+dissipation factors of App. E, and the convergence of the split integration."""
+import numpy as np
+import pytest
+
+from oracle import ops, pulse
+
+B0, B1, BD = 1 / 16, 1 / 16, 7 / 8
+
+
+def _diag_phase_unitary(p):
+    """exp(-i T (Delta n_r (x) I + I (x) Delta n_r + B n_r (x) n_r)) (the undriven pulse)."""
+    h = (p["delta"] * (np.kron(ops.N_R, ops.I3) + np.kron(ops.I3, ops.N_R))
+         + p["blockade"] * np.kron(ops.N_R, ops.N_R))
+    return np.diag(np.exp(-1j * p["T"] * np.diag(h)))
+
+
+def test_undriven_pulse_is_closed_form_noise_times_phases():
+    """Omega = 0 and B = 0: the detuning phases do not change under a jump (each jump moves
+    both sides of a coherence by the same energy), so decay/dephasing commute with the
+    Hamiltonian and the channel is the closed-form one-atom noise of the total rates (G0
+    form) on both atoms times the phase unitary, for any step count (pins the dissipator
+    embedding and the rate units)."""
+    p = dict(pulse.GAUSSIAN, omega_max=0.0, blockade=0.0)
+    g, gp = 0.3, 0.2
+    s = pulse.pulse_superop(g, gp, B0, B1, BD, 7, p)
+    n1 = ops.g0_noise_superop(g, gp, B0, B1, BD)
+    n2 = np.kron(n1, n1).reshape(3, 3, 3, 3, 3, 3, 3, 3).transpose(0, 2, 1, 3, 4, 6, 5, 7)
+    want = n2.reshape(81, 81) @ ops.superop([_diag_phase_unitary(p)])
+    assert np.abs(s - want).max() < 1e-13
+
+
+def test_noiseless_gaussian_pulse_is_a_cz():
+    """Sec. II: the Gaussian pulse returns the Rydberg population and, at B = 2 pi x 60 MHz,
+    leaves phi_11 - 2 phi_1 = pi (a CZ after one-qubit phase corrections).  The paper prints
+    a combined infidelity of 6e-8; this reading reaches 8.9e-7 average-gate infidelity at
+    exactly 60 MHz (phase error 2.4e-3 rad; the paper's metric and tuning differ)."""
+    u = pulse.pulse_unitary(4000)
+    assert np.abs(u.conj().T @ u - np.eye(9)).max() < 1e-12
+    q = [0, 1, 3, 4]
+    assert np.abs(np.abs(np.diag(u)[q]) - 1.0).max() < 1e-9        # no population left in |r>
+    assert abs(u[0, 0] - 1.0) < 1e-14                               # |00> is not driven
+    ph = np.angle(np.diag(u))
+    cz_phase = (ph[4] - 2 * ph[1]) % (2 * np.pi)
+    assert abs(cz_phase - np.pi) < 5e-3, cz_phase
+    assert pulse.average_cz_infidelity(u) < 3e-6
+
+
+def test_pulse_channel_is_cptp_or_trace_decreasing():
+    for bd in (0.0, BD):
+        s, _ = pulse.cz_superop(0.2, 0.1, 0.5 * (1 - bd), 0.5 * (1 - bd), bd, 300)
+        choi = s.reshape(9, 9, 9, 9).transpose(0, 2, 1, 3).reshape(81, 81)
+        assert np.linalg.eigvalsh(0.5 * (choi + choi.conj().T)).min() > -1e-12
+        tr = np.einsum("aacd->cd", s.reshape(9, 9, 9, 9))              # trace map
+        if bd == 0.0:
+            assert np.abs(tr - np.eye(9)).max() < 1e-12
+        else:
+            w = np.linalg.eigvalsh(0.5 * (tr + tr.conj().T))
+            assert w.max() <= 1.0 + 1e-12 and w.min() < 1.0 - 1e-4
+
+
+def test_app_e_coherent_dissipation_factors():
+    """App. E: under dissipation gamma the CZ scales <00|rho|01> by alpha = e^{-0.012291 gamma}
+    and <11|rho|11> by |beta|^2, beta = e^{-0.0185454 gamma}.  This reading gives 0.01298
+    (within 6%) and 0.01887 (within 2%): the pulse shape and units are the paper's up to the
+    details App. E does not print."""
+    g = 0.01
+    s, _ = pulse.cz_superop(g, 0.0, B0, B1, BD, 2000)
+    i01 = 0 * 9 + 1                       # vec index of |00><01|
+    i11 = 4 * 9 + 4                       # vec index of |11><11|
+    a_rate = -np.log(abs(s[i01, i01])) / g
+    b_rate = -np.log(abs(s[i11, i11])) / (2 * g)
+    assert abs(a_rate / 0.012291 - 1) < 0.08, a_rate
+    assert abs(b_rate / 0.0185454 - 1) < 0.04, b_rate
+
+
+def test_split_integration_converges_to_the_generator_exponential():
+    """The symmetric split and the midpoint exponential of the whole generator approach each
+    other as the steps shrink, and the split converges in the step count."""
+    args = (0.05, 0.02, 0.2, 0.3, 0.5)
+    d40 = np.abs(pulse.pulse_superop(*args, 40) - pulse.pulse_superop_exact(*args, 40)).max()
+    d80 = np.abs(pulse.pulse_superop(*args, 80) - pulse.pulse_superop_exact(*args, 80)).max()
+    assert d80 < 0.6 * d40 and d80 < 2e-3
+    s1 = pulse.pulse_superop(*args, 1000)
+    s2 = pulse.pulse_superop(*args, 2000)
+    assert np.abs(s1 - s2).max() < 1e-4
+
+
+def test_g1_block_reduces_to_the_g0_block_for_an_ideal_cz():
+    """With the ideal CZ channel in place of the pulse, the G1 block is the noiseless G0 ZZ
+    block (Eq. HZ_block_representation)."""
+    s_cz = ops.superop([ops.CZ])
+    k1 = pulse.g1_block_channel(0.7, s_cz, xtalk_phase=0.2)
+    k0 = ops.g0_block_channel(0.7, 0.0, 0.0, 0.2, 0.0, B0, B1, BD)
+    assert np.abs(ops.superop(k1) - ops.superop(k0)).max() < 1e-13
