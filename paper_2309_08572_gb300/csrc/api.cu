@@ -1177,8 +1177,11 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
     return fail(nullptr, MPDO_ERR_OOM, "pinned host allocation");
   }
   if (h->mixed) {
-    if ((rc = alloc_dev(hp, &h->mixmem, mix_work_bytes(ncap)))) return rc;
-    mix_work_bind(h->mixw, h->mixmem, ncap);
+    // the mixed solver only ever sees n <= kMixedEigMax (peig routes larger problems to
+    // the FP64 solvers), so its workspace is sized for that
+    const int mcap = std::min(ncap, kMixedEigMax);
+    if ((rc = alloc_dev(hp, &h->mixmem, mix_work_bytes(mcap)))) return rc;
+    mix_work_bind(h->mixw, h->mixmem, mcap);
     // MPDO_NO_GRAPHS=1: launch the mixed eigensolver's levels directly (no CUDA graphs)
     const char* ng = std::getenv("MPDO_NO_GRAPHS");
     if (ng && ng[0] == '1') h->mixw.use_graphs = false;
