@@ -289,6 +289,8 @@ def run_ours(args):
                   hx=ci.hx, b=ci.bz) for ci, d in zip(circs, dls)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     updates = c.p * (c.n_sites - 1)
+    # GEMM tile shapes picked by the library's autotuner (untimed)
+    tuned = [lib.autotune_gemm(pr, reps=3) for pr in (0, 1)] if args.autotune else None
 
     def step():
         return lib.batch_run(pool, descs)
@@ -422,6 +424,8 @@ def run_ours(args):
 
     if rank == 0:
         cfg = workload_desc(c, prec, sv)
+        cfg["gemm_tiles"] = (f"autotuned ({tuned[0]} FP64 and {tuned[1]} FP32 buckets)"
+                             if tuned else "built-in size rules")
         cfg["batch"] = f"{args.batch} circuits per step, run concurrently (one stream each); " \
                        f"circuit 0 uses seed {c.seed}, circuit j seeded angles {c.seed}*1000+j"
         line = {"metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
@@ -474,6 +478,7 @@ def run_batch512(args):
     descs = [dict(n_sites=ci.n_sites, chi_max=ci.chi_max, k_max=ci.k_max, layers=d, J=ci.J,
                   hx=ci.hx, b=ci.bz) for ci, d in zip(circs, dls)]
     updates = sum(ci.p * (ci.n_sites - 1) for ci in circs)
+    tuned = [lib.autotune_gemm(pr, reps=3) for pr in (0, 1)] if args.autotune else None
     for _ in range(args.warmup):
         lib.batch_run(pool, descs)
     torch.cuda.synchronize()
@@ -515,6 +520,8 @@ def run_batch512(args):
                        "updates_per_step": updates, "precision": PREC_DESC[args.prec],
                        "bond_cut": f"s > {sv:g} s_max" if sv else "numerical floor",
                        "pool": f"{args.batch} handles (one stream each) sized N=100, chi=128, K=8",
+                       "gemm_tiles": (f"autotuned ({tuned[0]} FP64 and {tuned[1]} FP32 buckets)"
+                                      if tuned else "built-in size rules"),
                        "l2": "inputs far larger than L2 across the step"},
             "energy_evals_per_s": args.steps * len(circs) / (total_ms / 1e3),
             "e2e": {"value": len(te) * updates / sum(te), "unit": "site-updates/s",
@@ -546,6 +553,9 @@ def main():
                     help="skip the plain FP64 single-circuit comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick GEMM tile shapes with the library's autotuner before timing "
+                         "(default: the built-in size rules, faster under concurrency)")
     ap.add_argument("--batch", type=int, default=32,
                     help="circuits per step, run concurrently by the batch executor")
     ap.add_argument("--workload", choices=["chain100", "chain40", "batch512"], default="chain100",

@@ -262,6 +262,21 @@ int mpdo_profile(mpdo_t h, int class_mask);
 int mpdo_profile_read(mpdo_t h, int cls, double* ms, long long* launches, double* flops);
 
 /* Kernel-level entry points used by the unit tests (device pointers). */
+/* Tile-shape autotuner of the complex GEMMs (all handles of the process).  For precision
+ * prec (0: FP64 products, including FP32 x FP32 -> FP64; 1: FP32) and each bucket of
+ * (number of 16 x 16 output tiles: 1 .. 1024 in powers of 2) x (K: 16 .. 4096 in powers of
+ * 2), times on `stream` (cudaStream_t; reps runs after one warm-up, minimum taken, CUDA
+ * events) the 64 x 64 tile kernel, the 16 x 16 tile kernel and the 16 x 16 kernel with K
+ * split over a thread-block cluster of 2, 4 or 8, on a representative shape of the
+ * bucket, and makes the fastest the choice for every product of that bucket.  Untuned
+ * buckets, and all of them after a call with reps <= 0, follow the built-in size rules.
+ * The choice changes the summation order of products, not their precision: call it
+ * before running circuits, not while another thread runs them.  Allocates ~70 MB of
+ * device scratch for the call; synchronises the stream.  *n_tuned (may be NULL) receives
+ * the number of buckets set.  MPDO_ERR_ARG for prec outside {0, 1}; MPDO_ERR_OOM;
+ * MPDO_ERR_CUDA (the table is then reset to the size rules). */
+int mpdo_autotune_gemm(int prec, void* stream, int reps, int* n_tuned);
+
 /* C[b] = op(A[b]) op(B[b]) for complex matrices; prec 0 = complex128, 1 = complex64.
  * opa/opb: 0 = N, 1 = T, 2 = C (conjugate transpose).  A is m x k after op, etc.;
  * leading dimensions in complex elements (row-major), batch strides in elements. */

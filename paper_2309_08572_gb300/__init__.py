@@ -119,6 +119,7 @@ def _load():
         "mpdo_mlp_adam_step": (I, [VP, C.c_float]),
         "mpdo_mlp_input_grad": (I, [VP, I, VP, P(C.c_float), VP]),
         "mpdo_mlp_destroy": (I, [VP]),
+        "mpdo_autotune_gemm": (I, [I, VP, I, P(I)]),
         "mpdo_kernel_cgemm": (I, [I, I, I, I, I, I, VP, C.c_long, C.c_long, VP, C.c_long,
                                   C.c_long, VP, C.c_long, C.c_long, I, VP]),
         "mpdo_kernel_heig": (I, [I, I, VP, VP, P(D), P(I), VP]),
@@ -521,6 +522,15 @@ def kernel_launches() -> int:
 
 
 # ------------------------------------------------------ kernel-level entry points (tests)
+def autotune_gemm(prec: int, reps: int = 3, stream=None) -> int:
+    """Tile-shape autotuner of the complex GEMMs (prec 0: FP64 products, 1: FP32); reps <= 0
+    resets to the built-in size rules.  Returns the number of buckets tuned."""
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    n = C.c_int(0)
+    _check(LIB.mpdo_autotune_gemm(prec, st, reps, C.byref(n)))
+    return n.value
+
+
 def kernel_cgemm(prec: int, opa: int, opb: int, m: int, n: int, k: int, a, lda: int, sa: int,
                  b, ldb: int, sb: int, c, ldc: int, sc: int, batch: int, stream=None):
     """c = op(a) op(b) on device tensors (complex128 if prec == 0 else complex64)."""

@@ -4,6 +4,11 @@
 // C64 modes and for the unit tests of the other GEMM paths.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <atomic>
+#include <vector>
+
+#include "../../include/mpdo.h"
 #include "common.cuh"
 #include "internal.h"
 
@@ -218,6 +223,21 @@ inline int split_count(long tiles, int K) {
   while (s < 8 && tiles * (2 * s) <= 152 && K >= 16 * (2 * s)) s *= 2;
   return s;
 }
+
+// Tile-shape table of the autotuner (mpdo_autotune_gemm): per precision (0: FP64 products,
+// 1: FP32), per bucket of the 16 x 16 output-tile count (log2, 0..10) and of K (log2(K/16),
+// 0..8), the kernel choice: 0 = size rules above (untuned), 1 = 64 x 64 tiles, 2 = 16 x 16
+// tiles, 3/4/5 = 16 x 16 tiles with K split over a cluster of 2/4/8.
+constexpr int kTileBuckets = 11, kKBuckets = 9, kChoices = 5;
+std::atomic<signed char> g_choice[2][kTileBuckets][kKBuckets];
+
+inline int log2_ceil(long x) {
+  int b = 0;
+  while ((1L << b) < x) ++b;
+  return b;
+}
+inline int tile_bucket(long tiles16) { return std::min(kTileBuckets - 1, log2_ceil(std::max(1L, tiles16))); }
+inline int k_bucket(int K) { return std::min(kKBuckets - 1, std::max(0, log2_ceil(std::max(1, K)) - 4)); }
 }  // namespace
 
 template <typename RA, typename RB, typename R>
@@ -234,13 +254,17 @@ cudaError_t cgemm_impl(cudaStream_t st, int opa, int opb, int m, int n, int k, c
     k = 0;
   }
   const long big_tiles = (long)((n + BN - 1) / BN) * ((m + BM - 1) / BM) * batch;
-  const bool small = big_tiles < 152;
+  const long tiles16 = (long)((n + ST - 1) / ST) * ((m + ST - 1) / ST) * batch;
+  const int choice =
+      g_choice[sizeof(R) == 8 ? 0 : 1][tile_bucket(tiles16)][k_bucket(k)].load(std::memory_order_relaxed);
+  const bool small = choice == 0 ? big_tiles < 152 : choice >= 2;
   for (int b0 = 0; b0 < batch; b0 += 65535) {
     int nb = batch - b0 < 65535 ? batch - b0 : 65535;
     count_launch();
-    if (small && sizeof(R) == 8) {
+    if (small && (sizeof(R) == 8 || choice >= 3)) {
       const long tiles = (long)((n + ST - 1) / ST) * ((m + ST - 1) / ST) * nb;
-      const int splits = split_count(tiles, k);
+      int splits = choice == 0 ? split_count(tiles, k) : (choice >= 3 ? 1 << (choice - 2) : 1);
+      while (splits > 1 && k < 16 * splits) splits >>= 1;   // every slice at least one step
       if (splits > 1) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(((n + ST - 1) / ST) * splits, (m + ST - 1) / ST, nb);
@@ -315,3 +339,95 @@ template cudaError_t cgemm<float>(cudaStream_t, int, int, int, int, int, const f
                                   float2, float2);
 
 }  // namespace mpdo
+
+// ------------------------------------------------------------------ autotuner
+namespace mpdo {
+void set_global_error(const char* msg);
+}
+
+extern "C" int mpdo_autotune_gemm(int prec, void* stream, int reps, int* n_tuned) {
+  using namespace mpdo;
+  if (prec != 0 && prec != 1) {
+    set_global_error("mpdo_autotune_gemm: prec must be 0 (FP64) or 1 (FP32)");
+    return MPDO_ERR_ARG;
+  }
+  if (n_tuned) *n_tuned = 0;
+  auto& table = g_choice[prec];
+  if (reps <= 0) {   // back to the size rules
+    for (auto& row : table)
+      for (auto& c : row) c.store(0, std::memory_order_relaxed);
+    return MPDO_OK;
+  }
+  reps = std::min(reps, 50);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t elt = prec == 0 ? sizeof(double2) : sizeof(float2);
+  // largest representative shape: 2^10 tiles of 16 x 16 (512 x 512), K = 4096
+  const long mmax = 512, kmax = 16L << (kKBuckets - 1);
+  void *a = nullptr, *b = nullptr, *c = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&]() {
+    if (a) cudaFree(a);
+    if (b) cudaFree(b);
+    if (c) cudaFree(c);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&a, mmax * kmax * elt) != cudaSuccess || cudaMalloc(&b, kmax * mmax * elt) != cudaSuccess ||
+      cudaMalloc(&c, mmax * mmax * elt) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    set_global_error("mpdo_autotune_gemm: allocation failed");
+    return MPDO_ERR_OOM;
+  }
+  cudaError_t err = cudaMemsetAsync(a, 0, mmax * kmax * elt, st);
+  if (err == cudaSuccess) err = cudaMemsetAsync(b, 0, kmax * mmax * elt, st);
+  int tuned = 0;
+  for (int tb = 0; tb < kTileBuckets && err == cudaSuccess; ++tb)
+    for (int kb = 0; kb < kKBuckets && err == cudaSuccess; ++kb) {
+      // representative shape of the bucket: 2^tb tiles, K = 16 * 2^kb
+      const int m = 16 << ((tb + 1) / 2), n = 16 << (tb / 2), k = 16 << kb;
+      float best = 1e30f;
+      int best_c = 0;
+      for (int ch = 1; ch <= kChoices && err == cudaSuccess; ++ch) {
+        if (ch >= 3 && k < 16 * (1 << (ch - 2))) continue;   // slices shorter than one step
+        table[tb][kb].store((signed char)ch, std::memory_order_relaxed);
+        auto run = [&]() {
+          return prec == 0
+                     ? cgemm<double>(st, OP_N, OP_N, m, n, k, (const double2*)a, k, 0,
+                                     (const double2*)b, n, 0, (double2*)c, n, 0, 1,
+                                     make_double2(1, 0), make_double2(0, 0))
+                     : cgemm<float>(st, OP_N, OP_N, m, n, k, (const float2*)a, k, 0,
+                                    (const float2*)b, n, 0, (float2*)c, n, 0, 1,
+                                    make_float2(1, 0), make_float2(0, 0));
+        };
+        err = run();   // warm-up
+        float t_min = 1e30f;
+        for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+          err = cudaEventRecord(e0, st);
+          if (err == cudaSuccess) err = run();
+          if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+          if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+          t_min = std::min(t_min, ms);
+        }
+        if (err == cudaSuccess && t_min < best) {
+          best = t_min;
+          best_c = ch;
+        }
+      }
+      table[tb][kb].store((signed char)best_c, std::memory_order_relaxed);
+      if (best_c) ++tuned;
+    }
+  release();
+  if (err != cudaSuccess) {
+    for (auto& row : table)
+      for (auto& cc : row) cc.store(0, std::memory_order_relaxed);
+    cudaGetLastError();
+    set_global_error(cudaGetErrorString(err));
+    return MPDO_ERR_CUDA;
+  }
+  if (n_tuned) *n_tuned = tuned;
+  return MPDO_OK;
+}

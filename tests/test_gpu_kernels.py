@@ -72,6 +72,33 @@ def test_cgemm_fp64_split_k(lib, m, n, k, batch):
     assert np.array_equal(outs[0], outs[1])
 
 
+def test_autotuned_gemm_tiles_stay_correct(lib):
+    """The tile-shape autotuner picks, per (output-tile count, K) bucket, the fastest of the
+    64x64, 16x16 and cluster split-K kernels; products afterwards still match numpy, and
+    reps <= 0 returns to the size rules."""
+    try:
+        for prec in (0, 1):
+            assert lib.autotune_gemm(prec, reps=2) == 11 * 9
+        for m, n, k, batch in [(16, 16, 257, 1), (67, 45, 130, 3), (200, 150, 40, 1),
+                               (5, 7, 33, 2), (300, 260, 500, 1)]:
+            rng = np.random.default_rng(m + n + k)
+            a = _rand(rng, (batch, m, k))
+            b = _rand(rng, (batch, k, n))
+            want = np.einsum("bik,bkj->bij", a, b)
+            for prec, ct, tol in ((0, torch.complex128, 1e-14), (1, torch.complex64, 2e-6)):
+                ta = torch.tensor(a, dtype=ct, device="cuda")
+                tb = torch.tensor(b, dtype=ct, device="cuda")
+                tc = torch.zeros((batch, m, n), dtype=ct, device="cuda")
+                lib.kernel_cgemm(prec, 0, 0, m, n, k, ta, k, m * k, tb, n, k * n, tc, n, m * n,
+                                 batch)
+                torch.cuda.synchronize()
+                err = np.abs(tc.cpu().numpy() - want).max() / np.abs(want).max()
+                assert err < tol, (prec, m, n, k, err)
+    finally:
+        for prec in (0, 1):
+            assert lib.autotune_gemm(prec, reps=0) == 0
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n", [1, 5, 16, 37, 130, 300])
 def test_heig_matches_numpy(lib, prec, n):
