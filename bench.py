@@ -238,6 +238,23 @@ def layer_bytes(layers, elt):
     return tot
 
 
+def max_over_ranks(ms: float, dist=None, device: str = "cuda") -> float:
+    """The job's time: the slowest rank's (all-reduce MAX over the process group); the
+    value itself on one process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, units_per_step: float, total_ms: float) -> float:
+    """Whole-job units per second under weak scaling: every rank processes units_per_step
+    per step, and the job takes the slowest rank's time."""
+    return world * steps * units_per_step / (total_ms / 1e3)
+
+
 def batch_circuits(c, batch):
     """The batch of one step: `batch` copies of the workload with seeded angle draws."""
     out = []
@@ -342,12 +359,8 @@ def run_ours(args):
         m.profile(0)
     dprof = {k: sum(d[k] for d in dprofs) for k in ("ms", "launches", "flops")}
     ck = clocks.stop()
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps * args.batch * updates / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(times), dist)
+    value = job_throughput(world, args.steps, args.batch * updates, total_ms)
 
     # end to end through the host-buffer API: every step uploads each circuit's ops from
     # host memory, runs the batch and reads the energies back
@@ -367,12 +380,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         lib.batch_run_host(pool, hosts)
         te.append(time.perf_counter() - t0)
-    e2e_ms = 1e3 * sum(te)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * len(te) * args.batch * updates / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(1e3 * sum(te), dist)
+    e2e_value = job_throughput(world, len(te), args.batch * updates, e2e_ms)
 
     # roofline of the dominant class
     pk = peaks()
