@@ -28,3 +28,7 @@ def table2():
 def philox_kat():
     return [([int(v, 16) for v in x[:4]], [int(v, 16) for v in x[4:6]],
              [int(v, 16) for v in x[6:10]]) for x in rows("philox_kat.txt")]
+
+
+def gaussian_cz():
+    return {x[0]: float(x[1]) for x in rows("gaussian_cz.txt")}

@@ -7,6 +7,10 @@ import pytest
 
 from oracle import ops, pulse
 
+from golden_io import gaussian_cz
+
+GOLD = gaussian_cz()
+
 B0, B1, BD = 1 / 16, 1 / 16, 7 / 8
 
 
@@ -72,8 +76,17 @@ def test_app_e_coherent_dissipation_factors():
     i11 = 4 * 9 + 4                       # vec index of |11><11|
     a_rate = -np.log(abs(s[i01, i01])) / g
     b_rate = -np.log(abs(s[i11, i11])) / (2 * g)
-    assert abs(a_rate / 0.012291 - 1) < 0.08, a_rate
-    assert abs(b_rate / 0.0185454 - 1) < 0.04, b_rate
+    assert abs(a_rate / GOLD["app_e_alpha_rate"] - 1) < 0.08, a_rate
+    assert abs(b_rate / GOLD["app_e_beta_rate"] - 1) < 0.04, b_rate
+
+
+def test_pulse_parameters_are_the_papers():
+    """The oracle's Gaussian CZ uses the Fig. 1 values (angular frequencies, 2 pi x MHz)."""
+    p = pulse.GAUSSIAN
+    assert p["T"] == GOLD["T_us"] and p["width"] == GOLD["width_over_T"]
+    assert p["omega_max"] == pytest.approx(2 * np.pi * GOLD["omega_max_MHz"], rel=1e-15)
+    assert p["delta"] == pytest.approx(2 * np.pi * GOLD["delta_MHz"], rel=1e-15)
+    assert p["blockade"] == pytest.approx(2 * np.pi * GOLD["blockade_MHz"], rel=1e-15)
 
 
 def test_split_integration_converges_to_the_generator_exponential():
