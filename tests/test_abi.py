@@ -124,3 +124,28 @@ def test_cz_pulse_rejects_bad_arguments(pkg):
         pkg.build_cz_pulse(gamma_diss=-1.0, n_steps=10)
     with pytest.raises(pkg.MpdoError):
         pkg.build_cz_pulse(n_steps=10, pulse=dict(pkg.GAUSSIAN_CZ, T=float("nan")))
+
+
+def test_qaoa_layer_cz_rejects_bad_channels(pkg):
+    """The G1 layer builder validates its CZ channel: non-finite entries are
+    MPDO_ERR_NUMERIC, not a silent layer."""
+    s = np.eye(81, dtype=complex)
+    s[3, 5] = np.nan
+    with pytest.raises(pkg.MpdoError) as err:
+        pkg.build_qaoa_layer_cz(5, 0, 0.3, 0.2, s)
+    assert err.value.code == -4
+    with pytest.raises(pkg.MpdoError):
+        pkg.build_qaoa_layer_cz(1, 0, 0.3, 0.2, np.eye(81))
+
+
+def test_g1_layer_of_the_ideal_cz_is_the_noiseless_g0_layer(pkg):
+    """With the ideal CZ channel, the G1 layer builder returns the noiseless G0 layer (same
+    ZZ block, same folded one-site gates)."""
+    c = synth.scaled(synth.chain40(), n_sites=5)
+    cz = oops.superop([oops.CZ])
+    for k in range(c.p):
+        g1 = pkg.build_qaoa_layer_cz(c.n_sites, k, c.alpha[k], c.beta[k], cz, c.J, c.bz, 0.0)
+        g0 = pkg.build_qaoa_layer(c.n_sites, k, c.alpha[k], c.beta[k], c.J, c.bz)
+        assert [s for s, _ in g1] == [s for s, _ in g0]
+        for (_, a), (_, b) in zip(g1, g0):
+            assert np.abs(oops.superop(a) - oops.superop(b)).max() < 1e-13
