@@ -49,10 +49,40 @@ DEV_STATS_BYTES = 48
 
 
 WORKLOAD = "chain100"
+GATE_MODEL = "g0"      # g0: ideal CZ + closed-form noise per block; g1: Gaussian-pulse CZ
+PULSE_STEPS = 2000     # integration steps of the G1 pulse channel
 
 
 def workload():
     return synth.chain40() if WORKLOAD == "chain40" else synth.chain100()
+
+
+_CZ_CACHE = {}
+
+
+def lib_layers(lib, c):
+    """The library-built op lists of every layer of circuit c in the selected gate model."""
+    if GATE_MODEL == "g0":
+        return lib.circuit_layers(c)
+    key = ("lib", c.gamma_diss, c.gamma_deph, c.b0, c.b1)
+    if key not in _CZ_CACHE:
+        _CZ_CACHE[key] = lib.build_cz_pulse(c.gamma_diss, c.gamma_deph, c.b0, c.b1,
+                                            n_steps=PULSE_STEPS)[0]
+    return [lib.build_qaoa_layer_cz(c.n_sites, k, c.alpha[k], c.beta[k], _CZ_CACHE[key], c.J,
+                                    c.bz, c.xtalk_phase) for k in range(c.p)]
+
+
+def oracle_layer_ops(c, k):
+    """The oracle's ops of layer k in the selected gate model (its own pulse integration)."""
+    from oracle import qaoa as oqaoa
+    if GATE_MODEL == "g0":
+        return oqaoa.layer_ops(c, k)
+    from oracle import pulse as opulse
+    key = ("oracle", c.gamma_diss, c.gamma_deph, c.b0, c.b1, c.bd)
+    if key not in _CZ_CACHE:
+        _CZ_CACHE[key] = opulse.cz_superop(c.gamma_diss, c.gamma_deph, c.b0, c.b1, c.bd,
+                                           PULSE_STEPS)[0]
+    return oqaoa.layer_ops_cz(c, k, _CZ_CACHE[key])
 
 
 PREC_DESC = {
@@ -67,11 +97,15 @@ PREC_DESC = {
 def workload_desc(c, prec, sv):
     return {"workload": f"{WORKLOAD}: N={c.n_sites} atoms (d=3), QAOA p={c.p}, chi={c.chi_max}, "
                         f"K={c.k_max}, decay {c.gamma_diss}, dephasing {c.gamma_deph}, "
-                        f"crosstalk {c.xtalk_phase} rad, post-promotion {c.delta_pp} rad, "
-                        f"TFIM J={c.J} h={c.hx}, seed {c.seed}",
+                        f"crosstalk {c.xtalk_phase} rad, "
+                        + (f"post-promotion {c.delta_pp} rad, " if GATE_MODEL == "g0" else "")
+                        + f"TFIM J={c.J} h={c.hx}, seed {c.seed}",
             "updates_per_circuit": c.p * (c.n_sites - 1),
             "precision": PREC_DESC[prec], "bond_cut": f"s > {sv:g} s_max" if sv else "numerical floor",
-            "parallelism": "replicas", "gate_model": "G0 (gate level)",
+            "parallelism": "replicas",
+            "gate_model": ("G0 (gate level)" if GATE_MODEL == "g0" else
+                           f"G1 (Gaussian-pulse CZ of Fig. 1, rates per pulse, {PULSE_STEPS} "
+                           f"integration steps)"),
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -92,10 +126,10 @@ def oracle_sample(c, budget_s: float, n_steps: int = 0, sv: float = 0.0):
     layer_t = []
     for k in range(c.p - 1):
         t0 = time.perf_counter()
-        for i, kr in oqaoa.layer_ops(c, k):
+        for i, kr in oracle_layer_ops(c, k):
             m.apply_two_site(i, kr)
         layer_t.append(time.perf_counter() - t0)
-    last = oqaoa.layer_ops(c, c.p - 1)
+    last = oracle_layer_ops(c, c.p - 1)
     per = []
     t_start = time.perf_counter()
     for i, kr in last:
@@ -134,10 +168,10 @@ def run_reference(args):
     layer_t = []
     for k in range(c.p - 1):
         t1 = time.perf_counter()
-        for i, kr in oqaoa.layer_ops(c, k):
+        for i, kr in oracle_layer_ops(c, k):
             m.apply_two_site(i, kr)
         layer_t.append(time.perf_counter() - t1)
-    last = oqaoa.layer_ops(c, c.p - 1)
+    last = oracle_layer_ops(c, c.p - 1)
     per = []
     for s, (i, kr) in enumerate(last[: args.warmup + args.steps]):
         t1 = time.perf_counter()
@@ -295,7 +329,7 @@ def run_ours(args):
     prec = args.prec
     sv = bond_cut(args)
     circs = batch_circuits(c, args.batch)
-    host_layers = [lib.circuit_layers(ci) for ci in circs]
+    host_layers = [lib_layers(lib, ci) for ci in circs]
     m_max = max(k.shape[0] for L in host_layers for layer in L for _, k in layer)
     lprec = "fp64" if prec == "fp64" else "c64"
     pool = [lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec=lprec, own_stream=True,
@@ -474,7 +508,7 @@ def run_batch512(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     sv = bond_cut(args)
     circs = synth.batch512()
-    host_layers = [lib.circuit_layers(ci) for ci in circs]
+    host_layers = [lib_layers(lib, ci) for ci in circs]
     m_max = max(k.shape[0] for L in host_layers for layer in L for _, k in layer)
     n_cap = max(ci.n_sites for ci in circs)
     chi_cap = max(ci.chi_max for ci in circs)
@@ -565,13 +599,20 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="pick GEMM tile shapes with the library's autotuner before timing "
                          "(default: the built-in size rules, faster under concurrency)")
+    ap.add_argument("--gate-model", choices=["g0", "g1"], default="g0",
+                    help="g0: ideal CZ with closed-form noise per block; g1: the Gaussian-pulse "
+                         "CZ channel integrated from the Lindbladian (chain workloads)")
     ap.add_argument("--batch", type=int, default=32,
                     help="circuits per step, run concurrently by the batch executor")
     ap.add_argument("--workload", choices=["chain100", "chain40", "batch512"], default="chain100",
                     help="chain40 (N=40, p=2, chi=64, K=8) is the small profiling case")
     args = ap.parse_args()
-    global WORKLOAD
+    global WORKLOAD, GATE_MODEL
     WORKLOAD = args.workload
+    GATE_MODEL = args.gate_model
+    if GATE_MODEL == "g1" and WORKLOAD == "batch512":
+        # every circuit there has its own rates, i.e. its own pulse integration
+        ap.error("--gate-model g1 runs the chain workloads only")
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
