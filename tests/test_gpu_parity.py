@@ -258,6 +258,32 @@ def test_batch512_sample_through_executor(lib):
         m.close()
 
 
+def _g1_run(lib, c, s_lib, s_or, prec, sv_cutoff=0.0, **kw):
+    g = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=63, prec=prec, sv_cutoff=sv_cutoff, **kw)
+    for k in range(c.p):
+        g.apply_layer(lib.build_qaoa_layer_cz(c.n_sites, k, c.alpha[k], c.beta[k], s_lib, c.J,
+                                              c.bz, c.xtalk_phase))
+    e = g.expect_energy(c.J, c.hx, c.bz)
+    g.close()
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max,
+                   sv_cutoff=sv_cutoff if sv_cutoff > 0 else 1e-14)
+    for i, kr in oqaoa.circuit_ops(c, s_or):
+        m.apply_two_site(i, kr)
+    return e, oobs.expect_energy(m, c.J, c.hx, c.bz)
+
+
+def test_g1_pulse_circuit_mixed_precision(lib):
+    """Gate model G1 in the mixed precision form (FP32 site tensors, FP64 Grams) at the bond
+    cut 1e-4, against the FP64 oracle at the same cut: within the mixed form's bounds."""
+    from oracle import pulse as opulse
+    c = synth.scaled(synth.chain40(), n_sites=7, chi_max=64, k_max=16)
+    s_lib, _, _ = lib.build_cz_pulse(c.gamma_diss, c.gamma_deph, c.b0, c.b1, n_steps=300)
+    s_or, _ = opulse.cz_superop(c.gamma_diss, c.gamma_deph, c.b0, c.b1, c.bd, 300)
+    e, r = _g1_run(lib, c, s_lib, s_or, "c64", sv_cutoff=1e-4, gram_fp64=True)
+    for key in r:
+        assert _rel(e[key], r[key]) < MIXED_TOL[key], (key, e[key], r[key])
+
+
 def test_g1_pulse_circuit_matches_oracle(lib):
     """Gate model G1: blocks built from the pulse-level CZ (63 Kraus operators each) by the
     library's host builder, run through the CUDA path in FP64, against the oracle MPDO on the
