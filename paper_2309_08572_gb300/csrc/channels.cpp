@@ -304,13 +304,13 @@ void apply_one_atom(Mat& s, const Mat& n1, int site) {
 int cz_pulse(const mpdo_pulse& p, double gd, double gp, double b0, double b1, int n_steps,
              Mat& s, double& phi1, double& infid) {
   const double tau = p.T / n_steps;
-  // noiseless pulse and its phase correction
+  auto step = [&](int k) {
+    return expmh(tau, pulse_hamiltonian(gaussian_omega((k + 0.5) * tau, p), p), 9);
+  };
+  // noiseless pulse and its phase correction (the step exponentials are recomputed in the
+  // second pass rather than stored: n_steps may be large)
   Mat u = eye(9);
-  std::vector<Mat> steps(n_steps);
-  for (int k = 0; k < n_steps; ++k) {
-    steps[k] = expmh(tau, pulse_hamiltonian(gaussian_omega((k + 0.5) * tau, p), p), 9);
-    u = matmul(steps[k], u, 9);
-  }
+  for (int k = 0; k < n_steps; ++k) u = matmul(step(k), u, 9);
   phi1 = std::arg(u[1 * 9 + 1]) - std::arg(u[0]);
   Mat c1 = op3({1, 0, 0, 0, std::exp(zc(0, -phi1)), 0, 0, 0, 1});
   Mat cc = kron(c1, 3, c1, 3);
@@ -325,7 +325,7 @@ int cz_pulse(const mpdo_pulse& p, double gd, double gp, double b0, double b1, in
   for (int k = 0; k < n_steps; ++k) {
     apply_one_atom(s, nh, 0);
     apply_one_atom(s, nh, 1);
-    apply_unitary(s, steps[k]);
+    apply_unitary(s, step(k));
     apply_one_atom(s, nh, 0);
     apply_one_atom(s, nh, 1);
   }
