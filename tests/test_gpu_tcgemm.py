@@ -1,0 +1,110 @@
+"""Tensor-core GEMM (tcgen05 + TMA) through the C ABI.
+
+The real core is checked bit-exactly on small-integer inputs (every product and partial
+sum is exact in FP32, so any layout, swizzle or descriptor slip shows as a wrong entry),
+over ragged shapes that span several 128 x BN tiles, k-blocks and pipeline stages.  The
+complex split-precision products are checked against numpy complex128 within the bound of
+their arithmetic, relative to sum |a||b|: the operand rounding (TF32x3 keeps ~22
+significand bits per operand, 3 x 2^-22 ~ 7e-7 per product plus headroom -> 3e-6; BF16x3
+~16 bits -> 6e-5; plain TF32 2^-11 -> 2e-3; plain BF16 2^-8 -> 1.6e-2) plus the FP32
+accumulation in tensor memory over the real K extent kr = parts * 2k, which behaves as a
+random walk of roundings: 2 sqrt(kr) 2^-24.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2309_08572_gb300 as pkg
+    return pkg
+
+
+def _ld(k, elt):
+    q = 16 // elt
+    return (k + q - 1) // q * q
+
+
+@pytest.mark.parametrize("elt", [4, 2])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (128, 64, 32), (129, 65, 33), (300, 200, 97),
+                                   (256, 256, 512), (77, 513, 1000), (640, 130, 70)])
+def test_real_core_exact_on_integers(lib, elt, m, n, k):
+    rng = np.random.default_rng(m * 7 + n * 13 + k + elt)
+    a = rng.integers(-4, 5, size=(m, k)).astype(np.float32)
+    b = rng.integers(-4, 5, size=(n, k)).astype(np.float32)
+    lda = ldb = _ld(k, elt)
+    dt = torch.float32 if elt == 4 else torch.bfloat16
+    ta = torch.zeros((m, lda), dtype=dt, device="cuda")
+    tb = torch.zeros((n, ldb), dtype=dt, device="cuda")
+    ta[:, :k] = torch.tensor(a, device="cuda").to(dt)
+    tb[:, :k] = torch.tensor(b, device="cuda").to(dt)
+    td = torch.full((m, n), float("nan"), dtype=torch.float32, device="cuda")
+    lib.kernel_tcgemm_real(elt, m, n, k, ta, lda, tb, ldb, td, n)
+    torch.cuda.synchronize()
+    want = a.astype(np.float64) @ b.astype(np.float64).T
+    got = td.cpu().numpy().astype(np.float64)
+    assert np.array_equal(got, want), np.argwhere(got != want)[:5]
+
+
+def _rand(rng, shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+
+
+def _op(x, op):
+    return {0: x, 1: x.T, 2: x.conj().T, 3: x.conj()}[op]
+
+
+BOUND = {"tf32x3": 3e-6, "bf16x3": 6e-5, "tf32": 2e-3, "bf16": 1.6e-2}
+PARTS = {"tf32x3": 3, "bf16x3": 3, "tf32": 1, "bf16": 1}
+
+
+def _bound(mode, k):
+    return BOUND[mode] + 2.0 * np.sqrt(PARTS[mode] * 2 * k) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("mode", ["tf32x3", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("opa,opb", [(0, 0), (1, 0), (2, 0), (0, 1), (0, 2), (3, 3), (2, 2)])
+def test_complex_modes_vs_numpy(lib, mode, opa, opb):
+    rng = np.random.default_rng(opa * 4 + opb)
+    m, n, k, batch = 150, 70, 133, 2
+    ash = (m, k) if opa in (0, 3) else (k, m)
+    bsh = (k, n) if opb in (0, 3) else (n, k)
+    a = _rand(rng, (batch,) + ash)
+    b = _rand(rng, (batch,) + bsh)
+    ta = torch.tensor(a, device="cuda")
+    tb = torch.tensor(b, device="cuda")
+    tc = torch.zeros((batch, m, n), dtype=torch.complex64, device="cuda")
+    lib.kernel_tcgemm(mode, opa, opb, m, n, k, ta, ash[1], ash[0] * ash[1], tb, bsh[1],
+                      bsh[0] * bsh[1], tc, n, m * n, batch)
+    torch.cuda.synchronize()
+    a64, b64 = a.astype(np.complex128), b.astype(np.complex128)
+    want = np.stack([_op(a64[i], opa) @ _op(b64[i], opb) for i in range(batch)])
+    scale = np.stack([np.abs(_op(a64[i], opa)) @ np.abs(_op(b64[i], opb)) for i in range(batch)])
+    err = (np.abs(tc.cpu().numpy() - want) / scale).max()
+    assert err < _bound(mode, k), err
+
+
+@pytest.mark.parametrize("m,n,k", [(2304, 2304, 768), (400, 400, 5292), (3150, 672, 126)])
+def test_tf32x3_update_shapes(lib, m, n, k):
+    """Shapes of the update's contractions at chi = 256 (bond Gram), and at D = 42 with 25
+    gate Kraus operators and K = 16 (inner Gram, centre tensor)."""
+    rng = np.random.default_rng(m + n + k)
+    a = _rand(rng, (m, k))
+    b = _rand(rng, (k, n))
+    tc = torch.zeros((m, n), dtype=torch.complex64, device="cuda")
+    lib.kernel_tcgemm("tf32x3", 0, 0, m, n, k, torch.tensor(a, device="cuda"), k, 0,
+                      torch.tensor(b, device="cuda"), n, 0, tc, n, 0, 1)
+    torch.cuda.synchronize()
+    rows = rng.choice(m, 24, replace=False)
+    want = a[rows].astype(np.complex128) @ b.astype(np.complex128)
+    scale = np.abs(a[rows]).astype(np.float64) @ np.abs(b).astype(np.float64)
+    err = (np.abs(tc.cpu().numpy()[rows] - want) / scale).max()
+    assert err < _bound("tf32x3", k), err
