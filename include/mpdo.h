@@ -47,11 +47,21 @@ enum {
  *  MPDO_C64  : complex64 state, FP32 GEMMs (FP32 accumulation), FP32 Jacobi;
  *              cutoff, PPT and trace renormalisation in FP64 scalars.  With
  *              mpdo_config.gram_fp64 = 1 the Grams and the small matrices are FP64.
- *  MPDO_TF32X3, MPDO_BF16X3 : reserved for tensor-core split-precision contractions;
- *              not built: mpdo_create rejects them with MPDO_ERR_ARG. */
+ *  MPDO_TF32X3, MPDO_BF16X3 : complex64 state as MPDO_C64, with every complex64 product
+ *              of at least 2^21 complex multiply-adds run on the tensor cores (tcgen05.mma,
+ *              TMA-fed) in split precision: operands x = hi + lo in TF32 (resp. BF16),
+ *              hi*hi + hi*lo + lo*hi accumulated in FP32 (~2^-22 resp. ~2^-16 relative per
+ *              product).  gram_fp64 = 0: the Grams are such products too, and the numerical
+ *              floor of the cuts is 10 x 2.4e-7 (TF32X3) resp. 10 x 1.5e-5 (BF16X3) of the
+ *              largest weight.  gram_fp64 = 1: the mixed form (FP64 Grams and small
+ *              matrices) with its FP32 products -- the new centre B_j, the inner isometry,
+ *              sampling -- on the tensor cores.
+ *              The routing threshold can be changed with the environment variable
+ *              MPDO_TC_MIN_MACS (read at create; 0 routes every product). */
 typedef enum { MPDO_FP64 = 0, MPDO_C64 = 1, MPDO_TF32X3 = 2, MPDO_BF16X3 = 3 } mpdo_prec;
 
-typedef struct mpdo_ctx* mpdo_t;   /* opaque; the library owns all its device memory */
+typedef struct mpdo_ctx* mpdo_t;   /* opaque; the handle owns its device memory (allocated
+                                      through the config's hooks when given)              */
 
 typedef struct {
   int n_sites;          /* N >= 2                                                       */
@@ -65,12 +75,28 @@ typedef struct {
   int use_ppt;          /* 1: purity-preserving inner truncation; 0: plain + trace renorm  */
   void* cuda_stream;    /* cudaStream_t to use; NULL = a non-blocking stream the handle owns
                            (pass cudaStreamLegacy to run on the legacy default stream)   */
-  int gram_fp64;        /* MPDO_C64 only.  1 = mixed precision: the Gram matrices (a2, a8)
+  int gram_fp64;        /* MPDO_C64, MPDO_TF32X3, MPDO_BF16X3.  1 = mixed precision: the Gram matrices (a2, a8)
                            are formed from the FP32 tensors with FP64 products and sums, and
                            everything derived from them (Jacobi eigenpairs, bond factors,
                            Phi and H, the cuts, PPT) is FP64; site tensors and the large
                            contractions stay FP32.  The numerical floor of the cuts drops
                            from ~6e-7 to ~1e-13 of the largest weight.  Ignored otherwise. */
+  int order;            /* sweep order of the layers (reading of Sec. IV, blocks "applied
+                           sequentially"): 0 = left to right -- when a layer's first two-site op
+                           is on bond (0,1) and the orthogonality centre is elsewhere, the centre
+                           is first moved to site 0 by identity two-site updates (truncated
+                           with the handle's cuts), so every layer can run left to right;
+                           1 = snake -- ops must touch the centre, layers alternate direction
+                           (as the QAOA layer builder orders them).  Both give the same result
+                           for snake-ordered layers.                                        */
+  /* Device-memory hooks.  When alloc is non-NULL every device buffer the handle owns is
+   * obtained as alloc(bytes, alloc_ctx) and returned with free(ptr, alloc_ctx) (free must
+   * then be non-NULL too), so an outside allocator (e.g. a framework's caching allocator)
+   * owns the memory; alloc returns NULL when it cannot serve the request, which the call
+   * reports as MPDO_ERR_OOM.  NULL hooks: cudaMalloc / cudaFree. */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
 } mpdo_config;
 
 /* One op of a layer.  kind 2: two-site channel on (site, site+1) with n_kraus Kraus
@@ -199,7 +225,8 @@ const char* mpdo_last_error(mpdo_t h);
  * (branching b0, b1, bd; Sec. II jump operators) and dephasing (linear rate) on both
  * atoms, then the one-site unitaries post_left / post_right (3x3 complex128, may be
  * NULL).  The Kraus set is the Choi eigendecomposition, eigenvalues below
- * eta*lambda_max dropped.  out: host complex128 [cap][9][9]; *n_kraus receives M.
+ * eta*lambda_max dropped (eta >= 0; the layer builders below reject a negative eta with
+ * MPDO_ERR_ARG too).  out: host complex128 [cap][9][9]; *n_kraus receives M.
  * Returns MPDO_ERR_ARG if cap < M. */
 int mpdo_build_block_channel(double angle_zz, double gamma_diss, double gamma_deph,
                              double xtalk_phase, double delta_pp, double b0, double b1,
@@ -288,6 +315,27 @@ int mpdo_kernel_cgemm(int prec, int opa, int opb, int m, int n, int k, const voi
  * columns of v (n x n row-major complex of the same precision).  Returns sweeps used
  * in *sweeps (host). */
 int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, void* stream);
+
+/* Tensor-core GEMMs (tcgen05.mma, TMEM accumulators, TMA-fed shared-memory pipeline) on
+ * which the contractions of the two-site update run in the split-precision modes (Sec.
+ * III.A: contracting the site tensors and the gate, Fig. 6a; the Gram products of the
+ * truncation).  Device pointers; stream = cudaStream_t (NULL = legacy default stream);
+ * both calls synchronise the stream and allocate their own scratch (test entry points).
+ * mpdo_kernel_tcgemm_real: d (m x n FP32, row stride ldd) = a b^T with a (m x k) and b
+ *   (n x k) K-major, elements FP32 read as TF32 (elt 4) or BF16 (elt 2); lda, ldb in
+ *   elements, >= k and multiples of 16 bytes.
+ * mpdo_kernel_tcgemm: complex64 c[b] = op(a[b]) op(b[b]) (ops and layouts as in
+ *   mpdo_kernel_cgemm) in mode 0 TF32, 1 TF32x3 (hi/lo split, FP32-level accuracy),
+ *   2 BF16, 3 BF16x3, FP32 accumulation.
+ * MPDO_ERR_ARG for bad sizes or layouts, MPDO_ERR_OOM, MPDO_ERR_CUDA, MPDO_ERR_TIMEOUT when a
+ * pipeline wait inside the kernel gave up (the output is then undefined). */
+/* Number of tensor-core GEMM kernels (tcgen05) this library has launched in the process. */
+long long mpdo_tc_gemm_launches(void);
+int mpdo_kernel_tcgemm_real(int elt, int m, int n, int k, const void* a, long lda, const void* b,
+                            long ldb, float* d, long ldd, void* stream);
+int mpdo_kernel_tcgemm(int mode, int opa, int opb, int m, int n, int k, const void* a, long lda,
+                       long sa, const void* b, long ldb, long sb, void* c, long ldc, long sc,
+                       int batch, void* stream);
 
 /* MLP surrogate (no counterpart in the paper; the workload's learned part).  A fully
  * connected network with tanh hidden layers and a linear output maps a circuit description

@@ -32,7 +32,14 @@ class Config(C.Structure):
     _fields_ = [("n_sites", C.c_int), ("d", C.c_int), ("chi_max", C.c_int), ("k_max", C.c_int),
                 ("m_max", C.c_int), ("prec", C.c_int), ("sv_cutoff", C.c_double),
                 ("kraus_cutoff", C.c_double), ("use_ppt", C.c_int), ("cuda_stream", C.c_void_p),
-                ("gram_fp64", C.c_int)]
+                ("gram_fp64", C.c_int), ("order", C.c_int),
+                ("alloc", C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)),
+                ("free", C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)), ("alloc_ctx", C.c_void_p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+ORDER = {"ltr": 0, "snake": 1}
 
 
 class Op(C.Structure):
@@ -124,6 +131,11 @@ def _load():
                                   C.c_long, VP, C.c_long, C.c_long, I, VP]),
         "mpdo_kernel_heig": (I, [I, I, VP, VP, P(D), P(I), VP]),
         "mpdo_heig_noalloc": (I, [I, I, VP, VP, P(D), P(I), VP]),
+        "mpdo_tc_gemm_launches": (C.c_longlong, []),
+        "mpdo_kernel_tcgemm_real": (I, [I, I, I, I, VP, C.c_long, VP, C.c_long, VP, C.c_long,
+                                        VP]),
+        "mpdo_kernel_tcgemm": (I, [I, I, I, I, I, I, VP, C.c_long, C.c_long, VP, C.c_long,
+                                   C.c_long, VP, C.c_long, C.c_long, I, VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -273,14 +285,23 @@ class Mpdo:
     def __init__(self, n_sites: int, chi_max: int, k_max: int, m_max: int = 25,
                  prec: str = "fp64", sv_cutoff: float = 0.0, kraus_cutoff: float = 0.0,
                  use_ppt: bool = True, init_vec: Optional[Sequence[complex]] = None,
-                 stream=None, own_stream: bool = False, gram_fp64: bool = False):
+                 stream=None, own_stream: bool = False, gram_fp64: bool = False,
+                 order: str = "snake", allocator=None):
+        """allocator: optional (alloc(bytes) -> device address or 0, free(address)) pair that
+        will own every device buffer of the handle (e.g. torch's caching allocator)."""
         self.n = n_sites
         if own_stream:
             st = C.c_void_p(None)            # the library creates a non-blocking stream
         else:
             st = _current_stream() if stream is None else C.c_void_p(stream)
         cfg = Config(n_sites, 3, chi_max, k_max, m_max, PREC[prec], sv_cutoff, kraus_cutoff,
-                     int(use_ppt), st, int(gram_fp64))
+                     int(use_ppt), st, int(gram_fp64), ORDER[order])
+        self._hooks = None
+        if allocator is not None:
+            fa, ff = allocator
+            self._hooks = (ALLOC_FN(lambda nbytes, ctx: fa(int(nbytes)) or None),
+                           FREE_FN(lambda ptr, ctx: ff(ptr)))
+            cfg.alloc, cfg.free = self._hooks
         self._h = C.c_void_p(None)
         v = None if init_vec is None else np.ascontiguousarray(np.asarray(init_vec, complex)).view(float)
         rc = LIB.mpdo_create(C.byref(cfg), None if v is None else _dptr(v), C.byref(self._h))
@@ -374,16 +395,6 @@ class Mpdo:
         dims = (C.c_int * 4)()
         _check(LIB.mpdo_get_site(self._h, n, _dptr(out), cap, dims), self._h)
         return out.view(complex).reshape(tuple(dims))
-
-    def to_dense(self) -> np.ndarray:
-        """rho as a d^N x d^N matrix (tiny chains only; host-side reassembly for tests)."""
-        x = np.ones((1, 1, 1, 1), dtype=complex)
-        for n in range(self.n):
-            a = self.site(n)
-            x = np.einsum("pqab,askr,btkc->psqtrc", x, a, a.conj(), optimize=True)
-            p, s, q, t, r, c = x.shape
-            x = x.reshape(p * s, q * t, r, c)
-        return x[:, :, 0, 0]
 
 
 def batch_run(pool: Sequence["Mpdo"], circuits: Sequence[dict]) -> np.ndarray:
@@ -561,3 +572,32 @@ def kernel_heig_noalloc(prec: int, n: int, a, v, w, stream=None) -> int:
                                  C.cast(C.c_void_p(w.data_ptr()), C.POINTER(C.c_double)),
                                  C.byref(sweeps), st))
     return sweeps.value
+
+
+TC_MODES = {"tf32": 0, "tf32x3": 1, "bf16": 2, "bf16x3": 3}
+
+
+def tc_gemm_launches() -> int:
+    """Tensor-core (tcgen05) GEMM kernels launched by libmpdo in this process so far."""
+    return int(LIB.mpdo_tc_gemm_launches())
+
+
+def kernel_tcgemm_real(elt: int, m: int, n: int, k: int, a, lda: int, b, ldb: int, d, ldd: int,
+                       stream=None):
+    """d (m x n, FP32) = a (m x k) b (n x k)^T on the tensor cores; a, b FP32 (read as TF32,
+    elt 4) or BF16 (elt 2) device tensors, K-major."""
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    _check(LIB.mpdo_kernel_tcgemm_real(elt, m, n, k, C.c_void_p(a.data_ptr()), lda,
+                                       C.c_void_p(b.data_ptr()), ldb, C.c_void_p(d.data_ptr()),
+                                       ldd, st))
+
+
+def kernel_tcgemm(mode, opa: int, opb: int, m: int, n: int, k: int, a, lda: int, sa: int, b,
+                  ldb: int, sb: int, c, ldc: int, sc: int, batch: int, stream=None):
+    """c = op(a) op(b) (complex64 device tensors) on the tensor cores in mode "tf32",
+    "tf32x3", "bf16" or "bf16x3"."""
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    md = TC_MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(LIB.mpdo_kernel_tcgemm(md, opa, opb, m, n, k, C.c_void_p(a.data_ptr()), lda, sa,
+                                  C.c_void_p(b.data_ptr()), ldb, sb, C.c_void_p(c.data_ptr()),
+                                  ldc, sc, batch, st))

@@ -34,6 +34,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "kernels.h"
+#include "tcgemm.h"
 
 using namespace mpdo;
 
@@ -101,6 +102,15 @@ struct mpdo_ctx {
   EigWork<float> eig32;
   // FP32 site tensors with FP64 Gram matrices and small-matrix arithmetic (cfg.gram_fp64)
   bool mixed = false;
+  // complex64 products on the tensor cores (MPDO_TF32X3 / MPDO_BF16X3): the operand mode
+  // (TC_TF32X3 / TC_BF16X3, -1 = CUDA-core GEMMs), the packing workspace and the device flag
+  // the pipeline sets when one of its bounded waits gives up
+  int tcmode = -1;
+  void* tcws = nullptr;
+  size_t tcws_bytes = 0;
+  int* tcerr = nullptr;
+  int* htcerr = nullptr;   // pinned
+  double tc_min_macs = 0;  // routing threshold (kTcMinMacs; MPDO_TC_MIN_MACS overrides)
   // Waits for the host read-backs of the update: spinning (cudaStreamSynchronize) for one
   // circuit; blocking on an event (the thread sleeps) while the batch executor runs many
   // circuits, whose spinning host threads would otherwise take every core.
@@ -119,6 +129,8 @@ struct mpdo_ctx {
   StepScalars* hsc = nullptr;  // pinned
   DevStats* dstats = nullptr;
   DevStats* hstats = nullptr;  // pinned
+  // identity two-site channel (one op, uploaded at create) for the left-to-right order
+  mpdo_dlayer_s ident;
   // staging for host layers
   mpdo_dlayer_s staged;
   size_t staged_cap = 0;
@@ -204,19 +216,34 @@ EigWork<double>& eigw<double>(mpdo_ctx* h) { return h->eig64; }
 template <>
 EigWork<float>& eigw<float>(mpdo_ctx* h) { return h->eig32; }
 
+// Device memory of a handle: through the config's hooks when given, else cudaMalloc.
+void* dmalloc(mpdo_ctx* h, size_t bytes) {
+  if (h->cfg.alloc) return h->cfg.alloc(bytes, h->cfg.alloc_ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void dfree(mpdo_ctx* h, void* p) {
+  if (!p) return;
+  if (h->cfg.alloc) h->cfg.free(p, h->cfg.alloc_ctx);
+  else cudaFree(p);
+}
+
 int alloc_dev(mpdo_ctx* h, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(h, MPDO_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
-  }
+  *p = dmalloc(h, bytes);
+  if (!*p) return fail(h, MPDO_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
   // no handle buffer ever starts with stale contents of earlier allocations
-  e = cudaMemset(*p, 0, bytes);
+  cudaError_t e = cudaMemsetAsync(*p, 0, bytes, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(*p);
-    return fail(h, MPDO_ERR_CUDA, "cudaMemset of a new buffer failed");
+    dfree(h, *p);
+    *p = nullptr;
+    return fail(h, MPDO_ERR_CUDA, "clearing a new device buffer failed");
   }
   h->allocs.push_back(*p);
   return MPDO_OK;
@@ -232,16 +259,36 @@ cudaError_t sync_stream(mpdo_ctx* h) {
 
 int read_scalars(mpdo_ctx* h) {
   CK(cudaMemcpyAsync(h->hsc, h->dsc, sizeof(StepScalars), cudaMemcpyDeviceToHost, h->st));
+  if (h->tcerr) CK(cudaMemcpyAsync(h->htcerr, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(sync_stream(h));
   prof_drain(h);
+  if (h->tcerr && *h->htcerr)
+    return fail(h, MPDO_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait gave up");
   if (h->hsc->flags & 1) return fail(h, MPDO_ERR_NUMERIC, "zero or non-finite state in update");
   return MPDO_OK;
 }
+
+// Products at least this large (complex multiply-adds, both output sides >= kTcMinSide) run on
+// the tensor cores in the MPDO_TF32X3 / MPDO_BF16X3 modes; smaller ones stay on the CUDA-core
+// kernels, whose single launch has less latency than packing plus a pipelined tile.
+constexpr double kTcMinMacs = 1 << 21;
+constexpr int kTcMinSide = 16;
 
 template <typename R>
 cudaError_t pgemm(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<R>* A, long lda,
                   long sa, const cx<R>* B, long ldb, long sb, cx<R>* C, long ldc, long sc,
                   int batch) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (h->tcmode >= 0 && (double)m * n * k * batch >= h->tc_min_macs && m >= kTcMinSide &&
+        n >= kTcMinSide && k >= 1) {
+      int pi = prof_begin(h, 0);
+      cudaError_t e = tc_cgemm<float>(h->st, h->tcmode, opa, opb, m, n, k, A, lda, sa, B, ldb,
+                                      sb, C, ldc, sc, batch, make_float2(1.f, 0.f),
+                                      make_float2(0.f, 0.f), h->tcws, h->tcws_bytes, h->tcerr);
+      prof_end(h, 0, pi, 8.0 * m * n * (double)k * batch);
+      return e;
+    }
+  }
   int pi = prof_begin(h, 0);
   cudaError_t e = cgemm<R>(h->st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch,
                            one<R>(), zero<R>());
@@ -853,15 +900,20 @@ int prepare_layer(mpdo_ctx* h, const mpdo_layer* layer, mpdo_dlayer_s* dl, bool 
   void* dev = nullptr;
   if (staged) {
     if (h->staged_cap < total) {
-      if (h->staged.mem) { cudaFree(h->staged.mem); h->staged.mem = nullptr; }
-      cudaError_t ce = cudaMalloc(&h->staged.mem, total + 256);
-      if (ce != cudaSuccess) { cudaGetLastError(); return fail(h, MPDO_ERR_OOM, "layer staging"); }
+      if (h->staged.mem) {
+        CK(cudaStreamSynchronize(h->st));
+        dfree(h, h->staged.mem);
+        h->staged.mem = nullptr;
+        h->staged_cap = 0;
+      }
+      h->staged.mem = dmalloc(h, total + 256);
+      if (!h->staged.mem) return fail(h, MPDO_ERR_OOM, "layer staging");
       h->staged_cap = total;
     }
     dev = h->staged.mem;
   } else {
-    cudaError_t ce = cudaMalloc(&dev, total + 256);
-    if (ce != cudaSuccess) { cudaGetLastError(); return fail(h, MPDO_ERR_OOM, "layer upload"); }
+    dev = dmalloc(h, total + 256);
+    if (!dev) return fail(h, MPDO_ERR_OOM, "layer upload");
     dl->mem = dev;
   }
   CK(cudaMemcpyAsync(dev, hbuf, total, cudaMemcpyHostToDevice, h->st));
@@ -913,6 +965,25 @@ int run_ops(mpdo_ctx* h, const std::vector<DevOp>& ops, mpdo_trunc_stats* stats,
                                        std::to_string(h->n) + " sites");
   int rc = reset_stats(h);
   if (rc) return rc;
+  // left-to-right order: a layer that starts on bond (0,1) with the centre elsewhere first
+  // brings the centre to site 0 by identity two-site updates
+  if (h->cfg.order == 0 && !ops.empty() && h->centre != 0) {
+    const DevOp* first = nullptr;
+    for (const DevOp& op : ops)
+      if (op.kind == 2) { first = &op; break; }
+    if (first && first->site == 0) {
+      std::vector<DevOp> moves;
+      for (int i = h->centre - 1; i >= 0; --i) {
+        DevOp d = h->ident.ops[0];
+        d.site = i;
+        moves.push_back(d);
+      }
+      rc = h->dbl     ? apply_ops<double, double>(h, moves, chi, kmax, use_ppt)
+           : h->mixed ? apply_ops<float, double>(h, moves, chi, kmax, use_ppt)
+                      : apply_ops<float, float>(h, moves, chi, kmax, use_ppt);
+      if (rc) return rc;
+    }
+  }
   rc = h->dbl     ? apply_ops<double, double>(h, ops, chi, kmax, use_ppt)
        : h->mixed ? apply_ops<float, double>(h, ops, chi, kmax, use_ppt)
                   : apply_ops<float, float>(h, ops, chi, kmax, use_ppt);
@@ -966,10 +1037,12 @@ int energy(mpdo_ctx* h, double J, double hx, double bz, double out[6]) {
   const long env = chi * chi, fsz = chi * 3 * K * chi;
   size_t need = (2 * 6 * env + 2 * 6 * fsz) * sizeof(TD) + 512;
   if (h->obs_bytes < need) {
-    if (h->obs) cudaFree(h->obs);
-    h->obs = nullptr;
-    cudaError_t ce = cudaMalloc(&h->obs, need);
-    if (ce != cudaSuccess) { cudaGetLastError(); h->obs_bytes = 0; return fail(h, MPDO_ERR_OOM, "energy buffers"); }
+    if (h->obs) {
+      CK(cudaStreamSynchronize(st));
+      dfree(h, h->obs);
+    }
+    h->obs = dmalloc(h, need);
+    if (!h->obs) { h->obs_bytes = 0; return fail(h, MPDO_ERR_OOM, "energy buffers"); }
     h->obs_bytes = need;
   }
   TD* ebuf[2] = {static_cast<TD*>(h->obs), static_cast<TD*>(h->obs) + 6 * env};
@@ -1021,10 +1094,16 @@ int sample(mpdo_ctx* h, int ns, uint64_t seed, uint8_t* bits, double* probs) {
   size_t renv_bytes = (size_t)(N + 1) * env * sizeof(T);
   size_t need = renv_bytes + (size_t)sizeof(T) * (fsz + chunk * (2 * fsz + 5 * env) + env) +
                 (size_t)ns * (N + 8) + 4096;
-  void* mem = nullptr;
-  cudaError_t ce = cudaMalloc(&mem, need);
-  if (ce != cudaSuccess) { cudaGetLastError(); return fail(h, MPDO_ERR_OOM, "sampling buffers"); }
-  std::unique_ptr<void, void (*)(void*)> guard(mem, [](void* p) { cudaFree(p); });
+  void* mem = dmalloc(h, need);
+  if (!mem) return fail(h, MPDO_ERR_OOM, "sampling buffers");
+  struct Guard {
+    mpdo_ctx* h;
+    void* p;
+    ~Guard() {
+      cudaStreamSynchronize(h->st);
+      dfree(h, p);
+    }
+  } guard{h, mem};
   T* renv = static_cast<T*>(mem);                 // R_n, n = 0..N, each env
   T* Y = renv + (N + 1) * env;                    // fsz
   T* Ecur = Y + fsz;                              // chunk * env
@@ -1089,9 +1168,20 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   if (cfg->k_max < 1 || cfg->k_max > 1024) return fail(nullptr, MPDO_ERR_ARG, "k_max out of 1..1024");
   if (cfg->m_max < 1 || (long)cfg->m_max * cfg->k_max > 1024)
     return fail(nullptr, MPDO_ERR_ARG, "m_max*k_max must be in 1..1024");
-  if (cfg->prec != MPDO_FP64 && cfg->prec != MPDO_C64)
-    return fail(nullptr, MPDO_ERR_ARG, "precision mode not available in this build");
-  std::unique_ptr<mpdo_ctx> h(new (std::nothrow) mpdo_ctx());
+  if (cfg->prec < MPDO_FP64 || cfg->prec > MPDO_BF16X3)
+    return fail(nullptr, MPDO_ERR_ARG, "unknown precision mode");
+  if (cfg->order != 0 && cfg->order != 1)
+    return fail(nullptr, MPDO_ERR_ARG, "order must be 0 (left to right) or 1 (snake)");
+  if (cfg->alloc && !cfg->free)
+    return fail(nullptr, MPDO_ERR_ARG, "an alloc hook needs a free hook");
+  // a failed create releases what it allocated (through the hooks) and keeps the message
+  struct CtxDel {
+    void operator()(mpdo_ctx* p) const {
+      if (!p->err.empty()) g_err = p->err;
+      mpdo_destroy(p);
+    }
+  };
+  std::unique_ptr<mpdo_ctx, CtxDel> h(new (std::nothrow) mpdo_ctx());
   if (!h) return fail(nullptr, MPDO_ERR_OOM, "host allocation");
   mpdo_ctx* hp = h.get();
   h->cfg = *cfg;
@@ -1114,11 +1204,20 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   h->elt = h->dbl ? 16 : 8;
   h->mixed = !h->dbl && cfg->gram_fp64;
   h->eltm = (h->dbl || h->mixed) ? 16 : 8;
+  h->tcmode = cfg->prec == MPDO_TF32X3 ? TC_TF32X3 : cfg->prec == MPDO_BF16X3 ? TC_BF16X3 : -1;
+  h->tc_min_macs = kTcMinMacs;
+  if (const char* tm = std::getenv("MPDO_TC_MIN_MACS")) h->tc_min_macs = std::atof(tm);
   // Numerical-zero cuts.  Gram eigenvalues resolve only down to ~eps * max, so the cuts
   // are applied there: bond lambda = s^2 > htol*lambda_0, inner w > kcut^2 * w_0.  With
   // FP64 Grams of FP32 tensors the floor is the rounding of the tensors themselves
   // (relative 6e-8 per entry, i.e. ~4e-15 on lambda), taken as eps = 1e-14.
-  const double eps = h->dbl ? 1e-16 : h->mixed ? 1e-14 : 6e-8;
+  // Tensor-core products of FP32 Grams: TF32x3 keeps ~22 significand bits per operand
+  // (2^-22), BF16x3 ~16 (2^-16); the mixed form's Grams stay FP64 whatever the product engine.
+  const double eps = h->dbl     ? 1e-16
+                     : h->mixed ? 1e-14
+                     : h->tcmode == TC_TF32X3 ? 2.4e-7
+                     : h->tcmode == TC_BF16X3 ? 1.5e-5
+                                              : 6e-8;
   double sv = cfg->sv_cutoff > 0 ? cfg->sv_cutoff : 1e-14;
   h->htol = std::max(sv * sv, 10 * eps);
   // The left factor's rank cut: directions of G_i below gtol carry less than gtol of the
@@ -1194,8 +1293,30 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
     cudaGetLastError();
     return fail(nullptr, MPDO_ERR_OOM, "pinned host allocation");
   }
+  if (h->tcmode >= 0) {
+    // packed operands of the tensor-core products: long K loops are processed in chunks
+    // that fit (tc_cgemm), so the workspace only needs to hold a few k-blocks of the
+    // largest packed pair
+    const size_t want = (size_t)(D <= 64 ? 64 : 256) << 20;
+    if ((rc = alloc_dev(hp, &h->tcws, want))) return rc;
+    h->tcws_bytes = want;
+    if ((rc = alloc_dev(hp, (void**)&h->tcerr, sizeof(int)))) return rc;
+    if (cudaMallocHost((void**)&h->htcerr, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(nullptr, MPDO_ERR_OOM, "pinned host allocation");
+    }
+    *h->htcerr = 0;
+  }
+  {
+    // identity channel for the left-to-right order's centre moves
+    std::vector<double> idop(2 * 81, 0.0);
+    for (int a = 0; a < 9; ++a) idop[2 * (a * 9 + a)] = 1.0;
+    mpdo_op op{2, 0, 1, idop.data()};
+    mpdo_layer L{1, &op};
+    if ((rc = prepare_layer(hp, &L, &h->ident, false))) return rc;
+  }
   rc = init_state(hp, init_site_vec);
-  if (rc) { g_err = h->err; return rc; }
+  if (rc) return rc;
   *out = h.release();
   return MPDO_OK;
 }
@@ -1229,9 +1350,16 @@ int mpdo_apply_dlayer(mpdo_t h, mpdo_dlayer dl, mpdo_trunc_stats* stats) {
 
 int mpdo_layer_free(mpdo_t h, mpdo_dlayer dl) {
   if (!dl) return MPDO_OK;
-  if (dl->mem) cudaFree(dl->mem);
+  if (dl->mem) {
+    if (h) {
+      cudaStreamSynchronize(h->st);
+      dfree(h, dl->mem);
+    } else {
+      cudaDeviceSynchronize();
+      cudaFree(dl->mem);
+    }
+  }
   delete dl;
-  (void)h;
   return MPDO_OK;
 }
 
@@ -1436,15 +1564,17 @@ int mpdo_destroy(mpdo_t h) {
   else cudaDeviceSynchronize();
   mix_work_release(h->mixw);
   if (h->bev) cudaEventDestroy(h->bev);
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) dfree(h, p);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   if (h->prof_counts) cudaFreeHost(h->prof_counts);
-  if (h->staged.mem) cudaFree(h->staged.mem);
+  if (h->staged.mem) dfree(h, h->staged.mem);
+  if (h->ident.mem) dfree(h, h->ident.mem);
   if (h->hstage) cudaFreeHost(h->hstage);
-  if (h->obs) cudaFree(h->obs);
+  if (h->obs) dfree(h, h->obs);
   if (h->hsc) cudaFreeHost(h->hsc);
   if (h->hstats) cudaFreeHost(h->hstats);
   if (h->hpc) cudaFreeHost(h->hpc);
+  if (h->htcerr) cudaFreeHost(h->htcerr);
   if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
   return MPDO_OK;

@@ -373,6 +373,8 @@ extern "C" int mpdo_build_block_channel(double angle_zz, double gamma_diss, doub
   if (!finite_all({angle_zz, gamma_diss, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd, eta}))
     return MPDO_ERR_NUMERIC;
   if (gamma_diss < 0 || gamma_deph < 0 || b0 < 0 || b1 < 0 || bd < 0) return MPDO_ERR_ARG;
+  // a negative eta would keep negative Choi eigenvalues (square roots of them are NaN)
+  if (eta < 0) return MPDO_ERR_ARG;
   Mat pl, pr;
   if (post_left) {
     pl.resize(9);
@@ -402,7 +404,8 @@ extern "C" int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double be
                                      double bd, double eta, int* sites, int* ms, double* out,
                                      size_t cap) {
   if (n_sites < 2 || k < 0 || !sites || !ms || !out) return MPDO_ERR_ARG;
-  if (!finite_all({alpha, beta, J, bz})) return MPDO_ERR_NUMERIC;
+  if (!finite_all({alpha, beta, J, bz, eta})) return MPDO_ERR_NUMERIC;
+  if (eta < 0) return MPDO_ERR_ARG;
   // one-site gate exp(-i beta S^x) exp(-i b J alpha S^z), folded after the last block
   Mat v = matmul(expmh(beta, xq(), 3), expmh(bz * J * alpha, zq(), 3), 3);
   std::vector<Mat> both, mid;
@@ -460,6 +463,7 @@ extern "C" int mpdo_build_qaoa_layer_cz(int n_sites, int k, double alpha, double
                                         size_t cap) {
   if (n_sites < 2 || k < 0 || !cz_superop || !sites || !ms || !out) return MPDO_ERR_ARG;
   if (!finite_all({alpha, beta, J, bz, xtalk_phase, eta})) return MPDO_ERR_NUMERIC;
+  if (eta < 0) return MPDO_ERR_ARG;
   Mat scz(81 * 81);
   for (int i = 0; i < 81 * 81; ++i) {
     scz[i] = zc(cz_superop[2 * i], cz_superop[2 * i + 1]);

@@ -149,3 +149,58 @@ def test_g1_layer_of_the_ideal_cz_is_the_noiseless_g0_layer(pkg):
         assert [s for s, _ in g1] == [s for s, _ in g0]
         for (_, a), (_, b) in zip(g1, g0):
             assert np.abs(oops.superop(a) - oops.superop(b)).max() < 1e-13
+
+
+def test_negative_eta_is_rejected(pkg):
+    """A negative Choi cut would keep negative eigenvalues (NaN Kraus operators): every
+    channel builder refuses it."""
+    import ctypes as C
+    out = np.zeros(81 * 81 * 2)
+    m = C.c_int(0)
+    rc = pkg.LIB.mpdo_build_block_channel(0.3, 0.01, 0.01, 0.0, 0.0, 1 / 16, 1 / 16, 7 / 8, None,
+                                          None, -1e-9, pkg._dptr(out), 81, C.byref(m))
+    assert rc == -1
+    sites = (C.c_int * 8)()
+    ms = (C.c_int * 8)()
+    big = np.zeros(8 * 81 * 81 * 2)
+    rc = pkg.LIB.mpdo_build_qaoa_layer(4, 0, 0.3, 0.2, 1.0, 0.0, 0.01, 0.01, 0.0, 0.0, 1 / 16,
+                                       1 / 16, 7 / 8, -1.0, sites, ms, pkg._dptr(big), big.size // 2)
+    assert rc == -1
+    sup = np.eye(81, dtype=complex).view(float).reshape(-1).copy()
+    rc = pkg.LIB.mpdo_build_qaoa_layer_cz(4, 0, 0.3, 0.2, 1.0, 0.0, pkg._dptr(sup), 0.0, -1.0,
+                                          sites, ms, pkg._dptr(big), big.size // 2)
+    assert rc == -1
+
+
+def test_create_rejects_bad_order_and_hooks(pkg):
+    import ctypes as C
+    cfg = pkg.Config(6, 3, 8, 4, 4, pkg.PREC["fp64"], 0.0, 0.0, 1, None, 0, 2)
+    h = C.c_void_p(None)
+    assert pkg.LIB.mpdo_create(C.byref(cfg), None, C.byref(h)) == -1
+    cfg = pkg.Config(6, 3, 8, 4, 4, pkg.PREC["fp64"], 0.0, 0.0, 1, None, 0, 1)
+    cfg.alloc = pkg.ALLOC_FN(lambda n, ctx: None)   # alloc without free
+    assert pkg.LIB.mpdo_create(C.byref(cfg), None, C.byref(h)) == -1
+
+
+def test_forced_oom_through_the_alloc_hook(pkg):
+    """The handle's device memory comes from the config's hooks: an allocator that refuses
+    makes mpdo_create fail with MPDO_ERR_OOM (no GPU needed: the stream is given, so the
+    first device request is the hook's), and nothing it handed out is left behind."""
+    import ctypes as C
+    calls = {"alloc": 0, "free": 0}
+
+    def alloc(n, ctx):
+        calls["alloc"] += 1
+        return None
+
+    def free(p, ctx):
+        calls["free"] += 1
+
+    fa, ff = pkg.ALLOC_FN(alloc), pkg.FREE_FN(free)
+    cfg = pkg.Config(6, 3, 8, 4, 4, pkg.PREC["fp64"], 0.0, 0.0, 1, C.c_void_p(1), 0, 1)
+    cfg.alloc, cfg.free = fa, ff
+    h = C.c_void_p(None)
+    rc = pkg.LIB.mpdo_create(C.byref(cfg), None, C.byref(h))
+    assert rc == -2 and not h.value
+    assert calls["alloc"] == 1 and calls["free"] == 0
+    assert b"allocation" in pkg.LIB.mpdo_last_error(None)

@@ -63,6 +63,18 @@ def _rel(a, b):
     return abs(a - b) / max(1.0, abs(b))
 
 
+def _dense(g):
+    """rho of a GPU handle as a d^N x d^N matrix, reassembled on the host from the site
+    tensors the library returns (tiny chains only; test helper)."""
+    x = np.ones((1, 1, 1, 1), dtype=complex)
+    for n in range(g.n):
+        a = g.site(n)
+        x = np.einsum("pqab,askr,btkc->psqtrc", x, a, a.conj(), optimize=True)
+        p, s, q, t, r, c = x.shape
+        x = x.reshape(p * s, q * t, r, c)
+    return x[:, :, 0, 0]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "c64"])
 def test_tiny_exact_matches_dense(lib, prec):
     c = dataclasses.replace(synth.tiny(), k_max=40)
@@ -73,7 +85,7 @@ def test_tiny_exact_matches_dense(lib, prec):
     r = d.expect(c.J, c.hx, c.bz)
     for key in r:
         assert _rel(e[key], r[key]) < TOL[prec], (key, e[key], r[key])
-    rho = g.to_dense()
+    rho = _dense(g)
     assert np.abs(rho - d.matrix()).max() < (1e-11 if prec == "fp64" else 5e-5)
 
 
@@ -306,3 +318,41 @@ def test_g1_pulse_circuit_matches_oracle(lib):
     r = oobs.expect_energy(m, c.J, c.hx, c.bz)
     for key in r:
         assert _rel(e[key], r[key]) < 1e-9, (key, e[key], r[key])
+
+
+# Tensor-core modes.  Every complex64 product of the update (and of sampling) runs on the
+# tcgen05 path here (MPDO_TC_MIN_MACS=0 routes even the smallest), checked against the
+# oracle at the same bond cut, chosen above each mode's numerical floor (10 x the relative
+# error of one split product: 2.4e-6 for TF32x3, 1.5e-4 for BF16x3, in lambda = s^2) so the
+# cut, not the floor, decides what is kept.  Bounds: one product of relative error e per
+# update and output, accumulated over the ~100 updates of these circuits: ~100 e for the
+# FP32-Gram forms (TF32x3: 2.4e-7 -> 1e-4 with headroom for the FP32 site rounding; BF16x3:
+# 1.5e-5 -> 2e-3); with FP64 Grams (gram_fp64) only the centre tensor and the inner
+# isometry carry the split products, as FP32 products do in the mixed form (MIXED_TOL x 4).
+TC_CASES = {
+    ("tf32x3", False): (3e-3, {"e_succ": 1e-4, "e_raw": 1e-4, "p_succ": 1e-4, "trace": 1e-4}),
+    ("bf16x3", False): (2e-2, {"e_succ": 2e-3, "e_raw": 2e-3, "p_succ": 2e-3, "trace": 2e-3}),
+    ("tf32x3", True): (1e-4, {k: 4 * v for k, v in MIXED_TOL.items()}),
+    ("bf16x3", True): (1e-4, {"e_succ": 1e-4, "e_raw": 1e-4, "p_succ": 1e-4, "trace": 1e-4}),
+}
+
+
+@pytest.mark.parametrize("prec,gram", list(TC_CASES))
+@pytest.mark.parametrize("case", ["n12c16k4", "chain40"])
+def test_tensor_core_modes_match_oracle(lib, monkeypatch, prec, gram, case):
+    monkeypatch.setenv("MPDO_TC_MIN_MACS", "0")
+    sv, tol = TC_CASES[(prec, gram)]
+    if case == "chain40":
+        c = synth.chain40()
+    else:
+        c = synth.scaled(synth.chain40(), n_sites=12, chi_max=16, k_max=4)
+    _, r = _oracle(c, sv_cutoff=sv)
+    n0 = lib.tc_gemm_launches()
+    g, e, _ = _gpu(lib, c, prec, gram_fp64=gram, sv_cutoff=sv)
+    used = lib.tc_gemm_launches() - n0
+    errs = {key: _rel(e[key], r[key]) for key in r}
+    print(prec, "gram_fp64" if gram else "", case, used, errs)
+    assert used > 0
+    for key in r:
+        assert errs[key] < tol[key], (key, e[key], r[key])
+    g.close()
