@@ -127,6 +127,8 @@ struct mpdo_ctx {
   void* wAcM = nullptr;      // polar-corrected left factor in FP64 (mixed only)
   StepScalars* dsc = nullptr;
   StepScalars* hsc = nullptr;  // pinned
+  double* dtrace = nullptr;    // trace of the state, carried in FP64 across updates
+  double htrace0 = 1.0;        // its initial value (host copy, source of the upload)
   DevStats* dstats = nullptr;
   DevStats* hstats = nullptr;  // pinned
   // identity two-site channel (one op, uploaded at create) for the left-to-right order
@@ -295,20 +297,22 @@ cudaError_t pgemm(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<R
   prof_end(h, 0, pi, 8.0 * m * n * (double)k * batch);
   return e;
 }
-// floor: eigenpairs below floor * lambda_max need not be resolved (used by the mixed mode)
+// floor: eigenpairs below floor * lambda_max need not be resolved (used by the mixed mode).
+// kMixedEigMax: largest factor rank taken through the lifted route (the factor buffer holds
+// 128 columns); the mixed solver itself serves any n up to the handle's capacity (one-CTA
+// FP32 sweeps up to n = 118, the cooperative FP32 block Jacobi above, FP64 refinement).
+// max_vals > 0: only that many leading pairs are needed (the rest come back as zeros).
 constexpr int kMixedEigMax = 118;
 template <typename R>
 cudaError_t peig(mpdo_ctx* h, int n, const cx<R>* a, long lda, cx<R>* v, long ldv, double* w,
-                 double floor) {
+                 double floor, int max_vals = 0) {
   int pi = prof_begin(h, 1);
   const int sweeps = std::is_same<R, double>::value ? 30 : 20;
   cudaError_t e;
   if constexpr (std::is_same<R, double>::value) {
-    // mixed mode: FP32 sweeps with FP64 refinement while the sweeps fit one CTA's shared
-    // memory; larger problems take the FP64 solver
-    if (h->mixed && n <= kMixedEigMax) {
+    if (h->mixed && n <= h->mixw.n_cap) {
       double fl = 0.0;
-      e = heig_mixed(h->st, n, a, lda, v, ldv, w, floor, h->mixw, nullptr, &fl);
+      e = heig_mixed(h->st, n, a, lda, v, ldv, w, floor, h->mixw, nullptr, &fl, max_vals);
       prof_end(h, 1, pi, fl);
       return e;
     }
@@ -503,7 +507,8 @@ int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
                     false, &nv);
   if (rc) return rc;
   if (nv == 0) {
-    CK(peig<RM>(h, nin, W, nin, V, nin, h->wWv, 1e-10));
+    // at most k_max pairs are kept; the PPT's sum of squares comes from ||W||_F
+    CK(peig<RM>(h, nin, W, nin, V, nin, h->wWv, 1e-10, h->kmax + 1));
     nv = nin;
   }
   *nvals = nv;
@@ -558,6 +563,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
   CK((pgram<RS, RM>(h, OP_C, OP_N, n3, n3, dl * ki, wM, n3, wM, n3, wGi, n3)));
   CK((pgram<RS, RM>(h, OP_N, OP_C, n3, n3, kj * dr, aj, (long)kj * dr, aj, (long)kj * dr, wGj,
                     n3)));
+  PO(trace_pre<RM>(st, dm, wGi, wGj, h->dsc));
   // a3: left factor from the eigendecomposition of G_i (numerical rank by gtol)
   {
     int nv = 0;
@@ -570,7 +576,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
                         0.1 * h->gtol, true, &nv);
       if (rc) return rc;
     }
-    if (nv == 0 && (h->dbl || (h->mixed && n3 > kMixedEigMax))) {
+    if (nv == 0 && (h->dbl || (h->mixed && n3 > h->mixw.n_cap))) {
       rc = pc_eig<RM>(h, n3, wGi, wVg, n3, h->wSig, pc_tol(h, h->gtol), true, &nv);
       if (rc) return rc;
     }
@@ -591,11 +597,13 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
                         0.1 * h->htol, true, &nv);
       if (rc) return rc;
     }
-    if (nv == 0 && (h->dbl || (h->mixed && n9 > kMixedEigMax))) {
+    if (nv == 0 && (h->dbl || (h->mixed && n9 > h->mixw.n_cap))) {
       rc = pc_eig<RM>(h, n9, wH, wU, n9, h->wLam, pc_tol(h, h->htol), true, &nv);
       if (rc) return rc;
     }
-    if (nv == 0) CK(peig<RM>(h, n9, wH, n9, wU, n9, h->wLam, 0.1 * h->htol));
+    // at most chi pairs are kept: the (chi+1)-th decides nothing more (the discarded weight
+    // comes from tr H)
+    if (nv == 0) CK(peig<RM>(h, n9, wH, n9, wU, n9, h->wLam, 0.1 * h->htol, chi + 1));
   }
   PO(bond_select<RM>(st, n9, h->wLam, wH, n9, h->htol, chi, h->dsc, h->dstats));
   rc = read_scalars(h);
@@ -660,7 +668,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
     if (rc) return rc;
     // a9: cut + PPT (FP64 scalars); tr(B^+B) = tr(B B^+)
     PO(kraus_select<RM>(st, nv, h->wWv, wWK, nc, h->kcut, kmax, use_ppt, h->wF, h->dsc,
-                        h->dstats));
+                        h->dstats, h->dtrace));
     rc = read_scalars(h);
     if (rc) return rc;
     kk = h->hsc->kkeep;
@@ -673,7 +681,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
     if (rc) return rc;
     // a9: cut + PPT (FP64 scalars)
     PO(kraus_select<RM>(st, nv, h->wWv, wWK, KM, h->kcut, kmax, use_ppt, h->wF, h->dsc,
-                        h->dstats));
+                        h->dstats, h->dtrace));
     rc = read_scalars(h);
     if (rc) return rc;
     kk = h->hsc->kkeep;
@@ -1001,6 +1009,11 @@ int init_state(mpdo_ctx* h, const double* v) {
   h->rev = false;
   h->centre = 0;
   CK(cudaMemsetAsync(h->dsc, 0, sizeof(StepScalars), h->st));
+  // tr rho of the product state: |v|^(2N)
+  h->htrace0 = std::pow(v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3] + v[4] * v[4] +
+                            v[5] * v[5],
+                        (double)h->n);
+  CK(cudaMemcpyAsync(h->dtrace, &h->htrace0, sizeof(double), cudaMemcpyHostToDevice, h->st));
   if (h->dbl)
     CK(product_state<double>(h->st, v, static_cast<double2*>(h->sites), (long)h->site_cap, h->n));
   else
@@ -1029,13 +1042,13 @@ cudaError_t penv(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<do
 // (FP32 site tensors are read and widened in the GEMMs): an FP32 transfer chain loses
 // ~1e-5 of the trace over 100 sites.
 template <typename R>
-int energy(mpdo_ctx* h, double J, double hx, double bz, double out[6]) {
+int energy(mpdo_ctx* h, double J, double hx, double bz, double out[7]) {
   using T = cx<R>;
   using TD = cx<double>;
   cudaStream_t st = h->st;
   const long chi = h->chi, K = h->kmax;
   const long env = chi * chi, fsz = chi * 3 * K * chi;
-  size_t need = (2 * 6 * env + 2 * 6 * fsz) * sizeof(TD) + 512;
+  size_t need = (2 * 6 * env + 2 * 6 * fsz) * sizeof(TD) + 1024;
   if (h->obs_bytes < need) {
     if (h->obs) {
       CK(cudaStreamSynchronize(st));
@@ -1070,9 +1083,13 @@ int energy(mpdo_ctx* h, double J, double hx, double bz, double out[6]) {
   TD res[6];
   for (int a = 0; a < 6; ++a)
     CK(cudaMemcpyAsync(&res[a], ebuf[cur] + a * env, sizeof(TD), cudaMemcpyDeviceToHost, st));
+  // the trace carried in FP64 by the updates (the norm the truncations keep)
+  double cnorm = 0;
+  CK(cudaMemcpyAsync(&cnorm, h->dtrace, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(sync_stream(h));
   prof_drain(h);
   for (int a = 0; a < 6; ++a) out[a] = res[a].x;
+  out[6] = cnorm;
   return MPDO_OK;
 }
 
@@ -1276,16 +1293,17 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
     return fail(nullptr, MPDO_ERR_OOM, "pinned host allocation");
   }
   if (h->mixed) {
-    // the mixed solver only ever sees n <= kMixedEigMax (peig routes larger problems to
-    // the FP64 solvers), so its workspace is sized for that
-    const int mcap = std::min(ncap, kMixedEigMax);
+    // the mixed solver serves every Gram of the update (bond H up to 9 chi, inner W up to
+    // m_max k_max), so its workspace is sized for the largest
+    const int mcap = ncap;
     if ((rc = alloc_dev(hp, &h->mixmem, mix_work_bytes(mcap)))) return rc;
     mix_work_bind(h->mixw, h->mixmem, mcap);
     // MPDO_NO_GRAPHS=1: launch the mixed eigensolver's levels directly (no CUDA graphs)
     const char* ng = std::getenv("MPDO_NO_GRAPHS");
     if (ng && ng[0] == '1') h->mixw.use_graphs = false;
   }
-  if ((rc = alloc_dev(hp, (void**)&h->dsc, sizeof(StepScalars))) ||
+  if ((rc = alloc_dev(hp, (void**)&h->dtrace, sizeof(double))) ||
+      (rc = alloc_dev(hp, (void**)&h->dsc, sizeof(StepScalars))) ||
       (rc = alloc_dev(hp, (void**)&h->dstats, sizeof(DevStats))))
     return rc;
   if (cudaMallocHost((void**)&h->hsc, sizeof(StepScalars)) != cudaSuccess ||
@@ -1383,15 +1401,21 @@ int mpdo_truncate(mpdo_t h, int chi_max, int k_max, int use_ppt, mpdo_trunc_stat
 int mpdo_expect_energy(mpdo_t h, double J, double hx, double b, double* e_raw, double* e_success,
                        double* success_prob, double* trace) {
   if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
-  double r[6];
+  double r[7];
   int rc = h->dbl ? energy<double>(h, J, hx, b, r) : energy<float>(h, J, hx, b, r);
   if (rc) return rc;
-  // r: [0] tr(Pi rho) [2] tr(Pi H Pi rho) [3] tr(rho) [5] tr(H rho)
+  // r: [0] tr(Pi rho) [2] tr(Pi H Pi rho) [3] tr(rho) [5] tr(H rho) [6] carried trace
   if (!(r[3] > 0) || !std::isfinite(r[3])) return fail(h, MPDO_ERR_NUMERIC, "zero trace");
+  // The contracted trace of FP32-stored sites differs from the state's trace by the rounding
+  // of the stored isometries (~1e-7 per site); the trace the updates keep is carried in FP64
+  // (kraus_select), so the unnormalised outputs are rescaled to it.  The energies are
+  // ratios of contractions and need no rescale.
+  const double tr = r[6];
+  if (!(tr > 0) || !std::isfinite(tr)) return fail(h, MPDO_ERR_NUMERIC, "zero trace");
   if (e_raw) *e_raw = r[5] / r[3];
   if (e_success) *e_success = r[0] > 0 ? r[2] / r[0] : NAN;
-  if (success_prob) *success_prob = r[0];
-  if (trace) *trace = r[3];
+  if (success_prob) *success_prob = r[0] / r[3] * tr;
+  if (trace) *trace = tr;
   return MPDO_OK;
 }
 

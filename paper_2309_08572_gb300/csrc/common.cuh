@@ -57,6 +57,7 @@ struct StepScalars {
   double theta;    // PPT angle
   int infeasible;
   int clamped;
+  double trpre;    // ||theta||^2 of the two-site block before the channel (FP64)
 };
 
 // Device-side accumulation of the per-call truncation statistics.

@@ -409,7 +409,7 @@ cudaError_t enqueue_level(cudaStream_t st, int n, int m, int level, const double
 
 cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, double2* v, long ldv,
                        double* w, double floor, MixWork& wk, int* levels_out,
-                       double* flops_out) {
+                       double* flops_out, int max_vals) {
   double flops = 0.0;
   if (n <= 0) return cudaSuccess;
   if (n > wk.n_cap) return cudaErrorInvalidValue;
@@ -473,6 +473,14 @@ cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, doubl
     const int nl = (int)hscan[1];
     // the device decided (scan[6]); the bounds below only guard the host loop
     if (hscan[6] != 0.0 || nl <= 0 || nl >= m || level + 1 >= kMaxLevels) break;
+    // enough leading pairs resolved for the caller: the rest is reported as zero
+    const int resolved = n - m + nl;
+    if (max_vals > 0 && resolved >= max_vals) {
+      MPDO_CUDA_TRY(cudaMemset2DAsync(v + resolved, ldv * sizeof(double2), 0,
+                                      (size_t)(n - resolved) * sizeof(double2), n, st));
+      MPDO_CUDA_TRY(cudaMemsetAsync(w + resolved, 0, (size_t)(n - resolved) * sizeof(double), st));
+      break;
+    }
     m -= nl;
   }
   if (levels_out) *levels_out = level + 1;

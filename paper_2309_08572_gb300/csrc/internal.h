@@ -89,8 +89,10 @@ void mix_work_release(MixWork& w);
 // down to floor * lambda_max: FP32 Jacobi levels with FP64 refinement.  Synchronises the
 // stream once per level.
 // *flops_out (may be NULL): executed flops (FP32 rotations plus FP64 products).
+// max_vals > 0: stop after the level at which at least max_vals leading pairs are resolved;
+// the remaining eigenvalues and eigenvector columns are written as zeros.
 cudaError_t heig_mixed(cudaStream_t st, int n, const double2* a, long lda, double2* v, long ldv,
                        double* w, double floor, MixWork& wk, int* levels_out,
-                       double* flops_out = nullptr);
+                       double* flops_out = nullptr, int max_vals = 0);
 
 }  // namespace mpdo

@@ -235,7 +235,28 @@ __global__ void make_q_kernel(int dm, int keep, int m_ops, const cx<R>* __restri
 template <typename R>
 __global__ void kraus_select_kernel(int n, const double* __restrict__ w, const cx<R>* __restrict__ wm,
                                     int ntr, double kcut, int kmax, int use_ppt, double* f,
-                                    StepScalars* sc, DevStats* st) {
+                                    StepScalars* sc, DevStats* st, double* trace) {
+  // total weight tr W and sum of squared weights ||W||_F^2 (= sum w^2 for the Hermitian W,
+  // whatever part of its spectrum was resolved), from the matrix in FP64
+  __shared__ double red_t[256], red_f[256];
+  {
+    double t = 0, f2 = 0;
+    for (long e = threadIdx.x; e < (long)ntr * ntr; e += blockDim.x) {
+      const cx<R> v = wm[e];
+      f2 += (double)v.x * v.x + (double)v.y * v.y;
+      if (e / ntr == e % ntr) t += (double)v.x;
+    }
+    red_t[threadIdx.x] = t;
+    red_f[threadIdx.x] = f2;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        red_t[threadIdx.x] += red_t[threadIdx.x + s];
+        red_f[threadIdx.x] += red_f[threadIdx.x + s];
+      }
+      __syncthreads();
+    }
+  }
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double w0 = w[0] > 0 ? w[0] : 0.0;
   bool bad = !(w0 > 0.0) || !isfinite(w0);
@@ -245,12 +266,20 @@ __global__ void kraus_select_kernel(int n, const double* __restrict__ w, const c
     while (kk < n && kk < kmax && w[kk] > thr) ++kk;
   }
   if (kk < 1) kk = 1;
-  double sum = 0, sq = 0, sumk = 0, sqk = 0;
-  for (int i = 0; i < ntr; ++i) sum += (double)wm[(long)i * ntr + i].x;   // trace = total weight
-  for (int i = 0; i < n; ++i) {
+  double sum = red_t[0], sq = red_f[0], sumk = 0, sqk = 0;
+  for (int i = 0; i < kk; ++i) {
     double v = w[i] > 0 ? w[i] : 0.0;
-    sq += v * v;
-    if (i < kk) { sumk += v; sqk += v * v; }
+    sumk += v;
+    sqk += v * v;
+  }
+  // The trace the truncation keeps (reading A2) is carried in FP64 across updates: the
+  // channel multiplies it by tr(theta')/tr(theta) of this block (bond total sc->tot over
+  // sc->trpre, both FP64 sums of the same stored tensors), so rounding of the stored
+  // tensors and of the products that form the new centre does not accumulate in the norm.
+  double target = sum;
+  if (trace && sc->trpre > 0 && sc->tot > 0 && isfinite(*trace)) {
+    target = *trace * (sc->tot / sc->trpre);
+    *trace = target;
   }
 
   double theta = 0.0;
@@ -274,10 +303,10 @@ __global__ void kraus_select_kernel(int n, const double* __restrict__ w, const c
       lt[i] = v;
       lsum += v;
     }
-    double sc_tr = (lsum > 0) ? sum / lsum : 0.0;
+    double sc_tr = (lsum > 0) ? target / lsum : 0.0;
     for (int i = 0; i < kk; ++i) lt[i] *= sc_tr;
   } else {
-    double sc_tr = (sumk > 0) ? sum / sumk : 0.0;
+    double sc_tr = (sumk > 0) ? target / sumk : 0.0;
     for (int i = 0; i < kk; ++i) lt[i] = (w[i] > 0 ? w[i] : 0.0) * sc_tr;
   }
   for (int i = 0; i < kk; ++i) {
@@ -295,6 +324,55 @@ __global__ void kraus_select_kernel(int n, const double* __restrict__ w, const c
   st->ppt_infeasible += infeas;
   st->ppt_clamped += clamped;
   if (kk > st->k_used_max) st->k_used_max = kk;
+}
+
+// ||theta||^2 of the two-site block before the channel, from the two Gram matrices:
+// sum_{s,b,b'} G_i[(s,b'),(s,b)] sum_t G_j[(b,t),(b',t)]  (G_i, G_j: 3D x 3D, index s*D+b
+// resp. b*3+t), accumulated in FP64 into sc->trpre.  One CTA.
+template <typename R>
+__global__ void trace_pre_kernel(int dm, const cx<R>* __restrict__ gi, const cx<R>* __restrict__ gj,
+                                 StepScalars* sc) {
+  __shared__ double red[256];
+  const long n3 = 3L * dm;
+  double t = 0;
+  for (long e = threadIdx.x; e < (long)dm * dm; e += blockDim.x) {
+    const int b = (int)(e / dm), bp = (int)(e % dm);
+    double gtr = 0, gti = 0;
+    for (int q = 0; q < 3; ++q) {
+      const cx<R> v = gj[(long)(b * 3 + q) * n3 + bp * 3 + q];
+      gtr += (double)v.x;
+      gti += (double)v.y;
+    }
+    for (int s = 0; s < 3; ++s) {
+      const cx<R> v = gi[(long)(s * dm + bp) * n3 + s * dm + b];
+      t += (double)v.x * gtr - (double)v.y * gti;
+    }
+  }
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sc->trpre = red[0];
+}
+
+// out = sum |a_e|^2 over n complex entries, in FP64 (one CTA; the norm of the centre site).
+template <typename R>
+__global__ void sumsq_kernel(long n, const cx<R>* __restrict__ a, double* out) {
+  __shared__ double red[256];
+  double t = 0;
+  for (long e = threadIdx.x; e < n; e += blockDim.x) {
+    const cx<R> v = a[e];
+    t += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
 }
 
 // Vks[kappa][k] = V[kappa][k] * f[k], k < kk (V has leading dimension ldv)
@@ -691,9 +769,22 @@ cudaError_t make_q(cudaStream_t st, int dm, int keep, int m_ops, const cx<R>* w,
 template <typename R>
 cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, int ntr,
                          double kcut, int kmax, int use_ppt, double* f, StepScalars* sc,
-                         DevStats* ds) {
+                         DevStats* ds, double* trace) {
   count_launch();
-  kraus_select_kernel<R><<<1, 32, 0, st>>>(n, w, wm, ntr, kcut, kmax, use_ppt, f, sc, ds);
+  kraus_select_kernel<R><<<1, 256, 0, st>>>(n, w, wm, ntr, kcut, kmax, use_ppt, f, sc, ds,
+                                            trace);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t trace_pre(cudaStream_t st, int dm, const cx<R>* gi, const cx<R>* gj, StepScalars* sc) {
+  count_launch();
+  trace_pre_kernel<R><<<1, 256, 0, st>>>(dm, gi, gj, sc);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t sumsq(cudaStream_t st, long n, const cx<R>* a, double* out) {
+  count_launch();
+  sumsq_kernel<R><<<1, 256, 0, st>>>(n, a, out);
   return cudaGetLastError();
 }
 template <typename R, typename RO>
@@ -790,8 +881,12 @@ template cudaError_t lift<float>(cudaStream_t, int, const float2*, const double*
   template cudaError_t bond_select<R>(cudaStream_t, int, const double*, const cx<R>*, long,  \
                                       double, int, StepScalars*, DevStats*);                 \
   template cudaError_t kraus_select<R>(cudaStream_t, int, const double*, const cx<R>*, int,   \
-                                       double, int, int, double*, StepScalars*, DevStats*);  \
+                                       double, int, int, double*, StepScalars*, DevStats*,   \
+                                       double*);                                             \
+  template cudaError_t trace_pre<R>(cudaStream_t, int, const cx<R>*, const cx<R>*,           \
+                                    StepScalars*);                                           \
   template cudaError_t polar_factors<R>(cudaStream_t, int, const cx<R>*, cx<R>*, cx<R>*);   \
+  template cudaError_t sumsq<R>(cudaStream_t, long, const cx<R>*, double*);                 \
   template cudaError_t sample_pick<R>(cudaStream_t, int, int, const cx<R>*, const cx<R>*,   \
                                       uint64_t, int, int, int, cx<R>*, uint8_t*, double*, int);
 INST(double)

@@ -37,10 +37,15 @@ cudaError_t dual_rows(cudaStream_t st, int kk, int cols, const cx<R>* y, long ld
 template <typename R>
 cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<R>* qm);
 // n eigenvalues w (descending); the total weight is the trace of wm (ntr x ntr)
+// trace (device FP64, may be NULL): the carried trace of the state, multiplied by the
+// block's tr(theta')/tr(theta) = sc->tot / sc->trpre; the kept weights are rescaled to it.
 template <typename R>
 cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, int ntr,
                          double kcut, int kmax, int use_ppt, double* f, StepScalars* sc,
-                         DevStats* ds);
+                         DevStats* ds, double* trace);
+// sc->trpre = ||theta||^2 of the block from its Gram matrices G_i, G_j (3 dm x 3 dm)
+template <typename R>
+cudaError_t trace_pre(cudaStream_t st, int dm, const cx<R>* gi, const cx<R>* gj, StepScalars* sc);
 // Pivoted Cholesky W ~ L L^+ of a Hermitian PSD matrix (n <= 1024, rmax <= 128); device
 // outputs: L (n x r, row stride lr), *rout = r, *resid = remaining diag max / tr W.
 template <typename R>
@@ -49,6 +54,9 @@ cudaError_t pchol(cudaStream_t st, int n, const cx<R>* w, int rmax, double tol, 
 // zs = z diag(s^-1/2) (r x r)
 template <typename R>
 cudaError_t lift(cudaStream_t st, int r, const cx<R>* z, const double* s, cx<R>* zs);
+// out (device double) = sum of |a|^2 over n complex entries, accumulated in FP64
+template <typename R>
+cudaError_t sumsq(cudaStream_t st, long n, const cx<R>* a, double* out);
 template <typename R, typename RO>
 cudaError_t scale_vk(cudaStream_t st, int n, int kk, const cx<R>* v, long ldv, const double* f,
                      cx<RO>* out);
