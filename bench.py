@@ -3,20 +3,25 @@
 
 Workload ("chain100"): N = 100 three-level atoms, QAOA p = 3 on the TFIM (J = h = 1),
 chi = 256, K = 16, Rydberg decay 0.005 and dephasing 0.005 per block, crosstalk phase
-0.01 rad, post-promotion 0.01 rad, seeded angles (seed 3).  One step = one full circuit:
-reset to |+>^N, the 3 layers (297 two-site updates: Gram contractions, Jacobi
-eigensolves, split, Kraus truncation with PPT) and the TFIM energy / success probability.
-One step runs a batch of such circuits (--batch, default 32, seeded angle draws)
-concurrently through the library's batch executor (one CUDA stream and host thread per
-circuit in flight); the single-circuit latency is reported beside it.
+0.01 rad, post-promotion 0.01 rad, seeded angles (seed 3).  One circuit = reset to |+>^N,
+the 3 layers (297 two-site updates: Gram contractions, eigensolves, split, Kraus truncation
+with PPT) and the TFIM energy / success probability.  The bond cut is reading A4's for the
+reduced-precision modes, s > 1e-7 s_max, applied at each mode's numerical floor (mixed form:
+lambda = s^2 > 1e-13 lambda_max, i.e. s > 3.2e-7 s_max); at that cut three layers take the bond
+dimension to D = 33, which the line reports (chi_used_max, mean D).  "chain100deep" runs the
+same chain with p = 8 layers, where D reaches chi = 256.
+One step runs a batch of circuits (--batch, default 32, seeded angle draws) concurrently
+through the library's batch executor (one CUDA stream and host thread per circuit in flight).
 
 value  = two-site updates per second, whole job (all ranks), device-resident inputs.
-e2e    = the same metric through the host-buffer API (mpdo_batch_run_host: every step
-         each worker converts its circuit's ops, copies them from pinned host memory and
-         runs them; energies read back), wall clock.
-Also reported: QAOA energy evaluations per second, the roofline of the dominant kernel
-class, the CPU oracle on a bounded sample (cpu_baseline), SM clocks during the timed
-region, and the kernel launch count.
+e2e    = the same metric through the host-buffer API (mpdo_batch_run_host: every step each
+         worker converts its circuit's ops, copies them from pinned host memory and runs
+         them; energies read back), wall clock.
+Also reported: QAOA energy evaluations per second; the plain FP64 form on the same circuits
+(single circuit and batched) and the error of every energy and probability against the
+CPU oracle; the GPU-wide roofline of the dominant kernel class against peaks measured on this
+GPU; the oracle on a bounded sample (cpu_baseline); SM clocks during the timed region; the
+kernel launch counts.
 
 Multi-GPU: one circuit does not shard (the bond sweep is sequential), so --gpus N runs N
 independent replicas (weak scaling), launched with torchrun.
@@ -54,7 +59,23 @@ PULSE_STEPS = 2000     # integration steps of the G1 pulse channel
 
 
 def workload():
-    return synth.chain40() if WORKLOAD == "chain40" else synth.chain100()
+    return {"chain40": synth.chain40, "chain100": synth.chain100,
+            "chain100deep": synth.chain100deep}[WORKLOAD]()
+
+
+# Product engines and Gram precision of each --prec form: (library precision, FP64 Grams).
+FORMS = {"mixed": ("c64", True), "mixed-tc": ("tf32x3", True), "c64": ("c64", False),
+         "tf32x3": ("tf32x3", False), "bf16x3": ("bf16x3", False), "fp64": ("fp64", False)}
+# Relative rounding of one Gram entry of each form (the library's numerical floor of the
+# cuts is lambda > 10 eps lambda_max).
+FORM_EPS = {"mixed": 1e-14, "mixed-tc": 1e-14, "c64": 6e-8, "tf32x3": 2.4e-7, "bf16x3": 1.5e-5,
+            "fp64": 1e-16}
+
+
+def effective_cut(prec: str, sv: float) -> float:
+    """The bond cut the library applies for a requested s > sv s_max: lambda = s^2 above
+    max(sv^2, 10 eps) lambda_max, i.e. s > max(sv, sqrt(10 eps)) s_max."""
+    return max(sv, float(np.sqrt(10.0 * FORM_EPS[prec])))
 
 
 _CZ_CACHE = {}
@@ -87,21 +108,31 @@ def oracle_layer_ops(c, k):
 
 PREC_DESC = {
     "mixed": "mixed: complex64 site tensors and large contractions (FP32), Gram matrices with "
-             "FP64 products and sums, FP32 Jacobi sweeps with FP64 refinement, FP64 cuts, PPT "
-             "and observables",
+             "FP64 products and sums, FP32 Jacobi sweeps with FP64 refinement, FP64 cuts, PPT, "
+             "trace and observables",
+    "mixed-tc": "mixed with the FP32 contractions (new centre, inner isometry) on the tensor "
+                "cores in TF32x3 split precision (tcgen05, FP32 accumulation); FP64 Grams",
     "c64": "complex64 throughout (FP32 Grams and Jacobi), FP64 scalars and observables",
+    "tf32x3": "complex64 with every large product (Grams included) on the tensor cores in "
+              "TF32x3 split precision (tcgen05, FP32 accumulation), FP32 Jacobi",
+    "bf16x3": "complex64 with every large product on the tensor cores in BF16x3 split "
+              "precision (tcgen05, FP32 accumulation), FP32 Jacobi",
     "fp64": "complex128 throughout",
 }
 
 
 def workload_desc(c, prec, sv):
+    eff = effective_cut(prec, sv)
     return {"workload": f"{WORKLOAD}: N={c.n_sites} atoms (d=3), QAOA p={c.p}, chi={c.chi_max}, "
                         f"K={c.k_max}, decay {c.gamma_diss}, dephasing {c.gamma_deph}, "
                         f"crosstalk {c.xtalk_phase} rad, "
                         + (f"post-promotion {c.delta_pp} rad, " if GATE_MODEL == "g0" else "")
-                        + f"TFIM J={c.J} h={c.hx}, seed {c.seed}",
+                        + f"TFIM J={c.J} h={c.hx}, seed {c.seed}; bond cut s > {eff:.2g} s_max "
+                        f"(reading A4: {sv:g} requested, the form's floor sqrt(10 eps) applied)",
             "updates_per_circuit": c.p * (c.n_sites - 1),
-            "precision": PREC_DESC[prec], "bond_cut": f"s > {sv:g} s_max" if sv else "numerical floor",
+            "precision": PREC_DESC[prec],
+            "bond_cut": f"s > {eff:.3g} s_max (requested {sv:g}; floor of the form "
+                        f"{np.sqrt(10 * FORM_EPS[prec]):.2g})",
             "parallelism": "replicas",
             "gate_model": ("G0 (gate level)" if GATE_MODEL == "g0" else
                            f"G1 (Gaussian-pulse CZ of Fig. 1, rates per pulse, {PULSE_STEPS} "
@@ -111,18 +142,18 @@ def workload_desc(c, prec, sv):
 
 # --------------------------------------------------------------------- CPU oracle
 def bond_cut(args):
-    """The bond cut of the timed configuration (s > cut * s_max; 0 = numerical floor)."""
+    """The requested bond cut s > cut * s_max: reading A4 (1e-7 for the reduced-precision
+    forms, 1e-14 for FP64) unless --sv-cutoff is given."""
     if args.sv_cutoff is not None:
         return args.sv_cutoff
-    return 0.0 if args.prec == "c64" else 1e-4
+    return 1e-14 if args.prec == "fp64" else 1e-7
 
 
 def oracle_sample(c, budget_s: float, n_steps: int = 0, sv: float = 0.0):
     """Time the oracle on the workload: layers 1..p-1 in full, then layer-p updates (the
     expensive ones) up to budget_s (or n_steps of them); extrapolate one full circuit."""
     from oracle import mpdo as ompdo, qaoa as oqaoa
-    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max,
-                   sv_cutoff=sv if sv > 0 else 1e-14)
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max, sv_cutoff=sv)
     layer_t = []
     for k in range(c.p - 1):
         t0 = time.perf_counter()
@@ -162,9 +193,9 @@ def run_reference(args):
         return 0
     from oracle import mpdo as ompdo, qaoa as oqaoa
     sv = bond_cut(args)
+    eff = effective_cut(args.prec, sv)
     t0 = time.perf_counter()
-    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max,
-                   sv_cutoff=sv if sv > 0 else 1e-14)
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max, sv_cutoff=eff)
     layer_t = []
     for k in range(c.p - 1):
         t1 = time.perf_counter()
@@ -188,7 +219,8 @@ def run_reference(args):
             "ms_per_step": 1e3 * statistics.mean(per), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_desc(c, args.prec, sv),
-            "oracle": "complex128 NumPy oracle on the host cores, same bond cut",
+            "oracle": f"complex128 NumPy oracle on the host cores, same bond cut (s > {eff:.3g} "
+                      f"s_max)",
             "energy_evals_per_s": 1.0 / t_circ,
             "cpu_baseline": {"value": ups, "unit": "site-updates/s", "cores": cpu_cores(),
                              "kind": "oracle", "sample": sample},
@@ -303,20 +335,106 @@ def batch_circuits(c, batch):
     return out
 
 
+def measure_peaks(torch):
+    """Dense GEMM throughput of this GPU per arithmetic, as roofline denominators (cuBLAS
+    through torch.matmul, CUDA events, best of 5 after 2 warm-ups): FP64 (4096^3), FP32 on
+    the CUDA cores (TF32 off, 8192^3) and TF32 (8192^3); 2 n^3 flops each."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, tf32, n in (("fp64", torch.float64, False, 4096),
+                                  ("fp32", torch.float32, False, 8192),
+                                  ("tf32", torch.float32, True, 8192)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device="cuda", dtype=dt)
+            b = torch.randn(n, n, device="cuda", dtype=dt)
+            for _ in range(2):
+                torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
+
+
+def oracle_results(circs, sv, n_max):
+    """The CPU oracle's observables for the first n_max circuits at bond cut sv."""
+    from oracle import mpdo as ompdo, observables as oobs, qaoa as oqaoa
+    out = []
+    for c in circs[:n_max]:
+        m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), c.chi_max, c.k_max, sv_cutoff=sv)
+        for k in range(c.p):
+            for i, kr in oracle_layer_ops(c, k):
+                m.apply_two_site(i, kr)
+        out.append(oobs.expect_energy(m, c.J, c.hx, c.bz))
+    return out
+
+
+KEYS = ("e_raw", "e_succ", "p_succ", "trace")
+
+
+def rel_errors(res_rows, refs):
+    """max over circuits of |gpu - oracle| / |oracle|, per observable."""
+    errs = {}
+    for j, key in enumerate(KEYS):
+        errs[key] = max(abs(row[j] - r[key]) / abs(r[key]) for row, r in zip(res_rows, refs))
+    return errs
+
+
+def single_circuit(lib, g, dls, circ):
+    """One circuit on handle g, layer by layer (untimed detail): truncation statistics,
+    the bond dimensions reached and the result."""
+    import torch
+    g.reconfigure(circ.n_sites, circ.chi_max, circ.k_max)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    chi_max = k_max = 0
+    for dl in dls:
+        st = g.apply_uploaded(dl)
+        chi_max = max(chi_max, st["chi_used_max"])
+        k_max = max(k_max, st["k_used_max"])
+    e = g.expect_energy(circ.J, circ.hx, circ.bz)
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0)
+    b, kd, _ = g.dims()
+    return {"ms": ms, "chi_used_max": int(chi_max), "k_used_max": int(k_max),
+            "mean_bond_dim_final": float(np.mean(b)), "max_bond_dim_final": int(np.max(b)),
+            "result": {k: float(e[k]) for k in KEYS}}
+
+
 def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     c = workload()
+    prec = args.prec
+    sv = bond_cut(args)
+    eff = effective_cut(prec, sv)
+    circs = batch_circuits(c, args.batch)
     cpu = None
+    refs = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        layer_t, per, n_last = oracle_sample(c, args.cpu_budget, sv=bond_cut(args))
+        layer_t, per, n_last = oracle_sample(c, args.cpu_budget, sv=eff)
         t_circ = oracle_rate(layer_t, per, n_last)
         ups = c.p * (c.n_sites - 1) / t_circ
         cpu = {"value": ups, "unit": "site-updates/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": (f"{WORKLOAD} oracle: layers 1..{c.p - 1} in full ({sum(layer_t):.1f} s) "
-                          f"+ {len(per)} layer-{c.p} updates (mean {statistics.mean(per):.2f} s); "
-                          f"circuit time extrapolated as layers + {n_last} x mean = {t_circ:.0f} s")}
+               "sample": (f"{WORKLOAD} oracle at the same cut (s > {eff:.3g} s_max): layers "
+                          f"1..{c.p - 1} in full ({sum(layer_t):.1f} s) + {len(per)} layer-{c.p} "
+                          f"updates (mean {statistics.mean(per):.2f} s); circuit time "
+                          f"extrapolated as layers + {n_last} x mean = {t_circ:.0f} s")}
+    if rank == 0 and world == 1 and args.oracle_check > 0:
+        # the oracle's observables of the first circuits, for the error of every output
+        refs = oracle_results(circs, eff, args.oracle_check)
 
     import torch
     torch.cuda.set_device(local)
@@ -326,21 +444,17 @@ def run_ours(args):
         dist.init_process_group("nccl")
     import paper_2309_08572_gb300 as lib
 
-    prec = args.prec
-    sv = bond_cut(args)
-    circs = batch_circuits(c, args.batch)
+    lprec, gram = FORMS[prec]
     host_layers = [lib_layers(lib, ci) for ci in circs]
     m_max = max(k.shape[0] for L in host_layers for layer in L for _, k in layer)
-    lprec = "fp64" if prec == "fp64" else "c64"
     pool = [lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec=lprec, own_stream=True,
-                     gram_fp64=(prec == "mixed"), sv_cutoff=sv)
+                     gram_fp64=gram, sv_cutoff=sv)
             for _ in range(args.batch)]
     dls = [[pool[0].upload_layer(layer) for layer in L] for L in host_layers]
     descs = [dict(n_sites=ci.n_sites, chi_max=ci.chi_max, k_max=ci.k_max, layers=d, J=ci.J,
                   hx=ci.hx, b=ci.bz) for ci, d in zip(circs, dls)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     updates = c.p * (c.n_sites - 1)
-    # GEMM tile shapes picked by the library's autotuner (untimed)
     tuned = [lib.autotune_gemm(pr, reps=3) for pr in (0, 1)] if args.autotune else None
 
     def step():
@@ -350,31 +464,29 @@ def run_ours(args):
         res = step()
     torch.cuda.synchronize()
 
-    # single-circuit latency and kernel-class breakdown (one profiled circuit, untimed)
+    # single-circuit latency, bond dimensions reached and kernel-class breakdown (untimed)
     g = pool[0]
     g.profile(7)
-    t0 = time.perf_counter()
-    single = lib.batch_run([g], descs[:1])
-    single_ms = 1e3 * (time.perf_counter() - t0)
+    single = single_circuit(lib, g, dls[0], circs[0])
     prof = [g.profile_read(k) for k in range(3)]
     g.profile(0)
-    dom = max(range(3), key=lambda k: prof[k]["ms"])
-    names = {0: "complex GEMM (cgemm_kernel)",
-             1: "eigensolver (jacobi_smem_kernel sweeps; mixed mode: FP32 sweeps + FP64 "
-                "refinement products)",
-             2: "other kernels"}
+    names = {0: "complex GEMMs (cgemm_kernel, cgemm_small_kernel, FP64-product cgemm_wide; "
+                "tc_gemm_kernel for the tensor-core forms)",
+             1: "eigensolvers (pchol_kernel, osj_kernel, jacobi_smem_kernel / jacobi_coop_kernel "
+                "FP32 sweeps, FP64 refinement sg_refine_kernel, level_out_kernel)",
+             2: "other kernels (selection, PPT, phi, layout)"}
 
-    # timed region: K steps (each a batch of circuits run concurrently), events around
-    # each step on the current stream after a device-wide synchronisation; L2 flushed
-    # between steps outside the events
+    # timed region: K steps (each a batch of circuits run concurrently); events around each
+    # step on the current stream after a device-wide synchronisation; L2 flushed between steps
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     for m in pool:
-        m.profile(1 << dom)
+        m.profile(3)
     launches0 = lib.kernel_launches()
+    tc0 = lib.tc_gemm_launches()
     times = []
     for _ in range(args.steps):
         flush.zero_()
@@ -388,27 +500,28 @@ def run_ours(args):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     launches = lib.kernel_launches() - launches0
-    dprofs = [m.profile_read(dom) for m in pool]
+    tc_launches = lib.tc_gemm_launches() - tc0
+    cls = [{k: sum(m.profile_read(q)[k] for m in pool) for k in ("ms", "launches", "flops")}
+           for q in (0, 1)]
     for m in pool:
         m.profile(0)
-    dprof = {k: sum(d[k] for d in dprofs) for k in ("ms", "launches", "flops")}
     ck = clocks.stop()
     total_ms = max_over_ranks(sum(times), dist)
+    ms_step = total_ms / args.steps
     value = job_throughput(world, args.steps, args.batch * updates, total_ms)
 
     # end to end through the host-buffer API: every step uploads each circuit's ops from
     # host memory, runs the batch and reads the energies back
-    h2d = sum(layer_bytes(L, 16 if prec == "fp64" else 8) for L in host_layers)
-    if prec == "mixed":   # the channel partial traces travel in FP64
-        h2d = sum(sum((2 * k.shape[0] * 81 * 8 + 2 * 729 * 16) for _, k in layer)
-                  for L in host_layers for layer in L)
+    elt = 16 if prec == "fp64" else 8
+    gelt = 16 if (prec == "fp64" or gram) else 8   # channel partial traces: Gram precision
+    h2d = sum(sum((2 * k.shape[0] * 81 * elt + 2 * 729 * gelt) for _, k in layer)
+              for L in host_layers for layer in L)
     d2h = args.batch * (4 * 8 + updates * 2 * STEP_SCALARS_BYTES + c.p * DEV_STATS_BYTES)
-    # the circuits' ops in host memory, in the C ABI's layout (marshalled once, untimed)
     hosts = [lib.HostCircuit(ci.n_sites, ci.chi_max, ci.k_max, L, J=ci.J, hx=ci.hx, b=ci.bz)
              for ci, L in zip(circs, host_layers)]
     torch.cuda.synchronize()
     te = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, min(args.steps, 3))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -417,53 +530,75 @@ def run_ours(args):
     e2e_ms = max_over_ranks(1e3 * sum(te), dist)
     e2e_value = job_throughput(world, len(te), args.batch * updates, e2e_ms)
 
-    # roofline of the dominant class
+    # peaks of this GPU and the GPU-wide roofline of the dominant class: its flops per step
+    # (8 m n k per complex product at the actual dims; the eigensolvers' executed rotations
+    # and FP64 refinement products) over the step time
     pk = peaks()
-    smax = (ck or {}).get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
-    roof = {"kernel": names[dom],
-            "share_of_single_circuit": prof[dom]["ms"] / max(1e-9, sum(p["ms"] for p in prof)),
-            "launches_per_step": dprof["launches"] / max(1, args.steps),
-            "avg_launch_us": 1e3 * dprof["ms"] / max(1, dprof["launches"])}
-    if dom in (0, 1) and dprof["flops"] > 0:
-        achieved = dprof["flops"] / (dprof["ms"] / 1e3) / 1e12
-        peak = alu_peak_tflops(prec, smax)
-        roof.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "traffic_note": "not a per-launch constant of this class (sizes vary); one "
-                                     "ncu capture of a level solve (n=24) read 36.6 KB and "
-                                     "wrote 0 B of DRAM: the solves live in shared memory",
-                     "flops_per_launch": dprof["flops"] / max(1, dprof["launches"]),
-                     "peak_note": f"CUDA-core {'FP64' if prec == 'fp64' else 'FP32'} FMA peak from "
-                                  f"unit counts (152 SMs x {'2' if prec == 'fp64' else '128'} FMA/clk "
-                                  f"x 2) at {smax:.0f} MHz; achieved = flops per launch / mean "
-                                  f"launch duration (concurrent circuits); flops = "
-                                  + ("8 m n k per complex GEMM" if dom == 0 else
-                                     "multiply-adds executed by the Jacobi rotations")})
+    mp = measure_peaks(torch) if rank == 0 and not args.no_peaks else {}
+    dom = 0 if cls[0]["ms"] >= cls[1]["ms"] else 1
+    fl_step = cls[dom]["flops"] / args.steps
+    roof = {"kernel": names[dom], "scope": "GPU-wide: class flops per step / ms_per_step",
+            "class_ms_per_step_summed_over_streams": cls[dom]["ms"] / args.steps,
+            "launches_per_step": cls[dom]["launches"] / args.steps,
+            "share_of_single_circuit": prof[dom]["ms"] / max(1e-9, sum(q["ms"] for q in prof))}
+    if fl_step > 0 and mp:
+        achieved = fl_step / (ms_step / 1e3) / 1e12
+        if dom == 0 and prec in ("tf32x3", "bf16x3"):
+            peak, pname = mp["tf32"] if prec == "tf32x3" else pk.get("bf16_tflops_sustained", 0), \
+                "TF32 cuBLAS, measured here" if prec == "tf32x3" else "BF16 cuBLAS, sustained"
+            bound = "tensor"
+        elif prec == "fp64":
+            peak, pname, bound = mp["fp64"], "FP64 DGEMM (cuBLAS), measured here", "alu"
+        else:
+            peak, pname, bound = mp["fp32"], "FP32 SGEMM on the CUDA cores (cuBLAS, TF32 off), " \
+                                             "measured here", "alu"
+        roof.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "peak_source": pname,
+                     "traffic_note": "not a per-launch constant of this class (hundreds of shapes "
+                                     "per circuit); the ncu summaries in profiles/ give DRAM bytes "
+                                     "of the individual kernels"})
     else:
         roof.update({"bound": "latency", "achieved": None, "peak": None, "unit": None,
                      "frac": None, "traffic": None})
 
-    # the plain FP64 single-circuit form on the same circuit and cut: its time, and the
-    # error of this run's circuit 0 against it, per observable
+    # the plain FP64 form on the same circuits and cut: one circuit alone, and the batch run
+    # concurrently (handles capped at chi = 64: the cut keeps D below that, checked)
     fp64 = None
     if not args.no_fp64_compare and prec != "fp64" and rank == 0 and world == 1:
         g64 = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec="fp64", own_stream=True,
-                       sv_cutoff=sv)
+                       sv_cutoff=eff)
         dl64 = [g64.upload_layer(layer) for layer in host_layers[0]]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r64 = lib.batch_run([g64], [dict(descs[0], layers=dl64)])
-        t64 = time.perf_counter() - t0
-        ups64 = updates / t64
-        fp64 = {"ms_per_circuit": 1e3 * t64, "site_updates_per_s": ups64,
-                "factor_batched_vs_fp64_single": value / ups64,
-                "factor_single_vs_fp64_single": (1e3 * t64) / single_ms,
-                "rel_err": {k: abs(res[0][j] - r64[0][j]) / abs(r64[0][j])
-                            for j, k in enumerate(("e_raw", "e_succ", "p_succ", "trace"))},
-                "bond_cut": f"s > {sv:g} s_max" if sv else "numerical floor"}
+        s64 = single_circuit(lib, g64, dl64, circs[0])
         for dl in dl64:
             g64.free_uploaded(dl)
         g64.close()
+        fp64 = {"single_circuit": s64,
+                "site_updates_per_s_single": updates / (s64["ms"] / 1e3),
+                "factor_single_vs_fp64_single": s64["ms"] / single["ms"]}
+        if not args.no_fp64_batch and single["chi_used_max"] < 64 and s64["chi_used_max"] < 64:
+            pool64 = [lib.Mpdo(c.n_sites, 64, c.k_max, m_max=m_max, prec="fp64", own_stream=True,
+                               sv_cutoff=eff) for _ in range(args.batch)]
+            dlb = [[pool64[0].upload_layer(layer) for layer in L] for L in host_layers]
+            d64 = [dict(dd, chi_max=64, layers=d) for dd, d in zip(descs, dlb)]
+            lib.batch_run(pool64, d64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r64 = lib.batch_run(pool64, d64)
+            torch.cuda.synchronize()
+            tb = time.perf_counter() - t0
+            fp64.update({"batched_ms_per_step": 1e3 * tb,
+                         "site_updates_per_s_batched": args.batch * updates / tb,
+                         "factor_batched_vs_fp64_batched": value / (args.batch * updates / tb),
+                         "batched_pool": f"{args.batch} FP64 handles with chi cap 64 (the cut "
+                                         f"keeps D <= {s64['chi_used_max']})"})
+            for d in dlb:
+                for dl in d:
+                    pool64[0].free_uploaded(dl)
+            for m in pool64:
+                m.close()
+        fp64["factor_batched_vs_fp64_single"] = value / fp64["site_updates_per_s_single"]
+        fp64["bond_cut"] = f"s > {eff:.3g} s_max (same as the timed form)"
 
     if rank == 0:
         cfg = workload_desc(c, prec, sv)
@@ -471,22 +606,32 @@ def run_ours(args):
                              if tuned else "built-in size rules")
         cfg["batch"] = f"{args.batch} circuits per step, run concurrently (one stream each); " \
                        f"circuit 0 uses seed {c.seed}, circuit j seeded angles {c.seed}*1000+j"
+        cfg["chi_used_max"] = single["chi_used_max"]
+        cfg["k_used_max"] = single["k_used_max"]
+        cfg["mean_bond_dim"] = single["mean_bond_dim_final"]
+        errs = None
+        if refs:
+            errs = {"vs": f"CPU oracle (complex128) at the same cut, circuits 0..{len(refs) - 1} "
+                          f"of the batch, max relative error",
+                    "batched": rel_errors(np.asarray(res)[:len(refs)], refs)}
         line = {"metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"fp64": "f64", "c64": "f32", "mixed": "f32+f64"}[prec],
+                "dtype": {"fp64": "f64", "c64": "f32", "mixed": "f32+f64", "mixed-tc": "tf32x3+f64",
+                          "tf32x3": "tf32x3", "bf16x3": "bf16x3"}[prec],
                 "data": "synthetic",
                 "config": cfg,
                 "energy_evals_per_s": world * args.steps * args.batch / (total_ms / 1e3),
-                "single_circuit": {"ms": single_ms, "site_updates_per_s": updates / (single_ms / 1e3),
-                                   "result": dict(zip(("e_raw", "e_succ", "p_succ", "trace"),
-                                                      single[0].tolist()))},
+                "single_circuit": dict(single, site_updates_per_s=updates / (single["ms"] / 1e3)),
+                "error_vs_oracle": errs,
                 "roofline": roof,
+                "peaks_measured_tflops": mp,
                 "kernel_profile_single_circuit_ms": {names[k]: prof[k]["ms"] for k in range(3)},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "clocks": ck, "fp64_plain": fp64}
+                "gpu_launches": launches, "tc_gemm_launches": tc_launches, "clocks": ck,
+                "fp64_plain": fp64}
         print(json.dumps(line), flush=True)
     for d in dls:
         for dl in d:
@@ -513,9 +658,9 @@ def run_batch512(args):
     n_cap = max(ci.n_sites for ci in circs)
     chi_cap = max(ci.chi_max for ci in circs)
     k_cap = max(ci.k_max for ci in circs)
-    lprec = "fp64" if args.prec == "fp64" else "c64"
+    lprec, gram = FORMS[args.prec]
     pool = [lib.Mpdo(n_cap, chi_cap, k_cap, m_max=m_max, prec=lprec, own_stream=True,
-                     gram_fp64=(args.prec == "mixed"), sv_cutoff=sv)
+                     gram_fp64=gram, sv_cutoff=sv)
             for _ in range(args.batch)]
     dls = [[pool[0].upload_layer(layer) for layer in L] for L in host_layers]
     descs = [dict(n_sites=ci.n_sites, chi_max=ci.chi_max, k_max=ci.k_max, layers=d, J=ci.J,
@@ -556,12 +701,15 @@ def run_batch512(args):
     line = {"metric": METRIC, "value": args.steps * updates / (total_ms / 1e3),
             "unit": "site-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "c64": "f32", "mixed": "f32+f64"}[args.prec],
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "c64": "f32", "mixed": "f32+f64", "mixed-tc": "tf32x3+f64",
+                      "tf32x3": "tf32x3", "bf16x3": "bf16x3"}[args.prec],
             "data": "synthetic",
             "config": {"workload": "batch512: 512 circuits, N ~ U{20..100}, chi in {32,64,128}, "
                                    "K=8, p in {1,2}, decay/dephasing log-U[1e-4,1e-2], seed 4",
                        "updates_per_step": updates, "precision": PREC_DESC[args.prec],
-                       "bond_cut": f"s > {sv:g} s_max" if sv else "numerical floor",
+                       "bond_cut": f"s > {effective_cut(args.prec, sv):.3g} s_max (requested "
+                                   f"{sv:g})",
                        "pool": f"{args.batch} handles (one stream each) sized N=100, chi=128, K=8",
                        "gemm_tiles": (f"autotuned ({tuned[0]} FP64 and {tuned[1]} FP32 buckets)"
                                       if tuned else "built-in size rules"),
@@ -588,12 +736,23 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["mixed", "c64", "fp64"], default="mixed",
-                    help="mixed: FP32 tensors with FP64 Grams and small matrices (default)")
+    ap.add_argument("--prec", choices=list(FORMS), default="mixed",
+                    help="mixed: FP32 tensors with FP64 Grams and small matrices (default); "
+                         "mixed-tc: the same with its FP32 products on the tensor cores; "
+                         "tf32x3 / bf16x3: complex64 with all large products on the tensor "
+                         "cores; c64; fp64")
     ap.add_argument("--sv-cutoff", type=float, default=None,
-                    help="bond cut s > cutoff * s_max (default 1e-4; c64: its numerical floor)")
+                    help="bond cut s > cutoff * s_max (default: reading A4, 1e-7 for the "
+                         "reduced-precision forms, 1e-14 for fp64; each form applies its "
+                         "numerical floor on top)")
     ap.add_argument("--no-fp64-compare", action="store_true",
-                    help="skip the plain FP64 single-circuit comparison")
+                    help="skip the plain FP64 comparison (single circuit and batch)")
+    ap.add_argument("--no-fp64-batch", action="store_true",
+                    help="skip only the batched FP64 comparison")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip measuring the FP64 / FP32 / TF32 GEMM peaks")
+    ap.add_argument("--oracle-check", type=int, default=2,
+                    help="circuits of the batch whose outputs are compared with the CPU oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--autotune", action="store_true",
@@ -601,11 +760,14 @@ def main():
                          "(default: the built-in size rules, faster under concurrency)")
     ap.add_argument("--gate-model", choices=["g0", "g1"], default="g0",
                     help="g0: ideal CZ with closed-form noise per block; g1: the Gaussian-pulse "
-                         "CZ channel integrated from the Lindbladian (chain workloads)")
+                         "CZ channel integrated from the Lindbladian (chain workloads; no timed "
+                         "measurement of it exists yet)")
     ap.add_argument("--batch", type=int, default=32,
                     help="circuits per step, run concurrently by the batch executor")
-    ap.add_argument("--workload", choices=["chain100", "chain40", "batch512"], default="chain100",
-                    help="chain40 (N=40, p=2, chi=64, K=8) is the small profiling case")
+    ap.add_argument("--workload", choices=["chain100", "chain100deep", "chain40", "batch512"],
+                    default="chain100",
+                    help="chain40 (N=40, p=2, chi=64, K=8) is the small profiling case; "
+                         "chain100deep has p=8 layers (bond dimension reaches chi=256)")
     args = ap.parse_args()
     global WORKLOAD, GATE_MODEL
     WORKLOAD = args.workload

@@ -12,6 +12,7 @@ build is measured on:
   tiny      N=6,   p=1, exact MPDO (no truncation), decay 0.01, dephasing 0.01
   chain40   N=40,  p=2, chi=64,  K=8,  decay 0.005, dephasing 0.005, crosstalk 0.01 rad
   chain100  N=100, p=3, chi=256, K=16, same noise as chain40 (precision form)
+  chain100deep  the same chain with p=8 layers (bond dimension reaches chi=256)
   batch512  512 circuits, N~U{20..100}, chi in {32,64,128}, K=8, p in {1,2},
             decay/dephasing log-uniform in [1e-4, 1e-2]
   surrogate MLP 4x256 trained on batch512-style samples
@@ -82,6 +83,14 @@ def chain40(seed: int = 2) -> Circuit:
 def chain100(seed: int = 3) -> Circuit:
     a, b = _angles(rng_for(seed), 3)
     return Circuit(n_sites=100, p=3, alpha=a, beta=b, gamma_diss=0.005, gamma_deph=0.005,
+                   xtalk_phase=0.01, delta_pp=0.01, chi_max=256, k_max=16, seed=seed)
+
+
+def chain100deep(seed: int = 3, p: int = 8) -> Circuit:
+    """chain100 with more QAOA layers (angles drawn from the same seed): at the numerical
+    floor of the cuts its bond dimension reaches the cap chi = 256, which three layers do not."""
+    a, b = _angles(rng_for(seed), p)
+    return Circuit(n_sites=100, p=p, alpha=a, beta=b, gamma_diss=0.005, gamma_deph=0.005,
                    xtalk_phase=0.01, delta_pp=0.01, chi_max=256, k_max=16, seed=seed)
 
 
