@@ -108,3 +108,51 @@ def test_tf32x3_update_shapes(lib, m, n, k):
     scale = np.abs(a[rows]).astype(np.float64) @ np.abs(b).astype(np.float64)
     err = (np.abs(tc.cpu().numpy()[rows] - want) / scale).max()
     assert err < _bound("tf32x3", k), err
+
+
+@pytest.mark.parametrize("elt", [2, 4])
+def test_real_core_throughput(lib, elt):
+    """Large square product (8192^3, the real core alone): correct on sampled entries, and
+    its rate (CUDA events, best of 5) printed against cuBLAS on the same GPU; the rate is
+    asserted only loosely (a tenth of cuBLAS), the measured fraction goes to the profiles."""
+    n = 8192
+    dt = torch.bfloat16 if elt == 2 else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(7)
+    a = torch.randn((n, n), device="cuda", generator=g).to(dt)
+    b = torch.randn((n, n), device="cuda", generator=g).to(dt)
+    d = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        lib.kernel_tcgemm_real(elt, n, n, n, a, n, b, n, d, n)
+    best = float("inf")
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lib.kernel_tcgemm_real(elt, n, n, n, a, n, b, n, d, n)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    ours = 2 * n ** 3 / (best / 1e3) / 1e12
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        bt = b.t()
+        for _ in range(2):
+            torch.matmul(a, bt)
+        ref_best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, bt)
+            e1.record()
+            torch.cuda.synchronize()
+            ref_best = min(ref_best, e0.elapsed_time(e1))
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    cublas = 2 * n ** 3 / (ref_best / 1e3) / 1e12
+    print(f"tc_gemm_kernel {'bf16' if elt == 2 else 'tf32'} {n}^3: {ours:.0f} TFLOP/s, "
+          f"cuBLAS {cublas:.0f} TFLOP/s, ratio {ours / cublas:.2f}")
+    rows = torch.randint(0, n, (8,), device="cuda", generator=g)
+    want = a[rows].double() @ b.double().t()
+    err = (d[rows].double() - want).abs().max().item() / (a[rows].double().abs() @ b.double().abs().t()).max().item()
+    assert err < (2e-3 if elt == 4 else 1e-2)
+    assert ours > 0.1 * cublas
