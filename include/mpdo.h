@@ -336,6 +336,18 @@ int mpdo_kernel_tcgemm_real(int elt, int m, int n, int k, const void* a, long ld
 int mpdo_kernel_tcgemm(int mode, int opa, int opb, int m, int n, int k, const void* a, long lda,
                        long sa, const void* b, long ldb, long sb, void* c, long ldc, long sc,
                        int batch, void* stream);
+/* FP64-accurate product of complex64 operands on the BF16 tensor cores: complex128
+ * c[b] = op(a[b]) op(b[b]), each operand row scaled by a power of two and split into six
+ * integer slices (exact in BF16), the 21 slice products of weight above 2^-48 accumulated
+ * exactly in FP32 over chunks of 1024 real terms and summed in FP64, so the result carries
+ * the product of the FP32 inputs to ~2^-48 of the rows' largest entries (error-free
+ * transformation of matrix products; Ozaki, Ogita, Oishi, Rump 2012).  This is what gives the
+ * Gram matrices of FP32 site tensors their FP64 eigenvalue floor in the mixed form (Sec.
+ * III.A truncation "removing the least significant diagonal elements" down to ~1e-13 of the
+ * largest).  Layouts as mpdo_kernel_cgemm; c has leading dimension ldc (complex128). */
+int mpdo_kernel_tcgemm_exact(int opa, int opb, int m, int n, int k, const void* a, long lda,
+                             long sa, const void* b, long ldb, long sb, void* c, long ldc,
+                             long sc, int batch, void* stream);
 
 /* MLP surrogate (no counterpart in the paper; the workload's learned part).  A fully
  * connected network with tanh hidden layers and a linear output maps a circuit description

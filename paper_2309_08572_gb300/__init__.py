@@ -132,6 +132,8 @@ def _load():
         "mpdo_kernel_heig": (I, [I, I, VP, VP, P(D), P(I), VP]),
         "mpdo_heig_noalloc": (I, [I, I, VP, VP, P(D), P(I), VP]),
         "mpdo_tc_gemm_launches": (C.c_longlong, []),
+        "mpdo_kernel_tcgemm_exact": (I, [I, I, I, I, I, VP, C.c_long, C.c_long, VP, C.c_long,
+                                         C.c_long, VP, C.c_long, C.c_long, I, VP]),
         "mpdo_kernel_tcgemm_real": (I, [I, I, I, I, VP, C.c_long, VP, C.c_long, VP, C.c_long,
                                         VP]),
         "mpdo_kernel_tcgemm": (I, [I, I, I, I, I, I, VP, C.c_long, C.c_long, VP, C.c_long,
@@ -601,3 +603,13 @@ def kernel_tcgemm(mode, opa: int, opb: int, m: int, n: int, k: int, a, lda: int,
     _check(LIB.mpdo_kernel_tcgemm(md, opa, opb, m, n, k, C.c_void_p(a.data_ptr()), lda, sa,
                                   C.c_void_p(b.data_ptr()), ldb, sb, C.c_void_p(c.data_ptr()),
                                   ldc, sc, batch, st))
+
+
+def kernel_tcgemm_exact(opa: int, opb: int, m: int, n: int, k: int, a, lda: int, sa: int, b,
+                        ldb: int, sb: int, c, ldc: int, sc: int, batch: int, stream=None):
+    """c (complex128) = op(a) op(b) for complex64 device tensors a, b: FP64-accurate exact
+    slice products on the BF16 tensor cores."""
+    st = _current_stream() if stream is None else C.c_void_p(stream)
+    _check(LIB.mpdo_kernel_tcgemm_exact(opa, opb, m, n, k, C.c_void_p(a.data_ptr()), lda, sa,
+                                        C.c_void_p(b.data_ptr()), ldb, sb,
+                                        C.c_void_p(c.data_ptr()), ldc, sc, batch, st))

@@ -276,10 +276,32 @@ int read_scalars(mpdo_ctx* h) {
 constexpr double kTcMinMacs = 1 << 21;
 constexpr int kTcMinSide = 16;
 
+// Products with FP64 outputs in the tensor-core forms with FP64 Grams (mixed form): the
+// error-free slice products on the BF16 tensor cores (tc_cgemm_exact) when large enough.
+inline bool tc_exact_route(const mpdo_ctx* h, int m, int n, int k, int batch) {
+  return h->tcmode >= 0 && h->mixed && (double)m * n * k * batch >= h->tc_min_macs &&
+         m >= kTcMinSide && n >= kTcMinSide && k >= 1;
+}
+template <typename TA, typename TB>
+cudaError_t pexact(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const TA* A, long lda,
+                   long sa, const TB* B, long ldb, long sb, double2* C, long ldc, long sc,
+                   int batch) {
+  int pi = prof_begin(h, 0);
+  cudaError_t e = tc_cgemm_exact<TA, TB>(h->st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc,
+                                         sc, batch, h->tcws, h->tcws_bytes, h->tcerr);
+  prof_end(h, 0, pi, 8.0 * m * n * (double)k * batch);
+  return e;
+}
+
 template <typename R>
 cudaError_t pgemm(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<R>* A, long lda,
                   long sa, const cx<R>* B, long ldb, long sb, cx<R>* C, long ldc, long sc,
                   int batch) {
+  if constexpr (std::is_same<R, double>::value) {
+    if (tc_exact_route(h, m, n, k, batch))
+      return pexact<double2, double2>(h, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc,
+                                      batch);
+  }
   if constexpr (std::is_same<R, float>::value) {
     if (h->tcmode >= 0 && (double)m * n * k * batch >= h->tc_min_macs && m >= kTcMinSide &&
         n >= kTcMinSide && k >= 1) {
@@ -338,6 +360,8 @@ cudaError_t pgram(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<R
   if constexpr (std::is_same<RS, RM>::value) {
     return pgemm<RS>(h, opa, opb, m, n, k, A, lda, 0, B, ldb, 0, C, ldc, 0, 1);
   } else {
+    if (tc_exact_route(h, m, n, k, 1))
+      return pexact<float2, float2>(h, opa, opb, m, n, k, A, lda, 0, B, ldb, 0, C, ldc, 0, 1);
     int pi = prof_begin(h, 0);
     cudaError_t e = cgemm_wide<float>(h->st, opa, opb, m, n, k, A, lda, 0, B, ldb, 0, C, ldc, 0, 1);
     prof_end(h, 0, pi, 8.0 * m * n * (double)k);
@@ -350,6 +374,8 @@ template <typename RB>
 cudaError_t pwide(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<float>* A,
                   long lda, long sa, const cx<RB>* B, long ldb, long sb, cx<double>* C, long ldc,
                   long sc, int batch) {
+  if (tc_exact_route(h, m, n, k, batch))
+    return pexact<float2, cx<RB>>(h, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch);
   int pi = prof_begin(h, 0);
   cudaError_t e =
       cgemm_wide<RB>(h->st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch);
@@ -1031,6 +1057,9 @@ cudaError_t penv(mpdo_ctx* h, int opa, int opb, int m, int n, int k, const cx<do
   if constexpr (std::is_same<RS, double>::value) {
     return pgemm<double>(h, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch);
   } else {
+    if (tc_exact_route(h, m, n, k, batch))
+      return pexact<double2, float2>(h, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc,
+                                     batch);
     int pi = prof_begin(h, 0);
     cudaError_t e = cgemm_dx(h->st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch);
     prof_end(h, 0, pi, 8.0 * m * n * (double)k * batch);
@@ -1270,7 +1299,8 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
   const size_t rsz = em / 2;
   if ((rc = alloc_dev(hp, &h->wRs, n3 * rsz)) || (rc = alloc_dev(hp, &h->wIrs, n3 * rsz)) ||
       (rc = alloc_dev(hp, (void**)&h->wSig, n3 * 8)) || (rc = alloc_dev(hp, (void**)&h->wLam, n9 * 8)) ||
-      (rc = alloc_dev(hp, (void**)&h->wWv, KM * 8)) || (rc = alloc_dev(hp, (void**)&h->wF, K * 8)))
+      (rc = alloc_dev(hp, (void**)&h->wWv, KM * 8)) ||
+      (rc = alloc_dev(hp, (void**)&h->wF, (1024 + 2 * 64) * 8)))
     return rc;
   const int ncap = (int)std::max(n9, KM);
   size_t eb = em == 16 ? eig_work_bytes<double>(ncap) : eig_work_bytes<float>(ncap);

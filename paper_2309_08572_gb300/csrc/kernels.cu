@@ -232,29 +232,53 @@ __global__ void make_q_kernel(int dm, int keep, int m_ops, const cx<R>* __restri
 // Inner-index cut + purity-preserving truncation (Sec. III.D Eqs. xiformula / ppt with
 // T = 1, P = identity; theta = 0 when infeasible; clamp negatives; keep the trace).
 // Writes f[k] = sqrt(Lambda~_k / w_k) for k < kk.
+// Partial sums of tr W (diagonal real parts) and ||W||_F^2 over the n x n matrix wm, one pair
+// per CTA of a fixed grid (kNormBlocks), so the final sum is deterministic.
+constexpr int kNormBlocks = 64;
 template <typename R>
-__global__ void kraus_select_kernel(int n, const double* __restrict__ w, const cx<R>* __restrict__ wm,
-                                    int ntr, double kcut, int kmax, int use_ppt, double* f,
+__global__ void __launch_bounds__(256) gram_norms_kernel(int n, const cx<R>* __restrict__ wm,
+                                                         double* parts) {
+  __shared__ double rt[256], rf[256];
+  double t = 0, f2 = 0;
+  const long total = (long)n * n;
+  for (long e = blockIdx.x * 256L + threadIdx.x; e < total; e += 256L * kNormBlocks) {
+    const cx<R> v = wm[e];
+    f2 += (double)v.x * v.x + (double)v.y * v.y;
+    if (e / n == e % n) t += (double)v.x;
+  }
+  rt[threadIdx.x] = t;
+  rf[threadIdx.x] = f2;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      rt[threadIdx.x] += rt[threadIdx.x + s];
+      rf[threadIdx.x] += rf[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    parts[2 * blockIdx.x] = rt[0];
+    parts[2 * blockIdx.x + 1] = rf[0];
+  }
+}
+
+template <typename R>
+__global__ void kraus_select_kernel(int n, const double* __restrict__ w, const double* parts,
+                                    double kcut, int kmax, int use_ppt, double* f,
                                     StepScalars* sc, DevStats* st, double* trace) {
   // total weight tr W and sum of squared weights ||W||_F^2 (= sum w^2 for the Hermitian W,
-  // whatever part of its spectrum was resolved), from the matrix in FP64
-  __shared__ double red_t[256], red_f[256];
-  {
-    double t = 0, f2 = 0;
-    for (long e = threadIdx.x; e < (long)ntr * ntr; e += blockDim.x) {
-      const cx<R> v = wm[e];
-      f2 += (double)v.x * v.x + (double)v.y * v.y;
-      if (e / ntr == e % ntr) t += (double)v.x;
-    }
-    red_t[threadIdx.x] = t;
-    red_f[threadIdx.x] = f2;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        red_t[threadIdx.x] += red_t[threadIdx.x + s];
-        red_f[threadIdx.x] += red_f[threadIdx.x + s];
-      }
-      __syncthreads();
+  // whatever part of its spectrum was resolved), from the matrix in FP64: the per-CTA partial
+  // sums of gram_norms_kernel, added here in a fixed order
+  __shared__ double red_t[kNormBlocks], red_f[kNormBlocks];
+  if (threadIdx.x < kNormBlocks) {
+    red_t[threadIdx.x] = parts[2 * threadIdx.x];
+    red_f[threadIdx.x] = parts[2 * threadIdx.x + 1];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int b = 1; b < kNormBlocks; ++b) {
+      red_t[0] += red_t[b];
+      red_f[0] += red_f[b];
     }
   }
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -770,9 +794,11 @@ template <typename R>
 cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, int ntr,
                          double kcut, int kmax, int use_ppt, double* f, StepScalars* sc,
                          DevStats* ds, double* trace) {
-  count_launch();
-  kraus_select_kernel<R><<<1, 256, 0, st>>>(n, w, wm, ntr, kcut, kmax, use_ppt, f, sc, ds,
-                                            trace);
+  // the partial sums live after the kept scale factors f (at most 1024 of them)
+  double* parts = f + 1024;
+  count_launch(2);
+  gram_norms_kernel<R><<<kNormBlocks, 256, 0, st>>>(ntr, wm, parts);
+  kraus_select_kernel<R><<<1, 256, 0, st>>>(n, w, parts, kcut, kmax, use_ppt, f, sc, ds, trace);
   return cudaGetLastError();
 }
 template <typename R>

@@ -39,6 +39,7 @@ cudaError_t polar_factors(cudaStream_t st, int n, const cx<R>* g, cx<R>* pm, cx<
 // n eigenvalues w (descending); the total weight is the trace of wm (ntr x ntr)
 // trace (device FP64, may be NULL): the carried trace of the state, multiplied by the
 // block's tr(theta')/tr(theta) = sc->tot / sc->trpre; the kept weights are rescaled to it.
+// f holds 1024 + 128 doubles (scale factors, then partial sums of tr W and ||W||_F^2).
 template <typename R>
 cudaError_t kraus_select(cudaStream_t st, int n, const double* w, const cx<R>* wm, int ntr,
                          double kcut, int kmax, int use_ppt, double* f, StepScalars* sc,

@@ -396,6 +396,310 @@ __global__ void __launch_bounds__(PT * 8)
   }
 }
 
+// ------------------------------------------------------------------ exact products
+// FP64-accurate product of FP32 operands on the BF16 tensor cores, by error-free slicing
+// (the splitting scheme of Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012).  Every row r of the A operand (and of the
+// B operand) is scaled by 2^-e_r, e_r the exponent of its largest |Re|, |Im|, and written as
+// six slices of integers in [-128, 128] (exact in BF16):
+//   x 2^-e_r = 2^-7 (q_1 + 2^-8 q_2 + ... + 2^-40 q_6) + O(2^-48).
+// The product of slice t of A and slice u of B is a sum of integer products of at most
+// 2^14 each; over a chunk of 1024 real K terms it stays below 2^24 and is therefore exact in
+// the FP32 accumulator.  Each chunk's accumulator is drained into FP64 registers with the
+// weight 2^-(14 + 8(t+u)) (t, u from 0) and, at the end, scaled by 2^(e_r + e_q).  The slice
+// pairs with t + u <= 5 are computed (21 of 36): a dropped pair contributes terms below
+// 2^-48 of the two rows' largest entries.  The result carries the FP32 inputs' product to
+// ~2^-48 of the rows' largest entries, enough for the eigenvalues of a Gram matrix of FP32
+// data down to ~1e-14 of the largest (the floor of FP64 sums of the same products).
+constexpr int XS = 6;          // slices per operand
+constexpr int XPAIRS = 21;     // slice pairs (t, u) with t + u <= XS - 1
+constexpr int XBN = 64;        // output tile width (real columns)
+constexpr int XSTAGES = 8;
+constexpr int XCHUNK = 16;     // k-blocks of 64 BF16 per exact chunk (1024 real terms)
+constexpr int XTHREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 drain
+
+// pair index -> (t, u), enumerating t = 0.., u = 0..XS-1-t
+__device__ __forceinline__ void pair_tu(int p, int& t, int& u) {
+  t = 0;
+  while (p >= XS - t) {
+    p -= XS - t;
+    ++t;
+  }
+  u = p;
+}
+
+__global__ void __launch_bounds__(XTHREADS, 1)
+    tc_exact_kernel(const __grid_constant__ CUtensorMap ma, const __grid_constant__ CUtensorMap mb,
+                    int M, int N, int kr, int ldk, const int* __restrict__ ea,
+                    const int* __restrict__ eb, double* C, long ldc, long sc, int accumulate,
+                    int* err) {
+  constexpr uint32_t A_BYTES = BM * 128, B_BYTES = XBN * 128;
+  constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (su32(smem_raw) & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + XSTAGES * STAGE_BYTES);
+  uint64_t* empty = full + XSTAGES;
+  uint64_t* tfull = empty + XSTAGES;   // [2] accumulator buffer ready for the drain
+  uint64_t* tempty = tfull + 2;        // [2] accumulator buffer drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + 2);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * XBN, m0 = blockIdx.y * BM, bz = blockIdx.z;
+  const int nkb = (kr + 63) / 64;                  // k-blocks per slice pair
+  const int nch = (nkb + XCHUNK - 1) / XCHUNK;     // exact chunks per slice pair
+  const int total_chunks = XPAIRS * nch;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < XSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tslot)),
+                 "r"(2 * XBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int ch = 0; ch < total_chunks && !*(volatile int*)abort_flag; ++ch) {
+        const int pair = ch / nch, c = ch % nch;
+        int t, u;
+        pair_tu(pair, t, u);
+        const int kb1 = min(nkb, (c + 1) * XCHUNK);
+        for (int kb = c * XCHUNK; kb < kb1; ++kb, ++it) {
+          const int s = it % XSTAGES;
+          if (it >= XSTAGES && !mbar_wait(&empty[s], ((it / XSTAGES) - 1) & 1)) {
+            atomicExch(abort_flag, 1);
+            atomicExch(err, 11);
+            break;
+          }
+          uint8_t* sa = smem + s * STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_3d(sa, &ma, &full[s], t * ldk + kb * 64, m0, bz);
+          tma_load_3d(sa + A_BYTES, &mb, &full[s], u * ldk + kb * 64, n0, bz);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t id = idesc<2>(XBN);
+      int it = 0;
+      for (int ch = 0; ch < total_chunks; ++ch) {
+        const int c = ch % nch, buf = ch & 1;
+        // the drain of chunk ch - 2 must have emptied this accumulator buffer
+        if (ch >= 2 && !mbar_wait(&tempty[buf], ((ch >> 1) - 1) & 1)) {
+          atomicExch(abort_flag, 1);
+          atomicExch(err, 12);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t td = tmem + buf * XBN;
+        const int kb1 = min(nkb, (c + 1) * XCHUNK);
+        bool ok = true;
+        for (int kb = c * XCHUNK; kb < kb1; ++kb, ++it) {
+          const int s = it % XSTAGES;
+          if (!mbar_wait(&full[s], (it / XSTAGES) & 1)) {
+            atomicExch(abort_flag, 1);
+            atomicExch(err, 13);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = su32(smem + s * STAGE_BYTES);
+          const uint64_t ad = sdesc(sa), bd = sdesc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            umma<2>(td, ad + 2 * kk, bd + 2 * kk, id, (kb > c * XCHUNK || kk) ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        umma_commit(&tfull[buf]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // drain warps: TMEM lanes 32 (warp % 4) .. +31 are tile rows
+    const int q = warp & 3;
+    const int row = m0 + q * 32 + lane;
+    double acc[XBN];
+#pragma unroll
+    for (int j = 0; j < XBN; ++j) acc[j] = 0.0;
+    bool ok = true;
+    for (int ch = 0; ch < total_chunks; ++ch) {
+      const int pair = ch / nch, buf = ch & 1;
+      int t, u;
+      pair_tu(pair, t, u);
+      bool ready = true;
+      if (lane == 0) ready = mbar_wait(&tfull[buf], (ch >> 1) & 1);
+      ready = __shfl_sync(0xffffffffu, ready ? 1 : 0, 0) != 0;
+      if (!ready || *(volatile int*)abort_flag) {
+        if (lane == 0 && !ready) atomicExch(err, 14);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const double w = ldexp(1.0, -(14 + 8 * (t + u)));
+      const uint32_t tw = tmem + ((uint32_t)(q * 32) << 16) + buf * XBN;
+#pragma unroll
+      for (int cb = 0; cb < XBN; cb += 32) {
+        float v[32];
+        tmem_ld32(tw + cb, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[cb + j] = fma(w, (double)v[j], acc[cb + j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[buf])) : "memory");
+    }
+    if (ok && row < M) {
+      const int er = ea[(long)bz * M + row];
+      double* cp = C + (long)bz * sc + (long)row * ldc;
+#pragma unroll
+      for (int j = 0; j < XBN; ++j) {
+        const int col = n0 + j;
+        if (col < N) {
+          const double v = ldexp(acc[j], er + eb[(long)bz * (N / 2) + col / 2]);
+          cp[col] = accumulate ? cp[col] + v : v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * XBN)
+                 : "memory");
+  }
+}
+
+// e[b][r] = exponent of the largest |Re|, |Im| of row r of X (X[r][c] = src[b*sb + r*s_r +
+// c*s_c], c < kc): max = f 2^e with f in [0.5, 1); 0 for an all-zero row.
+template <typename TIN>
+__global__ void __launch_bounds__(256) row_exp_kernel(int rows, int kc, const TIN* __restrict__ src,
+                                                     long s_r, long s_c, long sb, int* e) {
+  __shared__ double red[256];
+  const int r = blockIdx.x, b = blockIdx.y;
+  const TIN* x = src + (long)b * sb + (long)r * s_r;
+  double mx = 0.0;
+  for (int c = threadIdx.x; c < kc; c += blockDim.x) {
+    const TIN v = x[(long)c * s_c];
+    mx = fmax(mx, fmax(fabs((double)v.x), fabs((double)v.y)));
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int ex = 0;
+    if (red[0] > 0.0) frexp(red[0], &ex);
+    e[(long)b * rows + r] = ex;
+  }
+}
+
+// XS integer slices of x in (-1, 1): x = 2^-7 sum_t 2^-8t q_(t+1) + r, |q| <= 128,
+// |r| <= 2^-(8 XS) (every step is exact in FP32: y - rint(y) is a multiple of y's last bit).
+template <typename F>
+__device__ __forceinline__ void slice_all(F x, float* q) {
+  F y = x * (F)128;
+#pragma unroll
+  for (int t = 0; t < XS; ++t) {
+    const F r = rint(y);
+    q[t] = (float)r;
+    y = (y - r) * (F)256;
+  }
+}
+
+// Sliced packing (layout as pack_kernel, with XS K-segments of ldk elements, one per slice;
+// the segment tails up to ldk are written as zeros): row scale 2^-e[b][r] (A side) or the
+// column scale of the complex column (B side, rows 2r and 2r+1).
+template <typename TIN>
+__global__ void __launch_bounds__(PT * 8)
+    pack_exact_kernel(int rows, int kc, const TIN* __restrict__ src, long s_r, long s_c, long sb,
+                      int conj, int side, const int* __restrict__ e, __nv_bfloat16* __restrict__ out,
+                      long ldo, long so, int ldk) {
+  using F = decltype(TIN().x);
+  __shared__ TIN tile[PT][PT + 1];
+  const int r0 = blockIdx.y * PT, c0 = blockIdx.x * PT, b = blockIdx.z;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  src += (long)b * sb;
+  const bool c_fast = (s_c == 1);
+  for (int qq = ty; qq < PT; qq += 8) {
+    const int r = c_fast ? r0 + qq : r0 + tx;
+    const int c = c_fast ? c0 + tx : c0 + qq;
+    TIN v;
+    v.x = 0;
+    v.y = 0;
+    if (r < rows && c < kc) {
+      v = src[(long)r * s_r + (long)c * s_c];
+      if (conj) v.y = -v.y;
+    }
+    if (c_fast) tile[qq][tx] = v; else tile[tx][qq] = v;
+  }
+  __syncthreads();
+  for (int qq = ty; qq < PT; qq += 8) {
+    const int r = r0 + qq, c = c0 + tx;
+    if (r >= rows || c >= kc) continue;
+    const int er = e[(long)b * rows + r];
+    const TIN v = tile[qq][tx];
+    float qr[XS], qi[XS];
+    slice_all<F>(ldexp(v.x, -er), qr);
+    slice_all<F>(ldexp(v.y, -er), qi);
+    if (side == 0) {
+      __nv_bfloat16* o = out + (long)b * so + (long)r * ldo + 2L * c;
+#pragma unroll
+      for (int t = 0; t < XS; ++t) {
+        o[t * ldk] = __float2bfloat16_rn(qr[t]);
+        o[t * ldk + 1] = __float2bfloat16_rn(qi[t]);
+      }
+    } else {
+      __nv_bfloat16* o0 = out + (long)b * so + (2L * r) * ldo + 2L * c;
+      __nv_bfloat16* o1 = o0 + ldo;
+#pragma unroll
+      for (int t = 0; t < XS; ++t) {
+        o0[t * ldk] = __float2bfloat16_rn(qr[t]);
+        o0[t * ldk + 1] = __float2bfloat16_rn(-qi[t]);
+        o1[t * ldk] = __float2bfloat16_rn(qi[t]);
+        o1[t * ldk + 1] = __float2bfloat16_rn(qr[t]);
+      }
+    }
+  }
+}
+
+// Zero the K-segment tails [kr, ldk) of every slice of every packed row (rows_out rows).
+__global__ void zero_tails_kernel(long rows_out, int kr, int ldk, __nv_bfloat16* out, long ldo) {
+  const int w = ldk - kr;
+  const long total = rows_out * XS * w;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long r = e / (XS * w);
+    const int t = (int)((e / w) % XS), j = (int)(e % w);
+    out[r * ldo + (long)t * ldk + kr + j] = __float2bfloat16_rn(0.f);
+  }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -572,6 +876,97 @@ cudaError_t tc_cgemm(cudaStream_t st, int mode, int opa, int opb, int m, int n, 
   return cudaSuccess;
 }
 
+// ---- exact products: C (complex FP64) = op(A) op(B), FP32 complex A and B
+static size_t exact_bytes(long m, long n, long kc, int batch) {
+  const long ldk = (2 * kc + 63) / 64 * 64;
+  const size_t a = ((size_t)batch * m * XS * ldk * 2 + 255) & ~(size_t)255;
+  const size_t b = ((size_t)batch * 2 * n * XS * ldk * 2 + 255) & ~(size_t)255;
+  return a + b + ((size_t)batch * (m + n) * sizeof(int) + 256);
+}
+
+size_t tc_exact_ws_bytes(long m, long n, long k, int batch) {
+  return exact_bytes(m, n, std::min<long>(k, 4096), batch);
+}
+
+template <typename TA, typename TB>
+cudaError_t tc_cgemm_exact(cudaStream_t st, int opa, int opb, int m, int n, int k, const TA* A,
+                           long lda, long sa, const TB* B, long ldb, long sb, double2* C, long ldc,
+                           long sc, int batch, void* ws, size_t ws_bytes, int* err) {
+  if (m <= 0 || n <= 0 || batch <= 0) return cudaSuccess;
+  if (k <= 0) return cudaErrorInvalidValue;
+  long kc = k;
+  while (kc > 64 && exact_bytes(m, n, kc, batch) > ws_bytes) kc = (kc + 1) / 2;
+  if (kc < k) kc = std::max(64L, kc / 64 * 64);
+  if (exact_bytes(m, n, kc, batch) > ws_bytes) return cudaErrorMemoryAllocation;
+  long sra, sca, srb, scb;
+  int cja, cjb;
+  op_strides(0, opa, lda, &sra, &sca, &cja);
+  op_strides(1, opb, ldb, &srb, &scb, &cjb);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      tc_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(XSTAGES * (BM + XBN) * 128 + 1024 + 256));
+  if (attr != cudaSuccess) return attr;
+  for (long k0 = 0; k0 < k; k0 += kc) {
+    const int kn = (int)std::min<long>(kc, k - k0);
+    const int kr = 2 * kn;
+    const int ldk = (kr + 63) / 64 * 64;
+    const long ldo = (long)XS * ldk;
+    char* p = static_cast<char*>(ws);
+    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(p);
+    p += ((size_t)batch * m * ldo * 2 + 255) & ~(size_t)255;
+    __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(p);
+    p += ((size_t)batch * 2 * n * ldo * 2 + 255) & ~(size_t)255;
+    int* ea = reinterpret_cast<int*>(p);
+    int* eb = ea + (size_t)batch * m;
+    const TA* a0 = A + k0 * sca;
+    const TB* b0 = B + k0 * scb;
+    row_exp_kernel<TA><<<dim3(m, batch), 256, 0, st>>>(m, kn, a0, sra, sca, sa, ea);
+    row_exp_kernel<TB><<<dim3(n, batch), 256, 0, st>>>(n, kn, b0, srb, scb, sb, eb);
+    dim3 blk(PT, 8);
+    pack_exact_kernel<TA><<<dim3((kn + PT - 1) / PT, (m + PT - 1) / PT, batch), blk, 0, st>>>(
+        m, kn, a0, sra, sca, sa, cja, 0, ea, pa, ldo, (long)m * ldo, ldk);
+    pack_exact_kernel<TB><<<dim3((kn + PT - 1) / PT, (n + PT - 1) / PT, batch), blk, 0, st>>>(
+        n, kn, b0, srb, scb, sb, cjb, 1, eb, pb, ldo, 2L * n * ldo, ldk);
+    count_launch(4);
+    if (ldk > kr) {
+      zero_tails_kernel<<<256, 256, 0, st>>>((long)batch * m, kr, ldk, pa, ldo);
+      zero_tails_kernel<<<256, 256, 0, st>>>((long)batch * 2 * n, kr, ldk, pb, ldo);
+      count_launch(2);
+    }
+    MPDO_CUDA_TRY(cudaGetLastError());
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, 2, pa, ldo, m, ldo, (long)m * ldo, batch, BM) ||
+        !make_map(&mb, 2, pb, ldo, 2L * n, ldo, 2L * n * ldo, batch, XBN))
+      return cudaErrorInvalidValue;
+    dim3 grid((2 * n + XBN - 1) / XBN, (m + BM - 1) / BM, batch);
+    const size_t smem = XSTAGES * (BM + XBN) * 128 + 1024 + 256;
+    tc_exact_kernel<<<grid, XTHREADS, smem, st>>>(ma, mb, m, 2 * n, kr, ldk, ea, eb,
+                                                  reinterpret_cast<double*>(C), 2 * ldc, 2 * sc,
+                                                  k0 > 0 ? 1 : 0, err);
+    count_launch();
+    g_tc_launches.fetch_add(1, std::memory_order_relaxed);
+    MPDO_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+template cudaError_t tc_cgemm_exact<float2, float2>(cudaStream_t, int, int, int, int, int,
+                                                    const float2*, long, long, const float2*,
+                                                    long, long, double2*, long, long, int, void*,
+                                                    size_t, int*);
+template cudaError_t tc_cgemm_exact<float2, double2>(cudaStream_t, int, int, int, int, int,
+                                                     const float2*, long, long, const double2*,
+                                                     long, long, double2*, long, long, int, void*,
+                                                     size_t, int*);
+template cudaError_t tc_cgemm_exact<double2, float2>(cudaStream_t, int, int, int, int, int,
+                                                     const double2*, long, long, const float2*,
+                                                     long, long, double2*, long, long, int, void*,
+                                                     size_t, int*);
+template cudaError_t tc_cgemm_exact<double2, double2>(cudaStream_t, int, int, int, int, int,
+                                                      const double2*, long, long, const double2*,
+                                                      long, long, double2*, long, long, int, void*,
+                                                      size_t, int*);
+
 size_t tc_cgemm_ws_bytes(int mode, long m, long n, long k, int batch) {
   const int elt = tc_mode_elt(mode);
   const long ld = tc_pack_ld(mode, k);
@@ -660,6 +1055,31 @@ int mpdo_kernel_tcgemm(int mode, int opa, int opb, int m, int n, int k, const vo
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) return tc_fail(MPDO_ERR_CUDA, cudaGetErrorString(ce));
   if (herr) return tc_fail(MPDO_ERR_TIMEOUT, "tcgemm: a pipeline wait gave up");
+  return MPDO_OK;
+}
+
+int mpdo_kernel_tcgemm_exact(int opa, int opb, int m, int n, int k, const void* a, long lda,
+                             long sa, const void* b, long ldb, long sb, void* c, long ldc,
+                             long sc, int batch, void* stream) {
+  if (opa < 0 || opa > 3 || opb < 0 || opb > 3 || m < 0 || n < 0 || k < 1 || batch < 0 || !a ||
+      !b || !c)
+    return tc_fail(MPDO_ERR_ARG, "bad tcgemm_exact arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t ws = mpdo::tc_exact_ws_bytes(m, n, k, batch);
+  DevBuf w, err;
+  if (cudaMalloc(&w.p, ws) != cudaSuccess || cudaMalloc(&err.p, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return tc_fail(MPDO_ERR_OOM, "tcgemm_exact workspace");
+  }
+  cudaMemsetAsync(err.p, 0, sizeof(int), st);
+  cudaError_t ce = mpdo::tc_cgemm_exact<float2, float2>(
+      st, opa, opb, m, n, k, static_cast<const float2*>(a), lda, sa, static_cast<const float2*>(b),
+      ldb, sb, static_cast<double2*>(c), ldc, sc, batch, w.p, ws, static_cast<int*>(err.p));
+  int herr = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return tc_fail(MPDO_ERR_CUDA, cudaGetErrorString(ce));
+  if (herr) return tc_fail(MPDO_ERR_TIMEOUT, "tcgemm_exact: a pipeline wait gave up");
   return MPDO_OK;
 }
 

@@ -53,4 +53,14 @@ cudaError_t tc_cgemm(cudaStream_t st, int mode, int opa, int opb, int m, int n, 
                      void* ws, size_t ws_bytes, int* err);
 size_t tc_cgemm_ws_bytes(int mode, long m, long n, long k, int batch);
 
+// Complex FP64 C[b] = op(A[b]) op(B[b]) of complex FP32 or FP64 operands (TA, TB: float2 or
+// double2), carried to ~2^-48 of each operand row's largest entry and summed in FP64
+// (error-free BF16 slices on the tensor cores; tcgemm.cu).  Long K is processed in pieces
+// that fit ws, added in FP64.
+template <typename TA, typename TB>
+cudaError_t tc_cgemm_exact(cudaStream_t st, int opa, int opb, int m, int n, int k, const TA* A,
+                           long lda, long sa, const TB* B, long ldb, long sb, double2* C, long ldc,
+                           long sc, int batch, void* ws, size_t ws_bytes, int* err);
+size_t tc_exact_ws_bytes(long m, long n, long k, int batch);
+
 }  // namespace mpdo

@@ -156,3 +156,55 @@ def test_real_core_throughput(lib, elt):
     err = (d[rows].double() - want).abs().max().item() / (a[rows].double().abs() @ b.double().abs().t()).max().item()
     assert err < (2e-3 if elt == 4 else 1e-2)
     assert ours > 0.1 * cublas
+
+
+@pytest.mark.parametrize("opa,opb", [(0, 0), (2, 0), (0, 2), (1, 3), (3, 1)])
+@pytest.mark.parametrize("m,n,k", [(70, 45, 130), (129, 200, 1100), (5, 300, 3000)])
+def test_exact_slices_match_fp64_product(lib, opa, opb, m, n, k):
+    """The exact-slice product of FP32 operands equals their product in FP64 (numpy
+    complex128) up to the 2^-48 row slicing: |err| <= 2^-40 sum |a||b| per entry; chunks of
+    1024 real terms (k > 512) and ragged tiles included."""
+    rng = np.random.default_rng(m + n + k + opa * 5 + opb)
+    ash = (m, k) if opa in (0, 3) else (k, m)
+    bsh = (k, n) if opb in (0, 3) else (n, k)
+    a = _rand(rng, (2,) + ash)
+    b = _rand(rng, (2,) + bsh)
+    tc = torch.zeros((2, m, n), dtype=torch.complex128, device="cuda")
+    lib.kernel_tcgemm_exact(opa, opb, m, n, k, torch.tensor(a, device="cuda"), ash[1],
+                            ash[0] * ash[1], torch.tensor(b, device="cuda"), bsh[1],
+                            bsh[0] * bsh[1], tc, n, m * n, 2)
+    torch.cuda.synchronize()
+    a64, b64 = a.astype(np.complex128), b.astype(np.complex128)
+    want = np.stack([_op(a64[i], opa) @ _op(b64[i], opb) for i in range(2)])
+    scale = np.stack([np.abs(_op(a64[i], opa)) @ np.abs(_op(b64[i], opb)) for i in range(2)])
+    err = (np.abs(tc.cpu().numpy() - want) / scale).max()
+    assert err < 2.0 ** -40, err
+
+
+def test_exact_gram_keeps_the_small_eigenvalues(lib):
+    """Gram G = X^+ X of an FP32 matrix whose singular values fall from 1 to 1e-7: the
+    exact-slice Gram has the eigenvalues of the FP64 Gram of the same FP32 data down to
+    1e-14 of the largest (relative agreement 1e-6 on every eigenvalue above that), which an
+    FP32-accumulated (TF32x3) Gram cannot resolve below ~1e-7."""
+    rng = np.random.default_rng(11)
+    rows, cols = 600, 96
+    u, _ = np.linalg.qr(_rand(rng, (rows, cols)).astype(np.complex128))
+    v, _ = np.linalg.qr(_rand(rng, (cols, cols)).astype(np.complex128))
+    s = np.logspace(0, -7, cols)
+    x = ((u * s) @ v.conj().T).astype(np.complex64)
+    tx = torch.tensor(x, device="cuda")
+    g = torch.zeros((cols, cols), dtype=torch.complex128, device="cuda")
+    lib.kernel_tcgemm_exact(2, 0, cols, cols, rows, tx, cols, 0, tx, cols, 0, g, cols, 0, 1)
+    torch.cuda.synchronize()
+    x64 = x.astype(np.complex128)
+    want = np.linalg.eigvalsh(x64.conj().T @ x64)[::-1]
+    got = np.linalg.eigvalsh(g.cpu().numpy())[::-1]
+    keep = want > 1e-14 * want[0]
+    assert keep.sum() == cols
+    rel = np.abs(got[keep] - want[keep]) / want[keep]
+    assert rel.max() < 1e-6, rel.max()
+    g32 = torch.zeros((cols, cols), dtype=torch.complex64, device="cuda")
+    lib.kernel_tcgemm("tf32x3", 2, 0, cols, cols, rows, tx, cols, 0, tx, cols, 0, g32, cols, 0, 1)
+    torch.cuda.synchronize()
+    got32 = np.linalg.eigvalsh(g32.cpu().numpy().astype(np.complex128))[::-1]
+    assert np.abs(got32[-10:] - want[-10:]).max() > 1e3 * want[-1]
