@@ -161,6 +161,19 @@ int mpdo_truncate(mpdo_t h, int chi_max, int k_max, int use_ppt, mpdo_trunc_stat
 int mpdo_expect_energy(mpdo_t h, double J, double hx, double b, double* e_raw,
                        double* e_success, double* success_prob, double* trace);
 
+/* Second-order observables (quadratic in rho; Sec. III.E, costs of Fig. 6c-d), from
+ * environments of two copies of rho contracted site by site in the sites' precision with
+ * FP64 final sums:
+ *   xi        = tr(rho^2) / tr(rho)^2            (the purity PPT preserves, Sec. III.D)
+ *   collision = sum_x <x|rho|x>^2 / tr(rho)^2   (anticoncentration of the outcomes)
+ *   s2_left, s2_right = -log(tr(rho_A^2) / tr(rho)^2) for A = sites < cut resp. >= cut
+ *   i2        = s2_left + s2_right + log(xi)    (Renyi-2 mutual information across the cut)
+ * The environments have D^4 entries (D the largest bond dimension): the call allocates
+ * ~50 D^4 complex numbers for its duration (through the handle's hooks) and refuses more than
+ * 32 GB with MPDO_ERR_ARG.  cut in 1..N-1; outputs are host doubles, any may be NULL. */
+int mpdo_expect_second_order(mpdo_t h, int cut, double* xi, double* collision, double* s2_left,
+                             double* s2_right, double* i2);
+
 /* Draw n_samples configurations x in {0,1,2}^N from <x|rho|x>/tr(rho) by sequential
  * conditional sampling with Philox4x32-10 uniforms (counter (site, sample, 0, 0), key
  * = seed).  bits: host uint8 [n_samples][N]; probs: host double [n_samples] receives
@@ -373,6 +386,11 @@ int mpdo_mlp_loss_grad(mpdo_mlp m, int batch, const float* x, const float* t, fl
                        float* grad_host);
 int mpdo_mlp_adam_step(mpdo_mlp m, float lr);
 int mpdo_mlp_input_grad(mpdo_mlp m, int batch, const float* x, const float* wout_host, float* gx);
+/* Precision of the network's products: 0 = FP32 on the CUDA cores (default); 1 = BF16
+ * operands on the tensor cores (tcgen05, TMA-fed) with FP32 accumulation, parameters,
+ * gradients and Adam moments kept in FP32 (mixed-precision training).  Allocates the packed
+ * operand buffers on first use; MPDO_ERR_ARG for another mode. */
+int mpdo_mlp_set_precision(mpdo_mlp m, int mode);
 int mpdo_mlp_destroy(mpdo_mlp m);
 
 /* Allocation-free variant of mpdo_kernel_heig.  The paper has no counterpart: this entry

@@ -102,6 +102,7 @@ def _load():
         "mpdo_expect_energy": (I, [VP, D, D, D, P(D), P(D), P(D), P(D)]),
         "mpdo_sample_probs": (I, [VP, I, C.c_uint64, P(C.c_uint8), P(D)]),
         "mpdo_get_dims": (I, [VP, P(I), P(I), P(I)]),
+        "mpdo_expect_second_order": (I, [VP, I, P(D), P(D), P(D), P(D), P(D)]),
         "mpdo_reconfigure": (I, [VP, I, I, I, I, P(D)]),
         "mpdo_batch_run": (I, [I, P(VP), I, P(CircuitDesc), P(D), P(I)]),
         "mpdo_batch_run_host": (I, [I, P(VP), I, P(CircuitHostDesc), P(D), P(I)]),
@@ -126,6 +127,7 @@ def _load():
         "mpdo_mlp_adam_step": (I, [VP, C.c_float]),
         "mpdo_mlp_input_grad": (I, [VP, I, VP, P(C.c_float), VP]),
         "mpdo_mlp_destroy": (I, [VP]),
+        "mpdo_mlp_set_precision": (I, [VP, I]),
         "mpdo_autotune_gemm": (I, [I, VP, I, P(I)]),
         "mpdo_kernel_cgemm": (I, [I, I, I, I, I, I, VP, C.c_long, C.c_long, VP, C.c_long,
                                   C.c_long, VP, C.c_long, C.c_long, I, VP]),
@@ -356,6 +358,13 @@ class Mpdo:
                self._h)
         return dict(zip(("e_raw", "e_succ", "p_succ", "trace"), (v.value for v in vals)))
 
+    def second_order(self, cut: int) -> dict:
+        """xi = tr rho^2 / (tr rho)^2, collision probability, Renyi-2 entropies of the two
+        halves at `cut` and their mutual information (library environments)."""
+        v = [C.c_double(0) for _ in range(5)]
+        _check(LIB.mpdo_expect_second_order(self._h, cut, *[C.byref(x) for x in v]), self._h)
+        return dict(zip(("xi", "collision", "s2_left", "s2_right", "i2"), [x.value for x in v]))
+
     def sample_probs(self, n_samples: int, seed: int) -> Tuple[np.ndarray, np.ndarray]:
         bits = np.zeros((n_samples, self.n), dtype=np.uint8)
         probs = np.zeros(n_samples)
@@ -455,17 +464,22 @@ def batch_run_host(pool: Sequence["Mpdo"], circuits: Sequence[HostCircuit]) -> n
 
 
 class Mlp:
-    """MLP surrogate on the GPU (tanh hidden layers, linear output), FP32."""
+    """MLP surrogate on the GPU (tanh hidden layers, linear output): FP32, or BF16 tensor-core
+    products with FP32 accumulation and parameters."""
 
-    def __init__(self, widths: Sequence[int], max_batch: int, stream=None):
+    def __init__(self, widths: Sequence[int], max_batch: int, stream=None, bf16: bool = False):
         """stream: CUDA stream for the network's kernels; default torch's current stream,
-        so device inputs written by torch are ordered before the network reads them."""
+        so device inputs written by torch are ordered before the network reads them.
+        bf16: products on the tensor cores with BF16 operands (FP32 accumulation and FP32
+        master parameters)."""
         arr = (C.c_int * len(widths))(*widths)
         self._h = C.c_void_p(None)
         st = _current_stream() if stream is None else C.c_void_p(stream)
         _check(LIB.mpdo_mlp_create(len(widths) - 1, arr, max_batch, st, C.byref(self._h)))
         self.widths = list(widths)
         self.n_params = int(LIB.mpdo_mlp_n_params(self._h))
+        if bf16:
+            _check(LIB.mpdo_mlp_set_precision(self._h, 1))
 
     def close(self):
         if self._h:

@@ -1122,6 +1122,143 @@ int energy(mpdo_ctx* h, double J, double hx, double bz, double out[7]) {
   return MPDO_OK;
 }
 
+// ------------------------------------------------------- second-order observables
+// Environments of two copies of rho (Sec. III.E): one site of rho is the operator
+// R[(a,b)][s][s'][(r,r')] = sum_k A[a,s,k,r] conj(A[b,s',k,r']); two copies contract site by
+// site, crossed (tr rho^2: copy 1 [s][s'] with copy 2 [s'][s]), diagonal (collision) or
+// traced per copy (which factorises into the plain trace environment squared).  In the
+// storage precision of the sites, with FP64 final contractions.
+template <typename R>
+int second_order(mpdo_ctx* h, int cut, double out[5]) {
+  using T = cx<R>;
+  cudaStream_t st = h->st;
+  const int N = h->n;
+  int dmax = 1;
+  for (int b : h->bond) dmax = std::max(dmax, b);
+  const long d2 = (long)dmax * dmax, d4 = d2 * d2;
+  const double bytes = (double)sizeof(T) * (6.0 * 9 * d4 + 8.0 * d4 + 4.0 * d2 +
+                                            (double)h->site_cap) + 4096;
+  if (bytes > (double)((size_t)32 << 30))
+    return fail(h, MPDO_ERR_ARG, "second-order environments need " + std::to_string(bytes / 1e9) +
+                                     " GB at bond dimension " + std::to_string(dmax) +
+                                     " (limit 32 GB)");
+  void* mem = dmalloc(h, (size_t)bytes);
+  if (!mem) return fail(h, MPDO_ERR_OOM, "second-order environment buffers");
+  struct Guard {
+    mpdo_ctx* h;
+    void* p;
+    ~Guard() {
+      cudaStreamSynchronize(h->st);
+      dfree(h, p);
+    }
+  } guard{h, mem};
+  T* Ap = static_cast<T*>(mem);
+  T* Rf = Ap + h->site_cap;
+  T* Rp = Rf + 9 * d4;
+  T* Rd = Rp + 9 * d4;     // diagonal copy of Rp (collision)
+  T* W = Rd + 9 * d4;
+  T* W2 = W + 9 * d4;
+  T* RS = W2 + 9 * d4;
+  T* CL = RS + 9 * d4;     // crossed left env
+  T* CD = CL + d4;         // diagonal left env
+  T* CR = CD + d4;         // crossed right env
+  T* tmp = CR + d4;        // 2 d4
+  T* eL = tmp + 2 * d4;
+  T* eR = eL + d2;
+  T* etmp = eR + d2;       // 2 d2
+  T* Tr = etmp + 2 * d2;   // trace over s of R: dl^2 x dr^2 <= d4
+  double* parts = reinterpret_cast<double*>(Tr + d4);
+  double* res = parts + 64;   // 6 results
+  const T o = one<R>();
+  // site n: Rp (and the diagonal copy / trace) from its tensor
+  auto site_rho = [&](int n, int* dl_o, int* dr_o) -> int {
+    const int dl = h->bond[n], k = h->kd[n], dr = h->bond[n + 1];
+    const T* A = static_cast<const T*>(h->site(n));
+    PO(swap12<T>(st, (long)dl * 3, k, dr, 1, A, Ap));
+    const int rows = 3 * dl * dr;
+    CK(pgemm<R>(h, OP_N, OP_C, rows, rows, k, Ap, k, 0, Ap, k, 0, Rf, rows, 0, 1));
+    const int dd[6] = {dl, 3, dr, dl, 3, dr}, pp[6] = {0, 3, 1, 4, 2, 5};
+    PO(permute6<T>(st, dd, pp, Rf, Rp));
+    *dl_o = dl;
+    *dr_o = dr;
+    return MPDO_OK;
+  };
+  // left crossed transfer: env (dl^2 x dl^2) -> out (dr^2 x dr^2) with site operator r
+  auto left_cross = [&](const T* r, int dl, int dr, const T* env, T* outp) -> int {
+    const long l2 = (long)dl * dl, r2 = (long)dr * dr;
+    CK(pgemm<R>(h, OP_T, OP_N, (int)(9 * r2), (int)l2, (int)l2, r, 9 * r2, 0, env, l2, 0, W, l2,
+                0, 1));
+    const int dw[6] = {3, 3, dr, dr, dl, dl}, pw[6] = {2, 3, 0, 1, 4, 5};
+    PO(permute6<T>(st, dw, pw, W, W2));
+    const int drs[6] = {dl, dl, 3, 3, dr, dr}, prs[6] = {3, 2, 0, 1, 4, 5};
+    PO(permute6<T>(st, drs, prs, r, RS));
+    CK(pgemm<R>(h, OP_N, OP_N, (int)r2, (int)r2, (int)(9 * l2), W2, 9 * l2, 0, RS, r2, 0, outp,
+                r2, 0, 1));
+    return MPDO_OK;
+  };
+  int rc;
+  const T init = o;
+  CK(cudaMemcpyAsync(CL, &init, sizeof(T), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(CD, &init, sizeof(T), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(eL, &init, sizeof(T), cudaMemcpyHostToDevice, st));
+  // left sweep over all sites: crossed env saved at the cut, diagonal env and plain trace env
+  T* CLcut = tmp + d4;     // crossed env at the cut
+  T* eLcut = etmp + d2;
+  for (int n = 0; n < N; ++n) {
+    if (n == cut) {
+      const long c2 = (long)h->bond[n] * h->bond[n];
+      CK(cudaMemcpyAsync(CLcut, CL, sizeof(T) * c2 * c2, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(eLcut, eL, sizeof(T) * c2, cudaMemcpyDeviceToDevice, st));
+    }
+    int dl, dr;
+    if ((rc = site_rho(n, &dl, &dr))) return rc;
+    const long l2 = (long)dl * dl, r2 = (long)dr * dr;
+    CK(cudaMemcpyAsync(Rd, Rp, sizeof(T) * 9 * l2 * r2, cudaMemcpyDeviceToDevice, st));
+    PO(rho_site<R>(st, l2, r2, Rd, nullptr, 1));
+    PO(rho_site<R>(st, l2, r2, Rp, Tr, 2));
+    if ((rc = left_cross(Rp, dl, dr, CL, tmp))) return rc;
+    CK(cudaMemcpyAsync(CL, tmp, sizeof(T) * r2 * r2, cudaMemcpyDeviceToDevice, st));
+    if ((rc = left_cross(Rd, dl, dr, CD, tmp))) return rc;
+    CK(cudaMemcpyAsync(CD, tmp, sizeof(T) * r2 * r2, cudaMemcpyDeviceToDevice, st));
+    CK(pgemm<R>(h, OP_N, OP_N, 1, (int)r2, (int)l2, eL, l2, 0, Tr, r2, 0, etmp, r2, 0, 1));
+    CK(cudaMemcpyAsync(eL, etmp, sizeof(T) * r2, cudaMemcpyDeviceToDevice, st));
+  }
+  // right sweep from the far end down to the cut: crossed and plain envs
+  CK(cudaMemcpyAsync(CR, &init, sizeof(T), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(eR, &init, sizeof(T), cudaMemcpyHostToDevice, st));
+  for (int n = N - 1; n >= cut; --n) {
+    int dl, dr;
+    if ((rc = site_rho(n, &dl, &dr))) return rc;
+    const long l2 = (long)dl * dl, r2 = (long)dr * dr;
+    PO(rho_site<R>(st, l2, r2, Rp, Tr, 2));
+    // Z[(a,b,s,s'),(x,y)] = Rp (9 l2 x r2) CR (r2 x r2); CR' = Z RS^T with RS = Rp, s <-> s'
+    CK(pgemm<R>(h, OP_N, OP_N, (int)(9 * l2), (int)r2, (int)r2, Rp, r2, 0, CR, r2, 0, W, r2, 0,
+                1));
+    const int dd[6] = {dl, dl, 3, 3, dr, dr}, pp[6] = {0, 1, 3, 2, 4, 5};
+    PO(permute6<T>(st, dd, pp, Rp, RS));
+    CK(pgemm<R>(h, OP_N, OP_T, (int)l2, (int)l2, (int)(9 * r2), W, 9 * r2, 0, RS, 9 * r2, 0, tmp,
+                l2, 0, 1));
+    CK(cudaMemcpyAsync(CR, tmp, sizeof(T) * l2 * l2, cudaMemcpyDeviceToDevice, st));
+    CK(pgemm<R>(h, OP_N, OP_N, (int)l2, 1, (int)r2, Tr, r2, 0, eR, 1, 0, etmp, 1, 0, 1));
+    CK(cudaMemcpyAsync(eR, etmp, sizeof(T) * l2, cudaMemcpyDeviceToDevice, st));
+  }
+  const long c2 = (long)h->bond[cut] * h->bond[cut];
+  PO(env_dot<R>(st, c2 * c2, CLcut, CR, 0, parts, res + 0));      // tr rho^2
+  PO(env_dot<R>(st, c2, CLcut, eR, 1, parts, res + 1));           // tr rho_L^2
+  PO(env_dot<R>(st, c2, CR, eLcut, 1, parts, res + 2));           // tr rho_R^2
+  PO(env_dot<R>(st, c2, eLcut, eR, 0, parts, res + 3));           // tr rho
+  double hres[4];
+  CK(cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, st));
+  // the diagonal env ends as the 1 x 1 sum_x <x|rho|x>^2
+  T cd;
+  CK(cudaMemcpyAsync(&cd, CD, sizeof(T), cudaMemcpyDeviceToHost, st));
+  CK(sync_stream(h));
+  prof_drain(h);
+  for (int a = 0; a < 4; ++a) out[a] = hres[a];
+  out[4] = (double)cd.x;
+  return MPDO_OK;
+}
+
 template <typename R>
 int sample(mpdo_ctx* h, int ns, uint64_t seed, uint8_t* bits, double* probs) {
   using T = cx<R>;
@@ -1455,6 +1592,28 @@ int mpdo_sample_probs(mpdo_t h, int n_samples, uint64_t seed, uint8_t* bits, dou
   if (n_samples == 0) return MPDO_OK;
   return h->dbl ? sample<double>(h, n_samples, seed, bits, probs)
                 : sample<float>(h, n_samples, seed, bits, probs);
+}
+
+int mpdo_expect_second_order(mpdo_t h, int cut, double* xi, double* collision, double* s2_left,
+                             double* s2_right, double* i2) {
+  if (!h) return fail(nullptr, MPDO_ERR_ARG, "null handle");
+  if (cut < 1 || cut > h->n - 1) return fail(h, MPDO_ERR_ARG, "cut must be within 1..N-1");
+  // storage coordinates: a mirrored chain swaps the halves
+  const int sc = h->rev ? h->n - cut : cut;
+  double r[5];
+  int rc = h->dbl ? second_order<double>(h, sc, r) : second_order<float>(h, sc, r);
+  if (rc) return rc;
+  const double tr2 = r[3] * r[3];
+  if (!(tr2 > 0) || !std::isfinite(tr2) || !(r[0] > 0) || !(r[1] > 0) || !(r[2] > 0))
+    return fail(h, MPDO_ERR_NUMERIC, "non-positive second-order contraction");
+  const double pl = h->rev ? r[2] : r[1], pr = h->rev ? r[1] : r[2];
+  const double s2 = -std::log(r[0] / tr2), sl = -std::log(pl / tr2), sr = -std::log(pr / tr2);
+  if (xi) *xi = r[0] / tr2;
+  if (collision) *collision = r[4] / tr2;
+  if (s2_left) *s2_left = sl;
+  if (s2_right) *s2_right = sr;
+  if (i2) *i2 = sl + sr - s2;
+  return MPDO_OK;
 }
 
 int mpdo_reconfigure(mpdo_t h, int n_sites, int chi_max, int k_max, int use_ppt,

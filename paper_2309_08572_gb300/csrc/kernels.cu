@@ -399,6 +399,89 @@ __global__ void sumsq_kernel(long n, const cx<R>* __restrict__ a, double* out) {
   if (threadIdx.x == 0) *out = red[0];
 }
 
+// out = in with its 6 axes reordered: out axis i is in axis perm[i] (dims of in: d[0..5]).
+template <typename T>
+__global__ void permute6_kernel(const T* __restrict__ in, T* __restrict__ out, int d0, int d1,
+                                int d2, int d3, int d4, int d5, int p0, int p1, int p2, int p3,
+                                int p4, int p5) {
+  const int d[6] = {d0, d1, d2, d3, d4, d5};
+  const int p[6] = {p0, p1, p2, p3, p4, p5};
+  long st[6];
+  st[5] = 1;
+  for (int i = 4; i >= 0; --i) st[i] = st[i + 1] * d[i + 1];
+  const long total = st[0] * d[0];
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long rem = e, off = 0;
+    for (int i = 5; i >= 0; --i) {
+      const int od = d[p[i]];
+      const long idx = rem % od;
+      rem /= od;
+      off += idx * st[p[i]];
+    }
+    out[e] = in[off];
+  }
+}
+
+// R[(a,b)][s][s'][(r,r')] (a, b < dl; s, s' < 3; r, r' < dr): mode 0 keeps it, mode 1 zeroes
+// the blocks s != s' (the diagonal transfer of the collision probability), mode 2 writes the
+// trace over s into tr[(a,b)][(r,r')] instead.
+template <typename T>
+__global__ void rho_site_kernel(long dl2, long dr2, T* r, T* tr, int mode) {
+  const long total = dl2 * 9 * dr2;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long q = e % dr2, ss = (e / dr2) % 9, ab = e / (9 * dr2);
+    const int s = (int)(ss / 3), s2 = (int)(ss % 3);
+    if (mode == 1) {
+      if (s != s2) { r[e].x = 0; r[e].y = 0; }
+    } else if (mode == 2 && s == 0 && s2 == 0) {
+      T v = r[e];
+      const T v1 = r[e + 4 * dr2], v2 = r[e + 8 * dr2];
+      v.x += v1.x + v2.x;
+      v.y += v1.y + v2.y;
+      tr[ab * dr2 + q] = v;
+    }
+  }
+}
+
+// Deterministic FP64 contractions of environments into parts[blockIdx]: mode 0:
+// sum_e Re(x[e] y[e]); mode 1: sum_{(ab),(cd)} Re(c[(ab),(cd)] u[ab] u[cd]) with n2 = dim of
+// (ab).  A second pass (one CTA) adds the parts in order.
+template <typename T>
+__global__ void __launch_bounds__(256) env_dot_kernel(long n2, const T* __restrict__ x,
+                                                      const T* __restrict__ y, int mode,
+                                                      double* parts) {
+  __shared__ double red[256];
+  double t = 0;
+  const long total = mode == 0 ? n2 : n2 * n2;
+  for (long e = blockIdx.x * 256L + threadIdx.x; e < total; e += 256L * gridDim.x) {
+    if (mode == 0) {
+      t += (double)x[e].x * y[e].x - (double)x[e].y * y[e].y;
+    } else {
+      const long i = e / n2, j = e % n2;
+      // c[(ab),(cd)] u[ab] u[cd]
+      const double ur = (double)y[i].x * y[j].x - (double)y[i].y * y[j].y;
+      const double ui = (double)y[i].x * y[j].y + (double)y[i].y * y[j].x;
+      t += (double)x[e].x * ur - (double)x[e].y * ui;
+    }
+  }
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) parts[blockIdx.x] = red[0];
+}
+__global__ void sum_parts_kernel(int n, const double* parts, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0;
+    for (int i = 0; i < n; ++i) s += parts[i];
+    *out = s;
+  }
+}
+
 // Vks[kappa][k] = V[kappa][k] * f[k], k < kk (V has leading dimension ldv)
 template <typename R, typename RO>
 __global__ void scale_vk_kernel(int n, int kk, const cx<R>* __restrict__ v, long ldv,
@@ -807,6 +890,31 @@ cudaError_t trace_pre(cudaStream_t st, int dm, const cx<R>* gi, const cx<R>* gj,
   trace_pre_kernel<R><<<1, 256, 0, st>>>(dm, gi, gj, sc);
   return cudaGetLastError();
 }
+template <typename T>
+cudaError_t permute6(cudaStream_t st, const int* d, const int* p, const T* in, T* out) {
+  long total = 1;
+  for (int i = 0; i < 6; ++i) total *= d[i];
+  count_launch();
+  permute6_kernel<T><<<nblocks(total), 256, 0, st>>>(in, out, d[0], d[1], d[2], d[3], d[4], d[5],
+                                                     p[0], p[1], p[2], p[3], p[4], p[5]);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t rho_site(cudaStream_t st, long dl2, long dr2, cx<R>* r, cx<R>* tr, int mode) {
+  count_launch();
+  rho_site_kernel<cx<R>><<<nblocks(dl2 * 9 * dr2), 256, 0, st>>>(dl2, dr2, r, tr, mode);
+  return cudaGetLastError();
+}
+constexpr int kDotBlocks = 64;
+template <typename R>
+cudaError_t env_dot(cudaStream_t st, long n2, const cx<R>* x, const cx<R>* y, int mode,
+                    double* parts, double* out) {
+  count_launch(2);
+  env_dot_kernel<cx<R>><<<kDotBlocks, 256, 0, st>>>(n2, x, y, mode, parts);
+  sum_parts_kernel<<<1, 32, 0, st>>>(kDotBlocks, parts, out);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t sumsq(cudaStream_t st, long n, const cx<R>* a, double* out) {
   count_launch();
@@ -913,6 +1021,11 @@ template cudaError_t lift<float>(cudaStream_t, int, const float2*, const double*
                                     StepScalars*);                                           \
   template cudaError_t polar_factors<R>(cudaStream_t, int, const cx<R>*, cx<R>*, cx<R>*);   \
   template cudaError_t sumsq<R>(cudaStream_t, long, const cx<R>*, double*);                 \
+  template cudaError_t permute6<cx<R>>(cudaStream_t, const int*, const int*, const cx<R>*,    \
+                                       cx<R>*);                                              \
+  template cudaError_t rho_site<R>(cudaStream_t, long, long, cx<R>*, cx<R>*, int);           \
+  template cudaError_t env_dot<R>(cudaStream_t, long, const cx<R>*, const cx<R>*, int,       \
+                                  double*, double*);                                          \
   template cudaError_t sample_pick<R>(cudaStream_t, int, int, const cx<R>*, const cx<R>*,   \
                                       uint64_t, int, int, int, cx<R>*, uint8_t*, double*, int);
 INST(double)

@@ -55,6 +55,18 @@ cudaError_t pchol(cudaStream_t st, int n, const cx<R>* w, int rmax, double tol, 
 // zs = z diag(s^-1/2) (r x r)
 template <typename R>
 cudaError_t lift(cudaStream_t st, int r, const cx<R>* z, const double* s, cx<R>* zs);
+// out = in with its 6 axes reordered (out axis i = in axis p[i]; in dims d[0..5], host arrays)
+template <typename T>
+cudaError_t permute6(cudaStream_t st, const int* d, const int* p, const T* in, T* out);
+// r = R[(a,b)][s][s'][(r,r')] of one site: mode 1 zeroes the s != s' blocks; mode 2 writes
+// sum_s R[(a,b)][s][s][(r,r')] into tr
+template <typename R>
+cudaError_t rho_site(cudaStream_t st, long dl2, long dr2, cx<R>* r, cx<R>* tr, int mode);
+// *out (device) = sum Re(x y) over n2 entries (mode 0), or sum_{i,j} Re(x[i][j] y[i] y[j])
+// over n2 x n2 (mode 1), in FP64 with a fixed summation order; parts: 64 doubles of scratch
+template <typename R>
+cudaError_t env_dot(cudaStream_t st, long n2, const cx<R>* x, const cx<R>* y, int mode,
+                    double* parts, double* out);
 // out (device double) = sum of |a|^2 over n complex entries, accumulated in FP64
 template <typename R>
 cudaError_t sumsq(cudaStream_t st, long n, const cx<R>* a, double* out);

@@ -12,6 +12,7 @@
 // Weights are stored [fan_in][fan_out] row-major, one flat FP32 array W_0 b_0 W_1 b_1 ...
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <string>
@@ -19,6 +20,7 @@
 
 #include "../../include/mpdo.h"
 #include "common.cuh"
+#include "tcgemm.h"
 
 namespace mpdo {
 void set_global_error(const char* msg);
@@ -160,6 +162,11 @@ struct mpdo_mlp_s {
   int t = 0;
   int maxw = 0;
   std::string err;
+  // BF16 tensor-core products (mpdo_mlp_set_precision): packed operands and the pipeline's
+  // error flag; the parameters, gradients and Adam moments stay FP32
+  int tc = 0;
+  void *pa = nullptr, *pb = nullptr;
+  int* tcerr = nullptr;
 };
 
 namespace {
@@ -176,10 +183,36 @@ int mlp_fail(mpdo_mlp m, int code, const std::string& msg) {
     if (_e != cudaSuccess) return mlp_fail(m, MPDO_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
   } while (0)
 
-cudaError_t sgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, const float* A, long lda,
+__global__ void add_bias_kernel(int M, int N, float* C, long ldc, const float* __restrict__ bias) {
+  const long total = (long)M * N;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x)
+    C[(e / N) * ldc + e % N] += bias[e % N];
+}
+
+// C = op(A) op(B) (+ bias per column), A is M x K after op, B is K x N after op.  FP32 on the
+// CUDA cores, or (m->tc) BF16 operands on the tensor cores with FP32 accumulation: op(A) and
+// op(B)^T are packed K-major in BF16 and multiplied by the tcgen05 core.
+cudaError_t sgemm(mpdo_mlp m, bool ta, bool tb, int M, int N, int K, const float* A, long lda,
                   const float* B, long ldb, float* C, long ldc, const float* bias) {
+  cudaStream_t st = m->st;
   long sam = ta ? 1 : lda, sak = ta ? lda : 1;
   long sbk = tb ? 1 : ldb, sbn = tb ? ldb : 1;
+  if (m->tc && M > 0 && N > 0 && K > 0) {
+    const long ldk = (K + 7) / 8 * 8;   // 16-byte rows
+    MPDO_CUDA_TRY(mpdo::tc_pack_real_bf16(st, M, K, A, sam, sak, m->pa, ldk));
+    MPDO_CUDA_TRY(mpdo::tc_pack_real_bf16(st, N, K, B, sbn, sbk, m->pb, ldk));
+    mpdo::TcEpilogue e;
+    e.d = C;
+    e.ldd = ldc;
+    MPDO_CUDA_TRY(mpdo::tc_gemm_real(st, 2, M, N, K, m->pa, ldk, 0, m->pb, ldk, 0, 1, e,
+                                     m->tcerr, 0));
+    if (bias) {
+      mpdo::count_launch();
+      add_bias_kernel<<<nb((long)M * N), 256, 0, st>>>(M, N, C, ldc, bias);
+    }
+    return cudaGetLastError();
+  }
   dim3 grid((N + SBN - 1) / SBN, (M + SBM - 1) / SBM);
   mpdo::count_launch();
   sgemm_kernel<<<grid, SNT, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias);
@@ -190,7 +223,7 @@ cudaError_t sgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, const 
 int run_forward(mpdo_mlp m, int batch) {
   const int L = (int)m->w.size() - 1;
   for (int l = 0; l < L; ++l) {
-    MK(sgemm(m->st, false, false, batch, m->w[l + 1], m->w[l], m->acts[l], m->w[l],
+    MK(sgemm(m, false, false, batch, m->w[l + 1], m->w[l], m->acts[l], m->w[l],
              m->params + m->woff[l], m->w[l + 1], m->acts[l + 1], m->w[l + 1],
              m->params + m->boff[l]));
     if (l < L - 1) {
@@ -218,14 +251,14 @@ int run_backward(mpdo_mlp m, int batch, bool want_params) {
     }
     if (want_params) {
       // dW = a_{l-1}^T dz  (fi x fo), db = colsum(dz)
-      MK(sgemm(m->st, true, false, fi, fo, batch, m->acts[l], fi, cur, fo, m->grads + m->woff[l],
+      MK(sgemm(m, true, false, fi, fo, batch, m->acts[l], fi, cur, fo, m->grads + m->woff[l],
                fo, nullptr));
       mpdo::count_launch();
       colsum_kernel<<<(fo + 127) / 128, 128, 0, m->st>>>(batch, fo, cur, m->grads + m->boff[l]);
       MK(cudaGetLastError());
     }
     // da_{l-1} = dz W^T  (batch x fi)
-    MK(sgemm(m->st, false, true, batch, fi, fo, cur, fo, m->params + m->woff[l], fo, nxt, fi,
+    MK(sgemm(m, false, true, batch, fi, fo, cur, fo, m->params + m->woff[l], fo, nxt, fi,
              nullptr));
     std::swap(cur, nxt);
   }
@@ -338,7 +371,10 @@ int mpdo_mlp_loss_grad(mpdo_mlp m, int batch, const float* x, const float* t, fl
   if (rc) return rc;
   MK(cudaMemcpyAsync(m->hpart, m->part, sizeof(double) * blocks, cudaMemcpyDeviceToHost, m->st));
   if (grad_host) MK(cudaMemcpyAsync(grad_host, m->grads, sizeof(float) * m->n_params, cudaMemcpyDeviceToHost, m->st));
+  if (m->tc) MK(cudaMemcpyAsync(m->hpart + 4095, m->tcerr, sizeof(int), cudaMemcpyDeviceToHost, m->st));
   MK(cudaStreamSynchronize(m->st));
+  if (m->tc && *reinterpret_cast<int*>(m->hpart + 4095))
+    return mlp_fail(m, MPDO_ERR_TIMEOUT, "mlp: a tensor-core pipeline wait gave up");
   double s = 0;
   for (int b = 0; b < blocks; ++b) s += m->hpart[b];
   if (loss) *loss = (float)(s / (double)n);
@@ -376,9 +412,29 @@ int mpdo_mlp_input_grad(mpdo_mlp m, int batch, const float* x, const float* wout
   return MPDO_OK;
 }
 
+int mpdo_mlp_set_precision(mpdo_mlp m, int mode) {
+  if (!m || (mode != 0 && mode != 1)) return mlp_fail(m, MPDO_ERR_ARG, "mlp: precision mode must be 0 or 1");
+  MK(cudaStreamSynchronize(m->st));
+  if (mode == 1 && !m->pa) {
+    const long r = std::max(m->max_batch, m->maxw), ldk = (r + 7) / 8 * 8;
+    const size_t bytes = (size_t)r * ldk * 2;
+    if (cudaMalloc(&m->pa, bytes) != cudaSuccess || cudaMalloc(&m->pb, bytes) != cudaSuccess ||
+        cudaMalloc(&m->tcerr, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return mlp_fail(m, MPDO_ERR_OOM, "mlp: tensor-core operand buffers");
+    }
+    MK(cudaMemsetAsync(m->tcerr, 0, sizeof(int), m->st));
+  }
+  m->tc = mode;
+  return MPDO_OK;
+}
+
 int mpdo_mlp_destroy(mpdo_mlp m) {
   if (!m) return MPDO_OK;
   if (m->st) cudaStreamSynchronize(m->st);
+  if (m->pa) cudaFree(m->pa);
+  if (m->pb) cudaFree(m->pb);
+  if (m->tcerr) cudaFree(m->tcerr);
   for (float* p : m->acts) if (p) cudaFree(p);
   if (m->params) cudaFree(m->params);
   if (m->grads) cudaFree(m->grads);

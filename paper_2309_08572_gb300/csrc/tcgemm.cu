@@ -700,6 +700,29 @@ __global__ void zero_tails_kernel(long rows_out, int kr, int ldk, __nv_bfloat16*
   }
 }
 
+// Real operand packing for the BF16 core: out[r][c] = bf16(src[r*s_r + c*s_c]), r < rows,
+// c < kc (row stride ldo elements); tiled through shared memory so that both the read and
+// the write are coalesced whichever index is contiguous in the source.
+__global__ void __launch_bounds__(PT * 8)
+    pack_real_bf16_kernel(int rows, int kc, const float* __restrict__ src, long s_r, long s_c,
+                          __nv_bfloat16* __restrict__ out, long ldo) {
+  __shared__ float tile[PT][PT + 1];
+  const int r0 = blockIdx.y * PT, c0 = blockIdx.x * PT;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool c_fast = (s_c == 1);
+  for (int q = ty; q < PT; q += 8) {
+    const int r = c_fast ? r0 + q : r0 + tx;
+    const int c = c_fast ? c0 + tx : c0 + q;
+    const float v = (r < rows && c < kc) ? src[(long)r * s_r + (long)c * s_c] : 0.f;
+    if (c_fast) tile[q][tx] = v; else tile[tx][q] = v;
+  }
+  __syncthreads();
+  for (int q = ty; q < PT; q += 8) {
+    const int r = r0 + q, c = c0 + tx;
+    if (r < rows && c < kc) out[(long)r * ldo + c] = __float2bfloat16_rn(tile[q][tx]);
+  }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -948,6 +971,16 @@ cudaError_t tc_cgemm_exact(cudaStream_t st, int opa, int opb, int m, int n, int 
     MPDO_CUDA_TRY(cudaGetLastError());
   }
   return cudaSuccess;
+}
+
+cudaError_t tc_pack_real_bf16(cudaStream_t st, int rows, int kc, const float* src, long s_r,
+                              long s_c, void* out, long ldo) {
+  if (rows <= 0 || kc <= 0) return cudaSuccess;
+  dim3 grid((kc + PT - 1) / PT, (rows + PT - 1) / PT), block(PT, 8);
+  pack_real_bf16_kernel<<<grid, block, 0, st>>>(rows, kc, src, s_r, s_c,
+                                                static_cast<__nv_bfloat16*>(out), ldo);
+  count_launch();
+  return cudaGetLastError();
 }
 
 template cudaError_t tc_cgemm_exact<float2, float2>(cudaStream_t, int, int, int, int, int,

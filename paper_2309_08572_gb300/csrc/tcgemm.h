@@ -63,4 +63,9 @@ cudaError_t tc_cgemm_exact(cudaStream_t st, int opa, int opb, int m, int n, int 
                            long sc, int batch, void* ws, size_t ws_bytes, int* err);
 size_t tc_exact_ws_bytes(long m, long n, long k, int batch);
 
+// out[r][c] = bf16(src[r*s_r + c*s_c]) for r < rows, c < kc (row stride ldo elements): the
+// K-major BF16 operands of tc_gemm_real from a real FP32 matrix in either orientation.
+cudaError_t tc_pack_real_bf16(cudaStream_t st, int rows, int kc, const float* src, long s_r,
+                              long s_c, void* out, long ldo);
+
 }  // namespace mpdo

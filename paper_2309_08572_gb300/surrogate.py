@@ -76,10 +76,12 @@ def simulate(circuits: Sequence, pool: List[Mpdo]) -> np.ndarray:
     return np.stack([out[:, 1] / n, out[:, 2]], axis=1)
 
 
-def make_net(n_in: int, max_batch: int, seed: int) -> Mlp:
+def make_net(n_in: int, max_batch: int, seed: int, bf16: bool = True) -> Mlp:
+    """The 4-layer, width-256 network; bf16: its products on the tensor cores with BF16
+    operands (FP32 accumulation, FP32 master parameters and Adam moments)."""
     rng = np.random.default_rng(seed)
     widths = [n_in, WIDTH, WIDTH, WIDTH, 2]
-    net = Mlp(widths, max_batch=max_batch)
+    net = Mlp(widths, max_batch=max_batch, bf16=bf16)
     flat = []
     for a, b in zip(widths[:-1], widths[1:]):
         flat.append((rng.standard_normal((a, b)) / np.sqrt(a)).reshape(-1))

@@ -384,3 +384,30 @@ def test_chain100_mixed_at_a4_cut_matches_oracle(lib, prec):
     # floor itself may fall either side)
     assert abs(max(b) - max(ob)) <= 3
     g.close()
+
+
+# Second-order observables (Sec. III.E): the library's two-copy environments against the
+# oracle's (pinned to the dense definitions) on the same circuits.  FP64 sites: 1e-10
+# relative; complex64 sites (environments in FP32, FP64 final sums): 1e-4 relative on xi and
+# the collision probability, 1e-4 absolute on the entropies and the mutual information.
+@pytest.mark.parametrize("prec", ["fp64", "c64"])
+@pytest.mark.parametrize("case", ["tiny", "n10c12k4"])
+def test_second_order_matches_oracle(lib, prec, case):
+    from oracle import second_order as so
+    if case == "tiny":
+        c = dataclasses.replace(synth.tiny(), k_max=40)
+    else:
+        c = synth.scaled(synth.chain40(), n_sites=10, chi_max=12, k_max=4)
+    ref, _ = _oracle(c)
+    g, _, _ = _gpu(lib, c, prec)
+    for cut in (1, c.n_sites // 2, c.n_sites - 1):
+        got = g.second_order(cut)
+        want = so.second_order(ref, cut)
+        print(prec, case, cut, {k: (got[k], want[k]) for k in want})
+        for key in ("xi", "collision"):
+            tol = 1e-10 if prec == "fp64" else 1e-4
+            assert abs(got[key] - want[key]) < tol * abs(want[key]), (cut, key)
+        for key in ("s2_left", "s2_right", "i2"):
+            tol = 1e-9 if prec == "fp64" else 1e-4
+            assert abs(got[key] - want[key]) < tol, (cut, key)
+    g.close()
