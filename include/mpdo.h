@@ -258,6 +258,19 @@ int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double beta, double 
                           double bd, double eta, int* sites, int* ms, double* out,
                           size_t cap);
 
+/* Random-circuit layer k (0-based) of the paper's RCS workload (Sec. IV, Figs. 4 and 5 a-c):
+ * a Haar one-qubit gate on every atom, then a noisy CZ on the bonds (i, i+1) with
+ * i = k mod 2 (brickwork), written as one sweep of n_sites-1 two-site ops (left to right for
+ * even k, right to left for odd k): CZ bonds get the G0 channel (crosstalk phase
+ * exp(-i xtalk_phase n_r n_r), ideal CZ |11> -> -|11>, post-promotion, one unit of decay and
+ * dephasing on both atoms), the other bonds a one-Kraus unitary; each atom's gate is folded
+ * into the first op that touches it.  haar: host complex128 [n_sites][2][2] (qubit levels;
+ * |r> is left alone).  Outputs as for mpdo_build_qaoa_layer. */
+int mpdo_build_rcs_layer(int n_sites, int k, const double* haar, double gamma_diss,
+                         double gamma_deph, double xtalk_phase, double delta_pp, double b0,
+                         double b1, double bd, double eta, int* sites, int* ms, double* out,
+                         size_t cap);
+
 /* Gate model G1: the pulse-level CZ channel (Sec. II, Eqs. LME_Hamiltonian,
  * LME_Single_Site, LME; Fig. 1 caption; integrated into one channel as in Sec. III.A).
  * Two atoms under H_p = H_1 (x) I + I (x) H_2 + B|rr><rr|, H_i = Omega(t)/2 (|r><1| + h.c.)

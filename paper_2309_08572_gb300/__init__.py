@@ -115,6 +115,7 @@ def _load():
                                          C.c_size_t]),
         "mpdo_build_qaoa_layer": (I, [I, I, D, D, D, D, D, D, D, D, D, D, D, D, P(I), P(I),
                                       P(D), S]),
+        "mpdo_build_rcs_layer": (I, [I, I, P(D), D, D, D, D, D, D, D, D, P(I), P(I), P(D), S]),
         "mpdo_kernel_launches": (C.c_longlong, []),
         "mpdo_profile": (I, [VP, I]),
         "mpdo_profile_read": (I, [VP, I, P(D), P(C.c_longlong), P(D)]),
@@ -253,8 +254,38 @@ def build_qaoa_layer_cz(n_sites: int, k: int, alpha: float, beta: float, cz_supe
     return ops
 
 
+def build_rcs_layer(n_sites: int, k: int, haar, gamma_diss: float = 0.0,
+                    gamma_deph: float = 0.0, xtalk_phase: float = 0.0, delta_pp: float = 0.0,
+                    b0: float = 1 / 16, b1: float = 1 / 16, bd: float = 7 / 8,
+                    eta: float = 1e-15):
+    """Ordered two-site ops [(site, Kraus (M,9,9))] of random-circuit layer k (library
+    builder); haar: (n_sites, 2, 2) complex one-qubit gates of the layer."""
+    nops = n_sites - 1
+    sites = np.zeros(nops, dtype=np.int32)
+    ms = np.zeros(nops, dtype=np.int32)
+    cap = nops * 81 * 81
+    out = np.zeros((cap, 2))
+    h = np.ascontiguousarray(np.asarray(haar, dtype=complex).reshape(n_sites, 2, 2)).view(float)
+    rc = LIB.mpdo_build_rcs_layer(n_sites, k, _dptr(h.reshape(-1)), gamma_diss, gamma_deph,
+                                  xtalk_phase, delta_pp, b0, b1, bd, eta,
+                                  sites.ctypes.data_as(C.POINTER(C.c_int)),
+                                  ms.ctypes.data_as(C.POINTER(C.c_int)), _dptr(out), cap)
+    _check(rc)
+    flat = out.view(complex).reshape(-1)
+    ops, off = [], 0
+    for s_, m in zip(sites, ms):
+        ops.append((int(s_), flat[off: off + m * 81].reshape(m, 9, 9).copy()))
+        off += m * 81
+    return ops
+
+
 def circuit_layers(c) -> List[list]:
-    """Library-built op lists for every layer of a workload description (synth.Circuit)."""
+    """Library-built op lists for every layer of a workload description (synth.Circuit, or
+    synth.RcsCircuit for the random circuits)."""
+    if hasattr(c, "haar"):
+        return [build_rcs_layer(c.n_sites, k, c.haar[k], c.gamma_diss, c.gamma_deph,
+                                c.xtalk_phase, c.delta_pp, c.b0, c.b1, c.bd)
+                for k in range(c.depth)]
     return [build_qaoa_layer(c.n_sites, k, c.alpha[k], c.beta[k], c.J, c.bz, c.gamma_diss,
                              c.gamma_deph, c.xtalk_phase, c.delta_pp, c.b0, c.b1, c.bd)
             for k in range(c.p)]

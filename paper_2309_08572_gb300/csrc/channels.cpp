@@ -434,6 +434,71 @@ extern "C" int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double be
   return MPDO_OK;
 }
 
+// Random-circuit layer (the paper's RCS workload, Sec. IV / Figs. 4-5): one sweep over the
+// bonds (left to right for even k, right to left for odd k); bond i carries a noisy CZ when
+// i = k mod 2 (gate model G0: crosstalk phase, ideal CZ, post-promotion, one unit of decay and
+// dephasing on both atoms), otherwise only one-atom gates; every atom's Haar gate (2 x 2 on the
+// qubit levels, |r> untouched) is folded into the first op of the sweep that touches it.
+extern "C" int mpdo_build_rcs_layer(int n_sites, int k, const double* haar, double gamma_diss,
+                                    double gamma_deph, double xtalk_phase, double delta_pp,
+                                    double b0, double b1, double bd, double eta, int* sites,
+                                    int* ms, double* out, size_t cap) {
+  if (n_sites < 2 || k < 0 || !haar || !sites || !ms || !out) return MPDO_ERR_ARG;
+  if (!finite_all({gamma_diss, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd, eta}))
+    return MPDO_ERR_NUMERIC;
+  if (gamma_diss < 0 || gamma_deph < 0 || b0 < 0 || b1 < 0 || bd < 0 || eta < 0)
+    return MPDO_ERR_ARG;
+  std::vector<Mat> gates(n_sites);
+  for (int j = 0; j < n_sites; ++j) {
+    Mat g = eye(3);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        const double* p = haar + 2 * (4 * j + 2 * a + b);
+        if (!std::isfinite(p[0]) || !std::isfinite(p[1])) return MPDO_ERR_NUMERIC;
+        g[a * 3 + b] = zc(p[0], p[1]);
+      }
+    gates[j] = g;
+  }
+  const bool ltr = (k % 2 == 0);
+  std::vector<bool> seen(n_sites, false);
+  Mat cz = eye(9);
+  cz[4 * 9 + 4] = -1.0;
+  size_t off = 0;
+  for (int q = 0; q < n_sites - 1; ++q) {
+    const int i = ltr ? q : n_sites - 2 - q;
+    Mat pl = seen[i] ? eye(3) : gates[i];
+    Mat pr = seen[i + 1] ? eye(3) : gates[i + 1];
+    seen[i] = seen[i + 1] = true;
+    Mat pre = kron(pl, 3, pr, 3);
+    std::vector<Mat> ch;
+    if (i % 2 == k % 2) {
+      Mat u = cz;
+      if (xtalk_phase != 0.0) u = matmul(u, expmh(xtalk_phase, kron(nr(), 3, nr(), 3), 9), 9);
+      u = matmul(u, pre, 9);
+      if (delta_pp != 0.0) {
+        Mat pp = expmh(delta_pp, op3({0, 0, 0, 0, 0, 1, 0, 1, 0}), 3);
+        u = matmul(kron(pp, 3, pp, 3), u, 9);
+      }
+      Mat s = matmul(two_site_product(noise_superop(gamma_diss, gamma_deph, b0, b1)),
+                     unitary_superop(u, 9), 81);
+      int rc = kraus_from_superop(s, 9, eta, ch);
+      if (rc) return rc;
+    } else {
+      ch.push_back(pre);
+    }
+    sites[q] = i;
+    ms[q] = (int)ch.size();
+    if (off + ch.size() * 81 > cap) return MPDO_ERR_ARG;
+    for (const Mat& e : ch)
+      for (int a = 0; a < 81; ++a) {
+        out[2 * off] = e[a].real();
+        out[2 * off + 1] = e[a].imag();
+        ++off;
+      }
+  }
+  return MPDO_OK;
+}
+
 extern "C" int mpdo_build_cz_pulse(const mpdo_pulse* pulse, double gamma_diss,
                                    double gamma_deph, double b0, double b1, int n_steps,
                                    double* superop, double* phi1, double* infidelity) {

@@ -13,6 +13,10 @@ build is measured on:
   chain40   N=40,  p=2, chi=64,  K=8,  decay 0.005, dephasing 0.005, crosstalk 0.01 rad
   chain100  N=100, p=3, chi=256, K=16, same noise as chain40 (precision form)
   chain100deep  the same chain with p=8 layers (bond dimension reaches chi=256)
+  rcs8 / rcs12  random circuits: a Haar-random one-qubit gate on every atom, then noisy CZs on
+            alternating bonds (brickwork), per layer; 8 sites, depth 40, chi=32 (Fig. 5 a-c) and
+            12 sites, depth 20, chi=64, K=4 (Fig. 4), Rydberg decay 0.001 per CZ, post-promotion
+            0.01 rad
   batch512  512 circuits, N~U{20..100}, chi in {32,64,128}, K=8, p in {1,2},
             decay/dephasing log-uniform in [1e-4, 1e-2]
   surrogate MLP 4x256 trained on batch512-style samples
@@ -140,3 +144,50 @@ def random_site_tensors(seed: int, dims_left, d: int, kdims, dims_right):
 def philox_key(seed: int):
     """The 64-bit sampling seed split into the two 32-bit Philox key words."""
     return (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+
+
+def haar_u2(rng: np.random.Generator) -> np.ndarray:
+    """A Haar-random 2 x 2 unitary: QR of a complex Gaussian matrix with the phases of R's
+    diagonal moved into Q (Mezzadri, Notices AMS 54, 2007).  An input draw, like the angles."""
+    z = (rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))) / np.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diag(r)
+    return q * (d / np.abs(d))[None, :]
+
+
+@dataclasses.dataclass
+class RcsCircuit:
+    """Random circuit on a chain of three-level atoms: per layer a Haar one-qubit gate on
+    every atom (acting on the qubit levels, |r> untouched), then CZ channels on the bonds
+    (i, i+1) with i = layer mod 2 (brickwork)."""
+    n_sites: int
+    depth: int
+    haar: np.ndarray             # (depth, n_sites, 2, 2) complex
+    gamma_diss: float = 0.001
+    gamma_deph: float = 0.0
+    xtalk_phase: float = 0.0
+    delta_pp: float = 0.0
+    b0: float = 1.0 / 16
+    b1: float = 1.0 / 16
+    bd: float = 7.0 / 8
+    chi_max: int = 32
+    k_max: int = 4
+    seed: int = 0
+
+
+def rcs(n_sites: int, depth: int, chi_max: int, k_max: int, gamma_diss: float = 0.001,
+        seed: int = 5, delta_pp: float = 0.0) -> RcsCircuit:
+    rng = rng_for(seed)
+    haar = np.stack([np.stack([haar_u2(rng) for _ in range(n_sites)]) for _ in range(depth)])
+    return RcsCircuit(n_sites=n_sites, depth=depth, haar=haar, gamma_diss=gamma_diss,
+                      delta_pp=delta_pp, chi_max=chi_max, k_max=k_max, seed=seed)
+
+
+def rcs8(seed: int = 5) -> RcsCircuit:
+    # post-promotion 0.01 rad, as in the chain workloads: in the gate-level model decay acts
+    # only on Rydberg population, which the ideal CZ alone never leaves behind
+    return rcs(8, 40, 32, 4, seed=seed, delta_pp=0.01)
+
+
+def rcs12(seed: int = 6) -> RcsCircuit:
+    return rcs(12, 20, 64, 4, seed=seed, delta_pp=0.01)

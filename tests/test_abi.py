@@ -204,3 +204,18 @@ def test_forced_oom_through_the_alloc_hook(pkg):
     assert rc == -2 and not h.value
     assert calls["alloc"] == 1 and calls["free"] == 0
     assert b"allocation" in pkg.LIB.mpdo_last_error(None)
+
+
+def test_rcs_layer_ops_match_oracle(pkg):
+    """The library's random-circuit layers equal the oracle's op by op (same bonds, same
+    channel superoperators), in both sweep directions."""
+    from oracle import rcs as orcs
+    c = synth.rcs(6, 2, 16, 4, gamma_diss=0.01, delta_pp=0.05)
+    c.xtalk_phase = 0.02
+    for k in range(c.depth):
+        lib_ops = pkg.build_rcs_layer(c.n_sites, k, c.haar[k], c.gamma_diss, c.gamma_deph,
+                                      c.xtalk_phase, c.delta_pp)
+        or_ops = orcs.layer_ops(c, k)
+        assert [i for i, _ in lib_ops] == [i for i, _ in or_ops]
+        for (_, a), (_, b) in zip(lib_ops, or_ops):
+            assert np.abs(oops.superop(a) - oops.superop(b)).max() < 1e-13

