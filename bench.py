@@ -6,7 +6,7 @@ chi = 256, K = 16, Rydberg decay 0.005 and dephasing 0.005 per block, crosstalk 
 0.01 rad, post-promotion 0.01 rad, seeded angles (seed 3).  One circuit = reset to |+>^N,
 the 3 layers (297 two-site updates: Gram contractions, eigensolves, split, Kraus truncation
 with PPT) and the TFIM energy / success probability.  The bond cut is reading A4's for the
-reduced-precision modes, s > 1e-7 s_max, applied at each mode's numerical floor (mixed form:
+reduced-precision modes, s > 1e-7 s_max, applied at each mode's numerical floor (mixed forms:
 lambda = s^2 > 1e-13 lambda_max, i.e. s > 3.2e-7 s_max); at that cut three layers take the bond
 dimension to D = 33, which the line reports (chi_used_max, mean D).  "chain100deep" runs the
 same chain with p = 8 layers, where D reaches chi = 256.
@@ -110,8 +110,11 @@ PREC_DESC = {
     "mixed": "mixed: complex64 site tensors and large contractions (FP32), Gram matrices with "
              "FP64 products and sums, FP32 Jacobi sweeps with FP64 refinement, FP64 cuts, PPT, "
              "trace and observables",
-    "mixed-tc": "mixed with the FP32 contractions (new centre, inner isometry) on the tensor "
-                "cores in TF32x3 split precision (tcgen05, FP32 accumulation); FP64 Grams",
+    "mixed-tc": "mixed-tc: complex64 site tensors; the FP32 contractions (new centre, inner "
+                "isometry) on the tensor cores in TF32x3 split precision (tcgen05, FP32 "
+                "accumulation); the Grams and other FP64 products as exact BF16 slice products "
+                "on the tensor cores summed in FP64; FP32 Jacobi sweeps with FP64 refinement; "
+                "FP64 cuts, PPT, trace and observables",
     "c64": "complex64 throughout (FP32 Grams and Jacobi), FP64 scalars and observables",
     "tf32x3": "complex64 with every large product (Grams included) on the tensor cores in "
               "TF32x3 split precision (tcgen05, FP32 accumulation), FP32 Jacobi",
@@ -467,7 +470,7 @@ def run_ours(args):
     # single-circuit latency, bond dimensions reached and kernel-class breakdown (untimed)
     g = pool[0]
     g.profile(7)
-    single = single_circuit(lib, g, dls[0], circs[0])
+    single = single_circuit(lib, g, dls[0], circs[0]) if not args.no_single else None
     prof = [g.profile_read(k) for k in range(3)]
     g.profile(0)
     names = {0: "complex GEMMs (cgemm_kernel, cgemm_small_kernel, FP64-product cgemm_wide; "
@@ -521,14 +524,14 @@ def run_ours(args):
              for ci, L in zip(circs, host_layers)]
     torch.cuda.synchronize()
     te = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         lib.batch_run_host(pool, hosts)
         te.append(time.perf_counter() - t0)
-    e2e_ms = max_over_ranks(1e3 * sum(te), dist)
-    e2e_value = job_throughput(world, len(te), args.batch * updates, e2e_ms)
+    e2e_ms = max_over_ranks(1e3 * sum(te), dist) if te else None
+    e2e_value = job_throughput(world, len(te), args.batch * updates, e2e_ms) if te else None
 
     # peaks of this GPU and the GPU-wide roofline of the dominant class: its flops per step
     # (8 m n k per complex product at the actual dims; the eigensolvers' executed rotations
@@ -540,7 +543,8 @@ def run_ours(args):
     roof = {"kernel": names[dom], "scope": "GPU-wide: class flops per step / ms_per_step",
             "class_ms_per_step_summed_over_streams": cls[dom]["ms"] / args.steps,
             "launches_per_step": cls[dom]["launches"] / args.steps,
-            "share_of_single_circuit": prof[dom]["ms"] / max(1e-9, sum(q["ms"] for q in prof))}
+            "share_of_single_circuit": (prof[dom]["ms"] / max(1e-9, sum(q["ms"] for q in prof))
+                                        if single else None)}
     if fl_step > 0 and mp:
         achieved = fl_step / (ms_step / 1e3) / 1e12
         if dom == 0 and prec in ("tf32x3", "bf16x3"):
@@ -565,7 +569,7 @@ def run_ours(args):
     # the plain FP64 form on the same circuits and cut: one circuit alone, and the batch run
     # concurrently (handles capped at chi = 64: the cut keeps D below that, checked)
     fp64 = None
-    if not args.no_fp64_compare and prec != "fp64" and rank == 0 and world == 1:
+    if not args.no_fp64_compare and prec != "fp64" and rank == 0 and world == 1 and single:
         g64 = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=m_max, prec="fp64", own_stream=True,
                        sv_cutoff=eff)
         dl64 = [g64.upload_layer(layer) for layer in host_layers[0]]
@@ -606,9 +610,16 @@ def run_ours(args):
                              if tuned else "built-in size rules")
         cfg["batch"] = f"{args.batch} circuits per step, run concurrently (one stream each); " \
                        f"circuit 0 uses seed {c.seed}, circuit j seeded angles {c.seed}*1000+j"
-        cfg["chi_used_max"] = single["chi_used_max"]
-        cfg["k_used_max"] = single["k_used_max"]
-        cfg["mean_bond_dim"] = single["mean_bond_dim_final"]
+        if single is None:
+            # the timed circuits' reached dimensions, from the pool handles' final state
+            bd, kd, _ = pool[0].dims()
+            single_dims = {"chi_used_max": int(max(bd)), "k_used_max": int(max(kd)),
+                           "mean_bond_dim_final": float(np.mean(bd))}
+        else:
+            single_dims = single
+        cfg["chi_used_max"] = single_dims["chi_used_max"]
+        cfg["k_used_max"] = single_dims["k_used_max"]
+        cfg["mean_bond_dim"] = single_dims["mean_bond_dim_final"]
         errs = None
         if refs:
             errs = {"vs": f"CPU oracle (complex128) at the same cut, circuits 0..{len(refs) - 1} "
@@ -622,14 +633,18 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": cfg,
                 "energy_evals_per_s": world * args.steps * args.batch / (total_ms / 1e3),
-                "single_circuit": dict(single, site_updates_per_s=updates / (single["ms"] / 1e3)),
+                "single_circuit": (dict(single, site_updates_per_s=updates / (single["ms"] / 1e3))
+                                   if single else None),
                 "error_vs_oracle": errs,
                 "roofline": roof,
                 "peaks_measured_tflops": mp,
-                "kernel_profile_single_circuit_ms": {names[k]: prof[k]["ms"] for k in range(3)},
+                "kernel_profile_single_circuit_ms": ({names[k]: prof[k]["ms"] for k in range(3)}
+                                                     if single else None),
+                "kernel_class_ms_per_step_summed_over_streams": {
+                    names[q]: cls[q]["ms"] / args.steps for q in (0, 1)},
                 "cpu_baseline": cpu,
-                "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
+                "e2e": ({"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": d2h} if te else None),
                 "gpu_launches": launches, "tc_gemm_launches": tc_launches, "clocks": ck,
                 "fp64_plain": fp64}
         print(json.dumps(line), flush=True)
@@ -736,11 +751,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=list(FORMS), default="mixed",
-                    help="mixed: FP32 tensors with FP64 Grams and small matrices (default); "
-                         "mixed-tc: the same with its FP32 products on the tensor cores; "
-                         "tf32x3 / bf16x3: complex64 with all large products on the tensor "
-                         "cores; c64; fp64")
+    ap.add_argument("--prec", choices=list(FORMS), default="mixed-tc",
+                    help="mixed-tc (default): FP32 site tensors, FP64-accurate Grams and small "
+                         "matrices, every large product on the tensor cores (TF32x3 for the "
+                         "FP32 products, exact BF16 slices for the FP64 ones); mixed: the same "
+                         "arithmetic on the CUDA cores; tf32x3 / bf16x3: complex64 with FP32 "
+                         "Grams on the tensor cores; c64; fp64")
     ap.add_argument("--sv-cutoff", type=float, default=None,
                     help="bond cut s > cutoff * s_max (default: reading A4, 1e-7 for the "
                          "reduced-precision forms, 1e-14 for fp64; each form applies its "
@@ -751,6 +767,11 @@ def main():
                     help="skip only the batched FP64 comparison")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip measuring the FP64 / FP32 / TF32 GEMM peaks")
+    ap.add_argument("--no-single", action="store_true",
+                    help="skip the separate single-circuit run (workloads whose circuit takes "
+                         "minutes; the reached dimensions then come from the timed handles)")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--oracle-check", type=int, default=2,
                     help="circuits of the batch whose outputs are compared with the CPU oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -416,7 +416,9 @@ int mpdo_mlp_destroy(mpdo_mlp m);
  * Its scratch is one file-scope device array sized for n <= MPDO_HEIG_NOALLOC_NMAX; larger
  * n returns MPDO_ERR_ARG with a message in mpdo_last_error(NULL).  No call allocates.
  * The array's device address is looked up on the first call made on each device (with
- * that device current); make that first call before any stream capture.  Every GPU that
+ * that device current), and again on the first call after the device's context changed (a
+ * device reset loads the library's device code anew); make such first calls outside any
+ * stream capture.  Every GPU that
  * loads the library holds the array (~1.2 MB) until the process exits.  All calls share
  * the one array, and each call re-initialises the part it uses (padded matrix, identity
  * accumulator, zeroed counters); calls that overlap on the GPU -- on different streams

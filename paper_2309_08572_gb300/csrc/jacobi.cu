@@ -10,6 +10,7 @@
 // rotated ends the iteration.  Cost per sweep ~6 n^3 complex MACs; the matrix stays in
 // L2 (it is at most a few MB).
 #include <cooperative_groups.h>
+#include <cuda.h>
 
 #include <algorithm>
 #include <mutex>
@@ -608,7 +609,28 @@ static_assert(kNoAllocNMax % (2 * mpdo::JW) == 0, "maximum must be a whole numbe
 static __device__ __align__(256) unsigned char g_heig_scratch[kNoAllocBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
+// per device: the CUDA context the address was looked up in, and the address.  A device
+// reset (or a primary context destroyed and created again) loads the module anew, possibly
+// elsewhere, so the address is looked up again whenever the current context changes.
+void* g_scratch_ctx[kMaxDevices] = {};
 void* g_scratch_addr[kMaxDevices] = {};
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+void* current_context() {
+  static CtxGetCurrentFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return static_cast<CtxGetCurrentFn>(nullptr);
+    }
+    return reinterpret_cast<CtxGetCurrentFn>(p);
+  }();
+  CUcontext c = nullptr;
+  if (fn) fn(&c);
+  return c;
+}
 }  // namespace
 
 namespace mpdo {
@@ -639,7 +661,8 @@ extern "C" int mpdo_heig_noalloc(int prec, int n, void* a, void* v, double* w, i
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    void* ctx = current_context();
+    if (!g_scratch_addr[dev] || ctx != g_scratch_ctx[dev]) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_heig_scratch);
       if (e != cudaSuccess || !p) {
@@ -647,6 +670,7 @@ extern "C" int mpdo_heig_noalloc(int prec, int n, void* a, void* v, double* w, i
         return MPDO_ERR_CUDA;
       }
       g_scratch_addr[dev] = p;
+      g_scratch_ctx[dev] = current_context();
     }
     base = g_scratch_addr[dev];
   }
