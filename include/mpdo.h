@@ -301,6 +301,31 @@ int mpdo_build_qaoa_layer_cz(int n_sites, int k, double alpha, double beta, doub
                              double bz, const double* cz_superop, double xtalk_phase,
                              double eta, int* sites, int* ms, double* out, size_t cap);
 
+/* Vectorized MPO engine (the paper's main engine, Sec. III.A "vectorized MPO", with the
+ * purity-preserving truncation on the bond, Sec. III.D Eqs. xiformula and ppt, App. B):
+ * rho as an MPS over the doubled index (s, s') (local dimension 9), complex128, mixed-canonical
+ * in the Frobenius inner product.  Each two-site op (kind 2, its Kraus set as for mpdo_op) acts
+ * as its superoperator on the pair; the pair is split by an SVD (eigenpairs of the Gram of the
+ * updated pair, FP64 Jacobi) and cut to at most chi_max values above sv_cutoff (Schmidt values
+ * below sqrt(1e-15) of the largest are numerical zeros in any case).  use_ppt = 0 keeps the
+ * largest values unchanged ("naive"); 1 replaces them by PPT's values with the trace
+ * environment T_k of each Schmidt pair (from the trace contractions of the two sides), which
+ * keeps tr rho and tr rho^2 / tr rho^2 of the cut.  The op order rules are those of
+ * mpdo_apply_layer (ops must touch the centre; the centre moves to the other site).
+ * stats: disc_bond_w (sum over updates of the discarded sum of Lambda^2, fractions),
+ * PPT theta/infeasible/clamped, chi_used_max, n_updates.  mpdo_vmpo_purity: tr rho^2 (the
+ * centre's squared Frobenius norm in the canonical gauge).  chi_max in 1..256; init_site_vec
+ * as for mpdo_create; cuda_stream NULL = an own non-blocking stream. */
+typedef struct mpdo_vmpo_s* mpdo_vmpo;
+int mpdo_vmpo_create(int n_sites, int chi_max, int use_ppt, double sv_cutoff,
+                     const double* init_site_vec, void* cuda_stream, mpdo_vmpo* out);
+int mpdo_vmpo_apply_layer(mpdo_vmpo h, const mpdo_layer* layer, mpdo_trunc_stats* stats);
+int mpdo_vmpo_expect_energy(mpdo_vmpo h, double J, double hx, double b, double* e_raw,
+                            double* e_success, double* success_prob, double* trace);
+int mpdo_vmpo_purity(mpdo_vmpo h, double* purity);
+int mpdo_vmpo_get_dims(mpdo_vmpo h, int* bond_dims, int* centre);
+int mpdo_vmpo_destroy(mpdo_vmpo h);
+
 /* Instrumentation.
  * mpdo_kernel_launches: number of CUDA kernels this library has launched in the process.
  * mpdo_profile: time kernel launches of the selected classes on handle h with CUDA events

@@ -102,6 +102,12 @@ def _load():
         "mpdo_expect_energy": (I, [VP, D, D, D, P(D), P(D), P(D), P(D)]),
         "mpdo_sample_probs": (I, [VP, I, C.c_uint64, P(C.c_uint8), P(D)]),
         "mpdo_get_dims": (I, [VP, P(I), P(I), P(I)]),
+        "mpdo_vmpo_create": (I, [I, I, I, D, P(D), VP, P(VP)]),
+        "mpdo_vmpo_apply_layer": (I, [VP, P(Layer), P(TruncStats)]),
+        "mpdo_vmpo_expect_energy": (I, [VP, D, D, D, P(D), P(D), P(D), P(D)]),
+        "mpdo_vmpo_purity": (I, [VP, P(D)]),
+        "mpdo_vmpo_get_dims": (I, [VP, P(I), P(I)]),
+        "mpdo_vmpo_destroy": (I, [VP]),
         "mpdo_expect_second_order": (I, [VP, I, P(D), P(D), P(D), P(D), P(D)]),
         "mpdo_reconfigure": (I, [VP, I, I, I, I, P(D)]),
         "mpdo_batch_run": (I, [I, P(VP), I, P(CircuitDesc), P(D), P(I)]),
@@ -658,3 +664,49 @@ def kernel_tcgemm_exact(opa: int, opb: int, m: int, n: int, k: int, a, lda: int,
     _check(LIB.mpdo_kernel_tcgemm_exact(opa, opb, m, n, k, C.c_void_p(a.data_ptr()), lda, sa,
                                         C.c_void_p(b.data_ptr()), ldb, sb,
                                         C.c_void_p(c.data_ptr()), ldc, sc, batch, st))
+
+
+class Vmpo:
+    """Vectorized-MPO engine on the GPU (rho as an MPS over (s, s'), PPT on the bond)."""
+
+    def __init__(self, n_sites: int, chi_max: int, ppt: bool = True, sv_cutoff: float = 0.0,
+                 init_vec: Optional[Sequence[complex]] = None, stream=None):
+        self.n = n_sites
+        st = C.c_void_p(None) if stream is None else C.c_void_p(stream)
+        v = None if init_vec is None else np.ascontiguousarray(np.asarray(init_vec, complex)).view(float)
+        self._h = C.c_void_p(None)
+        _check(LIB.mpdo_vmpo_create(n_sites, chi_max, int(ppt), sv_cutoff,
+                                    None if v is None else _dptr(v), st, C.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            LIB.mpdo_vmpo_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_layer(self, ops) -> dict:
+        lay = _LayerArgs(ops)
+        st = TruncStats()
+        _check(LIB.mpdo_vmpo_apply_layer(self._h, C.byref(lay.layer), C.byref(st)))
+        return st.as_dict()
+
+    def expect_energy(self, J: float = 1.0, hx: float = 1.0, bz: float = 0.0) -> dict:
+        v = [C.c_double(0) for _ in range(4)]
+        _check(LIB.mpdo_vmpo_expect_energy(self._h, J, hx, bz, *[C.byref(x) for x in v]))
+        return dict(zip(("e_raw", "e_succ", "p_succ", "trace"), [x.value for x in v]))
+
+    def purity(self) -> float:
+        p = C.c_double(0)
+        _check(LIB.mpdo_vmpo_purity(self._h, C.byref(p)))
+        return p.value
+
+    def dims(self):
+        b = np.zeros(self.n - 1, dtype=np.int32)
+        c = C.c_int(0)
+        _check(LIB.mpdo_vmpo_get_dims(self._h, b.ctypes.data_as(C.POINTER(C.c_int)), C.byref(c)))
+        return b, c.value

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmpdo.so")
-SOURCES = ["api.cu", "gemm.cu", "jacobi.cu", "eigmix.cu", "kernels.cu", "mlp.cu", "tcgemm.cu", "channels.cpp"]
+SOURCES = ["api.cu", "gemm.cu", "jacobi.cu", "eigmix.cu", "kernels.cu", "mlp.cu", "tcgemm.cu", "vmpo.cu",
+           "channels.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
