@@ -472,7 +472,7 @@ int pc_eig(mpdo_ctx* h, int n, const cx<RM>* g, cx<RM>* v, long ldv, double* w, 
 // caller solves the full problem).  zero_tail: columns r..n-1 of v and w[r..n) zeroed.
 template <typename RM>
 int lift_eig(mpdo_ctx* h, int n, const cx<RM>* g, cx<RM>* v, long ldv, double* w, double tol,
-             int rmax, double floor, bool zero_tail, int* nvals) {
+             int rmax, double floor, bool zero_tail, int* nvals, int max_vals = 0) {
   using TM = cx<RM>;
   cudaStream_t st = h->st;
   *nvals = 0;
@@ -490,7 +490,7 @@ int lift_eig(mpdo_ctx* h, int n, const cx<RM>* g, cx<RM>* v, long ldv, double* w
   TM* Gs = static_cast<TM*>(h->wGs);
   TM* Z = static_cast<TM*>(h->wZ);
   CK(pgemm<RM>(h, OP_C, OP_N, r, r, n, L, kInnerRmax, 0, L, kInnerRmax, 0, Gs, r, 0, 1));
-  CK(peig<RM>(h, r, Gs, r, Z, r, w, floor));
+  CK(peig<RM>(h, r, Gs, r, Z, r, w, floor, max_vals));
   PO(lift<RM>(st, r, Z, w, Gs));
   CK(pgemm<RM>(h, OP_N, OP_N, n, r, r, L, kInnerRmax, 0, Gs, r, 0, v, ldv, 0, 1));
   if (zero_tail && r < n) {
@@ -529,8 +529,10 @@ int inner_eig(mpdo_ctx* h, int nin, int* nvals) {
   // mixed solver's size.
   const double tol = h->dbl ? kInnerTol64 : h->mixed ? kInnerTolMixed : kInnerTol;
   int nv = 0;
+  // at most k_max pairs are kept (the PPT's sum of squares comes from ||W||_F), so the
+  // solver may stop once k_max + 1 leading pairs are resolved
   rc = lift_eig<RM>(h, nin, W, V, nin, h->wWv, tol, h->mixed ? kMixedEigMax : kInnerRmax, 1e-10,
-                    false, &nv);
+                    false, &nv, h->kmax + 1);
   if (rc) return rc;
   if (nv == 0) {
     // at most k_max pairs are kept; the PPT's sum of squares comes from ||W||_F
@@ -620,7 +622,7 @@ int update_lr(mpdo_ctx* h, int i, const DevOp& op, bool mirrored, int chi, int k
     int nv = 0;
     if (h->mixed) {
       rc = lift_eig<RM>(h, n9, wH, wU, n9, h->wLam, pc_tol(h, h->htol), kMixedEigMax,
-                        0.1 * h->htol, true, &nv);
+                        0.1 * h->htol, true, &nv, chi + 1);
       if (rc) return rc;
     }
     if (nv == 0 && (h->dbl || (h->mixed && n9 > h->mixw.n_cap))) {

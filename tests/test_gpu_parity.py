@@ -413,3 +413,34 @@ def test_second_order_matches_oracle(lib, prec, case):
             tol = 1e-9 if prec == "fp64" else 1e-4
             assert abs(got[key] - want[key]) < tol, (cut, key)
     g.close()
+
+
+def test_batch512_first_32_circuits_match_oracle(lib):
+    """The batched workload's first 32 circuits (N ~ U{20..100}, chi in {32,64,128}, K = 8,
+    p in {1,2}, log-uniform rates) run concurrently through the executor in the mixed
+    tensor-core form at reading A4's cut, every one against the oracle at the effective cut
+    (s > sqrt(1e-13) s_max): 1e-6 relative on every energy and probability."""
+    circs = synth.batch512()[:32]
+    pool = [lib.Mpdo(100, 128, 8, m_max=25, prec="tf32x3", gram_fp64=True, sv_cutoff=1e-7,
+                     own_stream=True) for _ in range(16)]
+    descs, uploaded = [], []
+    for c in circs:
+        dls = [pool[0].upload_layer(layer) for layer in lib.circuit_layers(c)]
+        uploaded.append(dls)
+        descs.append(dict(n_sites=c.n_sites, chi_max=c.chi_max, k_max=c.k_max, layers=dls,
+                          J=c.J, hx=c.hx, b=c.bz))
+    out = lib.batch_run(pool, descs)
+    worst = {}
+    for i, c in enumerate(circs):
+        _, r = _oracle(c, sv_cutoff=MIXED_FLOOR_CUT)
+        for j, key in enumerate(("e_raw", "e_succ", "p_succ", "trace")):
+            err = _rel(out[i][j], r[key]) if key in ("p_succ", "trace") else \
+                abs(out[i][j] - r[key]) / abs(r[key])
+            worst[key] = max(worst.get(key, 0.0), err)
+            assert err < CHAIN100_TOL[key], (i, key, out[i][j], r[key])
+    print("batch512[:32] worst relative errors", worst)
+    for dls in uploaded:
+        for dl in dls:
+            pool[0].free_uploaded(dl)
+    for m in pool:
+        m.close()
