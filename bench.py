@@ -745,6 +745,76 @@ def run_batch512(args):
     return 0
 
 
+def run_compare(args):
+    """Fig. 7's comparison on this GPU: the collision probability (anticoncentration) of the
+    8-site random circuit with gamma_diss = 0.1 (depth 40, i.e. 20 two-layer periods, Haar
+    one-qubit gates and noisy CZ brickwork, seed 5), for the vectorized MPO with naive and
+    with purity-preserving truncation on the bond and for the MPDO, against the update time
+    per two-layer period.  Errors are the mean over the last 5 periods of |Z - Z_ref| / Z_ref,
+    Z_ref from the vectorized MPO with PPT at chi = 128 (tensor-core form, bond cut
+    s > 1e-5 s_max); the MPDO at (chi 64, K 8) is reported beside it as a check of the
+    reference.  Points: FP64, bond cut s > 1e-7 s_max.  One line of JSON with every point."""
+    import torch
+    import paper_2309_08572_gb300 as lib
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    depth, periods_avg = 40, 5
+    circ = synth.rcs(8, depth, 256, 16, gamma_diss=0.1, seed=5, delta_pp=0.01)
+    layers = lib.circuit_layers(circ)
+    probe = set(range(depth - 2 * periods_avg + 1, depth, 2))   # after periods 16..20
+    m_max = max(k.shape[0] for layer in layers for _, k in layer)
+
+    def run(kind, chi, k=1, mode=None, tc=False):
+        if kind == "vmpo":
+            g = lib.Vmpo(circ.n_sites, chi, ppt=(mode == "ppt"), sv_cutoff=1e-5 if tc else 1e-7,
+                         init_vec=[1, 0, 0], tc=tc)
+        else:
+            g = lib.Mpdo(circ.n_sites, chi, k, m_max=m_max, prec="fp64", sv_cutoff=1e-7,
+                         init_vec=[1, 0, 0])
+        zs, t = [], 0.0
+        for li, layer in enumerate(layers):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.apply_layer(layer)
+            torch.cuda.synchronize()
+            t += time.perf_counter() - t0
+            if li in probe:
+                zs.append(g.collision() if kind == "vmpo" else
+                          g.second_order(circ.n_sites // 2)["collision"])
+        g.close()
+        return np.array(zs), t / (depth / 2)
+
+    z_ref, t_ref = run("vmpo", 128, mode="ppt", tc=True)
+    z_chk, t_chk = run("mpdo", 64, 8)
+    points = []
+    for mode in ("naive", "ppt"):
+        for chi in (8, 16, 32, 64):
+            z, t = run("vmpo", chi, mode=mode)
+            points.append({"engine": f"vmpo-{mode}", "chi": chi, "K": None,
+                           "s_per_period": t,
+                           "collision_rel_err": float(np.mean(np.abs(z - z_ref) / z_ref))})
+    for chi, k in ((8, 2), (16, 2), (16, 4), (32, 4), (32, 8)):
+        z, t = run("mpdo", chi, k)
+        points.append({"engine": "mpdo", "chi": chi, "K": k, "s_per_period": t,
+                       "collision_rel_err": float(np.mean(np.abs(z - z_ref) / z_ref))})
+    line = {"metric": "collision-probability error vs update time per two-layer period "
+                      "(Fig. 7 comparison)",
+            "value": None, "unit": "relative error / s", "n_gpus": 1, "higher_is_better": False,
+            "data": "synthetic",
+            "config": {"workload": "rcs8 gamma_diss=0.1: 8 sites (d=3), depth 40, Haar U(2) on "
+                                   "the qubit levels + noisy CZ brickwork (G0), post-promotion "
+                                   "0.01 rad, seed 5, |0>^8; bond cut s > 1e-7 s_max",
+                       "precision": "FP64 (the reference: exact-slice tensor-core products + "
+                                    "mixed eigensolver)",
+                       "reference": "vMPO PPT chi=128", "reference_s_per_period": t_ref,
+                       "check_mpdo_64x8_vs_reference": float(np.mean(np.abs(z_chk - z_ref) /
+                                                                    z_ref)),
+                       "check_s_per_period": t_chk,
+                       "collision_reference": [float(x) for x in z_ref]},
+            "points": points}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -785,10 +855,12 @@ def main():
                          "measurement of it exists yet)")
     ap.add_argument("--batch", type=int, default=32,
                     help="circuits per step, run concurrently by the batch executor")
-    ap.add_argument("--workload", choices=["chain100", "chain100deep", "chain40", "batch512"],
+    ap.add_argument("--workload", choices=["chain100", "chain100deep", "chain40", "batch512",
+                                           "rcs8cmp"],
                     default="chain100",
                     help="chain40 (N=40, p=2, chi=64, K=8) is the small profiling case; "
-                         "chain100deep has p=8 layers (bond dimension reaches chi=256)")
+                         "chain100deep has p=8 layers (bond dimension reaches chi=256); "
+                         "rcs8cmp prints Fig. 7's engine comparison (vMPO naive / PPT, MPDO)")
     args = ap.parse_args()
     global WORKLOAD, GATE_MODEL
     WORKLOAD = args.workload
@@ -802,6 +874,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch512(args)
+    if args.workload == "rcs8cmp":
+        return run_compare(args)
     return run_ours(args)
 
 

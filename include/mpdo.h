@@ -314,7 +314,10 @@ int mpdo_build_qaoa_layer_cz(int n_sites, int k, double alpha, double beta, doub
  * mpdo_apply_layer (ops must touch the centre; the centre moves to the other site).
  * stats: disc_bond_w (sum over updates of the discarded sum of Lambda^2, fractions),
  * PPT theta/infeasible/clamped, chi_used_max, n_updates.  mpdo_vmpo_purity: tr rho^2 (the
- * centre's squared Frobenius norm in the canonical gauge).  chi_max in 1..256; init_site_vec
+ * centre's squared Frobenius norm in the canonical gauge).  mpdo_vmpo_collision: the
+ * collision probability sum_x <x|rho|x>^2 / (tr rho)^2 (Sec. III.E, the anticoncentration of
+ * Fig. 7), from the diagonal entries (s, s) of each site contracted over two copies; O(D^3)
+ * per site, FP64; MPDO_ERR_NUMERIC for a zero trace.  chi_max in 1..256; init_site_vec
  * as for mpdo_create; cuda_stream NULL = an own non-blocking stream. */
 typedef struct mpdo_vmpo_s* mpdo_vmpo;
 int mpdo_vmpo_create(int n_sites, int chi_max, int use_ppt, double sv_cutoff,
@@ -323,6 +326,17 @@ int mpdo_vmpo_apply_layer(mpdo_vmpo h, const mpdo_layer* layer, mpdo_trunc_stats
 int mpdo_vmpo_expect_energy(mpdo_vmpo h, double J, double hx, double b, double* e_raw,
                             double* e_success, double* success_prob, double* trace);
 int mpdo_vmpo_purity(mpdo_vmpo h, double* purity);
+int mpdo_vmpo_collision(mpdo_vmpo h, double* collision);
+/* Arithmetic of the vMPO updates.  mode 0 (default): FP64 products on the CUDA cores and
+ * the FP64 Jacobi eigensolver.  mode 1 (the tensor-core form): products of at least 2^21
+ * complex multiply-adds as error-free BF16 slice products on the tensor cores summed in
+ * FP64 (carried to ~2^-48 of each operand row's largest entry), and the Gram's eigenpairs
+ * from the mixed-precision solver (FP32 Jacobi levels with FP64 refinement); its
+ * resolution raises the numerical-zero floor of the Schmidt values from sqrt(1e-15) to
+ * sqrt(1e-13) of the largest.  The first switch to mode 1 allocates ~0.3 GB plus the
+ * solver's workspace (~1 GB at chi 256).  MPDO_ERR_TIMEOUT from a later update when a
+ * tensor-core pipeline wait gave up. */
+int mpdo_vmpo_set_precision(mpdo_vmpo h, int mode);
 int mpdo_vmpo_get_dims(mpdo_vmpo h, int* bond_dims, int* centre);
 int mpdo_vmpo_destroy(mpdo_vmpo h);
 
@@ -363,8 +377,13 @@ int mpdo_kernel_cgemm(int prec, int opa, int opb, int m, int n, int k, const voi
                       long ldc, long sc, int batch, void* stream);
 /* Hermitian eigendecomposition of a (n x n, row-major complex, overwritten): eigenvalues
  * descending into w (double, host-visible device array of n), eigenvectors as the
- * columns of v (n x n row-major complex of the same precision).  Returns sweeps used
- * in *sweeps (host). */
+ * columns of v (n x n row-major complex of the same precision).  prec 0: complex128 Jacobi;
+ * 1: complex64 Jacobi; 2: complex128 matrix through the mixed-precision solver (FP32
+ * Jacobi levels with FP64 refinement, resolved down to 1e-14 of the largest eigenvalue);
+ * 3: as 2 with the solver's FP64 products formed as error-free BF16 slice products on the
+ * tensor cores (allocates a 256 MiB workspace for the call).  Returns the sweeps (0, 1) or
+ * levels (2, 3) used in *sweeps (host).  n in 1..4096; MPDO_ERR_TIMEOUT when a tensor-core
+ * pipeline wait gave up. */
 int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, void* stream);
 
 /* Tensor-core GEMMs (tcgen05.mma, TMEM accumulators, TMA-fed shared-memory pipeline) on

@@ -45,6 +45,10 @@ class VMPO:
         self.sv_cutoff = sv_cutoff
         self.ppt_infeasible = 0
         self.t_imag_max = 0.0
+        # smallest (Lambda_chi-1^2 - Lambda_chi^2) / Lambda_0^2 over the truncations at chi:
+        # the conditioning of the kept subspace (a perturbation dH of the bond's Gram turns
+        # it by ~|dH| / gap)
+        self.cut_gap_min = np.inf
 
     # trace environments of the sites left of i and right of j (contractions with tau)
     def _left_trace(self, i: int) -> np.ndarray:
@@ -72,6 +76,9 @@ class VMPO:
         nz = max(1, int(np.count_nonzero(lam > self.sv_cutoff * lam[0])))
         u, lam, vh = u[:, :nz], lam[:nz], vh[:nz]
         keep = max(1, min(nz, self.chi_max))
+        if nz > keep:
+            self.cut_gap_min = min(self.cut_gap_min,
+                                   float((lam[keep - 1] ** 2 - lam[keep] ** 2) / lam[0] ** 2))
         if self.mode == "ppt":
             tl = np.einsum("l,h,lhk->k", self._left_trace(i), TAU, u.reshape(dl, 9, -1))
             tr = np.einsum("khr,h,r->k", vh.reshape(-1, 9, dr), TAU, self._right_trace(j))
@@ -132,6 +139,18 @@ class VMPO:
         for a in self.A:
             e = np.einsum("ab,ahr,bhq->rq", e, a, a.conj())
         return float(e[0, 0].real)
+
+    def collision(self) -> float:
+        """Collision probability sum_x <x|rho|x>^2 / (tr rho)^2 (Sec. III.E, the
+        anticoncentration of Fig. 7): the diagonal rho_xx = prod_n A_n[., (s_n, s_n), .]
+        contracted with itself over x, and the trace sum_x rho_xx, site by site."""
+        e2 = np.ones((1, 1), dtype=complex)
+        e1 = np.ones(1, dtype=complex)
+        for a in self.A:
+            dg = a.reshape(a.shape[0], D, D, a.shape[2])[:, np.arange(D), np.arange(D), :]
+            e2 = np.einsum("ab,asr,bsq->rq", e2, dg, dg)
+            e1 = np.einsum("a,asr->r", e1, dg)
+        return float(e2[0, 0].real / e1[0].real ** 2)
 
     def to_dense(self) -> np.ndarray:
         """rho as a d^N x d^N matrix (tiny N): x[(p,s),(q,s'),r] = sum_l x[p,q,l] A[l,(s,s'),r]."""

@@ -106,6 +106,8 @@ def _load():
         "mpdo_vmpo_apply_layer": (I, [VP, P(Layer), P(TruncStats)]),
         "mpdo_vmpo_expect_energy": (I, [VP, D, D, D, P(D), P(D), P(D), P(D)]),
         "mpdo_vmpo_purity": (I, [VP, P(D)]),
+        "mpdo_vmpo_collision": (I, [VP, P(D)]),
+        "mpdo_vmpo_set_precision": (I, [VP, I]),
         "mpdo_vmpo_get_dims": (I, [VP, P(I), P(I)]),
         "mpdo_vmpo_destroy": (I, [VP]),
         "mpdo_expect_second_order": (I, [VP, I, P(D), P(D), P(D), P(D), P(D)]),
@@ -670,13 +672,20 @@ class Vmpo:
     """Vectorized-MPO engine on the GPU (rho as an MPS over (s, s'), PPT on the bond)."""
 
     def __init__(self, n_sites: int, chi_max: int, ppt: bool = True, sv_cutoff: float = 0.0,
-                 init_vec: Optional[Sequence[complex]] = None, stream=None):
+                 init_vec: Optional[Sequence[complex]] = None, stream=None, tc: bool = False):
         self.n = n_sites
         st = C.c_void_p(None) if stream is None else C.c_void_p(stream)
         v = None if init_vec is None else np.ascontiguousarray(np.asarray(init_vec, complex)).view(float)
         self._h = C.c_void_p(None)
         _check(LIB.mpdo_vmpo_create(n_sites, chi_max, int(ppt), sv_cutoff,
                                     None if v is None else _dptr(v), st, C.byref(self._h)))
+        if tc:
+            self.set_precision(1)
+
+    def set_precision(self, mode: int):
+        """0: FP64 CUDA cores and Jacobi; 1: exact-slice tensor-core products and the mixed
+        eigensolver."""
+        _check(LIB.mpdo_vmpo_set_precision(self._h, mode))
 
     def close(self):
         if self._h:
@@ -704,6 +713,12 @@ class Vmpo:
         p = C.c_double(0)
         _check(LIB.mpdo_vmpo_purity(self._h, C.byref(p)))
         return p.value
+
+    def collision(self) -> float:
+        """sum_x <x|rho|x>^2 / (tr rho)^2."""
+        z = C.c_double(0)
+        _check(LIB.mpdo_vmpo_collision(self._h, C.byref(z)))
+        return z.value
 
     def dims(self):
         b = np.zeros(self.n - 1, dtype=np.int32)

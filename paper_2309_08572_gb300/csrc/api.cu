@@ -1494,6 +1494,17 @@ int mpdo_create(const mpdo_config* cfg, const double* init_site_vec, mpdo_t* out
     }
     *h->htcerr = 0;
   }
+  if (h->mixed && h->tcmode >= 0) {
+    // the mixed eigensolver's FP64 products take the same exact-slice tensor-core route
+    // (MPDO_EIG_TC=0 keeps them on the CUDA cores)
+    const char* et = std::getenv("MPDO_EIG_TC");
+    if (!(et && et[0] == '0')) {
+      h->mixw.tcws = h->tcws;
+      h->mixw.tcws_bytes = h->tcws_bytes;
+      h->mixw.tcerr = h->tcerr;
+      h->mixw.tc_min_macs = h->tc_min_macs;
+    }
+  }
   {
     // identity channel for the left-to-right order's centre moves
     std::vector<double> idop(2 * 81, 0.0);
@@ -1846,10 +1857,18 @@ int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, 
   if (n < 1 || n > 4096 || !a || !v || !w) return fail(nullptr, MPDO_ERR_ARG, "bad heig arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   void* mem = nullptr;
-  if (prec == 2) {
-    // mixed-precision solver on an FP64 matrix (resolved down to 1e-14 of the largest)
+  if (prec == 2 || prec == 3) {
+    // mixed-precision solver on an FP64 matrix (resolved down to 1e-14 of the largest);
+    // prec 3: its FP64 products as exact slice products on the tensor cores
     void* mm = nullptr;
     if (cudaMalloc(&mm, mix_work_bytes(n)) != cudaSuccess) { cudaGetLastError(); return fail(nullptr, MPDO_ERR_OOM, "heig work"); }
+    void* tw = nullptr;
+    const size_t tw_bytes = (size_t)256 << 20;
+    if (prec == 3 && cudaMalloc(&tw, tw_bytes + 256) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(mm);
+      return fail(nullptr, MPDO_ERR_OOM, "heig tensor-core workspace");
+    }
     // the solver's CTA ticket starts at zero
     if (cudaMemsetAsync(mm, 0, mix_work_bytes(n), st) != cudaSuccess) {
       cudaGetLastError();
@@ -1858,12 +1877,25 @@ int mpdo_kernel_heig(int prec, int n, void* a, void* v, double* w, int* sweeps, 
     }
     MixWork mw;
     mix_work_bind(mw, mm, n);
+    int herr = 0;
+    cudaError_t e2 = cudaSuccess;
+    if (tw) {
+      mw.tcws = static_cast<char*>(tw) + 256;
+      mw.tcws_bytes = tw_bytes;
+      mw.tcerr = static_cast<int*>(tw);
+      mw.tc_min_macs = kTcMinMacs;
+      e2 = cudaMemsetAsync(tw, 0, sizeof(int), st);
+    }
     int lv = 0;
-    cudaError_t e2 = heig_mixed(st, n, (const double2*)a, n, (double2*)v, n, w, 1e-14, mw, &lv);
+    if (e2 == cudaSuccess)
+      e2 = heig_mixed(st, n, (const double2*)a, n, (double2*)v, n, w, 1e-14, mw, &lv);
+    if (e2 == cudaSuccess && tw) e2 = cudaMemcpyAsync(&herr, tw, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
     mix_work_release(mw);
     cudaFree(mm);
+    if (tw) cudaFree(tw);
     if (e2 != cudaSuccess) return fail(nullptr, MPDO_ERR_CUDA, cudaGetErrorString(e2));
+    if (herr) return fail(nullptr, MPDO_ERR_TIMEOUT, "heig: a tensor-core pipeline wait gave up");
     if (sweeps) *sweeps = lv;
     return MPDO_OK;
   }

@@ -44,6 +44,19 @@ template <typename C> __host__ __device__ __forceinline__ auto cabs2(C a) -> dec
   return a.x * a.x + a.y * a.y;
 }
 
+// Round-robin pairing (circle method) of `players` (even) indices: pair k of round `round`,
+// rounds 0 .. players - 2 meet every pair once; player players - 1 stays fixed.
+__device__ __forceinline__ void tourney(int round, int k, int players, int& a, int& b) {
+  const int m = players - 1;
+  if (k == 0) {
+    a = m;
+    b = round % m;
+  } else {
+    a = (round + k) % m;
+    b = (round - k + m) % m;
+  }
+}
+
 // Scalars produced by one update step on the device and read by the host driver.
 struct StepScalars {
   int keep;        // bond values kept

@@ -74,12 +74,21 @@ struct MixWork {
   float2 *a32 = nullptr, *y32 = nullptr;
   double *lam = nullptr, *w32 = nullptr, *scan = nullptr;
   unsigned int* ticket = nullptr;   // CTA ticket of the fused refinement (0 between launches)
+  int* cid = nullptr;               // cluster of each column in the final refinement pass
+  unsigned char* sepf = nullptr;    // neighbour separation flags of levels wider than 4096
   EigWork<float> ew;
   MixGraphs* graphs = nullptr;   // created on first use; freed by mix_work_release
   bool use_graphs = true;
   cudaEvent_t block_ev = nullptr; // when set, level read-backs wait on it (blocking sync)
   double* hpin = nullptr;         // mapped pinned host area of the level scalars (lazy)
   double* hpin_dev = nullptr;     // its device address
+  // Tensor-core workspace lent by the caller: when set, products of at least tc_min_macs
+  // complex multiply-adds run as error-free BF16 slice products (tc_cgemm_exact) instead of
+  // CUDA-core FP64; tcerr is the device flag of their pipeline waits.
+  void* tcws = nullptr;
+  size_t tcws_bytes = 0;
+  int* tcerr = nullptr;
+  double tc_min_macs = 0;
 };
 size_t mix_work_bytes(int n_cap);
 void mix_work_bind(MixWork& w, void* base, int n_cap);

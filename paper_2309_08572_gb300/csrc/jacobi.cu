@@ -34,17 +34,6 @@ constexpr int CH = 64;         // staged chunk (columns in phase A, rows in phas
 // converged sub-problem buys little and costs 15 warp rounds per extra sweep.
 constexpr int kInnerSweeps = 1;
 
-__device__ __forceinline__ void tourney(int round, int k, int players, int& a, int& b) {
-  // circle method: player players-1 fixed, others rotate
-  int m = players - 1;
-  if (k == 0) {
-    a = m;
-    b = round % m;
-  } else {
-    a = (round + k) % m;
-    b = (round - k + m) % m;
-  }
-}
 
 template <typename R> struct Tol;
 template <> struct Tol<double> { static constexpr double rel = 1e-15, abs = 2.2e-16; };
@@ -580,6 +569,13 @@ cudaError_t heig(cudaStream_t st, int n, const cx<R>* a, long lda, cx<R>* v, lon
   int P = 1;
   while (P < n) P <<= 1;
   size_t sm = (size_t)P * (sizeof(double) + sizeof(int));
+  // sort keys beyond n = 2048 exceed the default 48 KB of shared memory (with the kernel's
+  // static flag): opt in up to n = 16384, 192 KB (once per instantiation)
+  static const cudaError_t fattr = cudaFuncSetAttribute(
+      eig_finalize_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(16384 * (sizeof(double) + sizeof(int))));
+  MPDO_CUDA_TRY(fattr);
+  if (P > 16384) return cudaErrorInvalidValue;
   eig_finalize_kernel<R><<<1, 1024, sm, st>>>(n, np, work.ap, work.vp, v, ldv, w);
   return cudaGetLastError();
 }

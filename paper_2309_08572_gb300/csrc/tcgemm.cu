@@ -911,6 +911,13 @@ size_t tc_exact_ws_bytes(long m, long n, long k, int batch) {
   return exact_bytes(m, n, std::min<long>(k, 4096), batch);
 }
 
+cudaError_t tc_exact_init() {
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      tc_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(XSTAGES * (BM + XBN) * 128 + 1024 + 256));
+  return attr;
+}
+
 template <typename TA, typename TB>
 cudaError_t tc_cgemm_exact(cudaStream_t st, int opa, int opb, int m, int n, int k, const TA* A,
                            long lda, long sa, const TB* B, long ldb, long sb, double2* C, long ldc,
@@ -925,10 +932,7 @@ cudaError_t tc_cgemm_exact(cudaStream_t st, int opa, int opb, int m, int n, int 
   int cja, cjb;
   op_strides(0, opa, lda, &sra, &sca, &cja);
   op_strides(1, opb, ldb, &srb, &scb, &cjb);
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      tc_exact_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)(XSTAGES * (BM + XBN) * 128 + 1024 + 256));
-  if (attr != cudaSuccess) return attr;
+  MPDO_CUDA_TRY(tc_exact_init());
   for (long k0 = 0; k0 < k; k0 += kc) {
     const int kn = (int)std::min<long>(kc, k - k0);
     const int kr = 2 * kn;

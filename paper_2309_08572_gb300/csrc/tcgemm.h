@@ -62,6 +62,9 @@ cudaError_t tc_cgemm_exact(cudaStream_t st, int opa, int opb, int m, int n, int 
                            long lda, long sa, const TB* B, long ldb, long sb, double2* C, long ldc,
                            long sc, int batch, void* ws, size_t ws_bytes, int* err);
 size_t tc_exact_ws_bytes(long m, long n, long k, int batch);
+// One-time kernel attribute setup of tc_cgemm_exact; call it before capturing a stream that
+// will run the first exact product of the process.
+cudaError_t tc_exact_init();
 
 // out[r][c] = bf16(src[r*s_r + c*s_c]) for r < rows, c < kc (row stride ldo elements): the
 // K-major BF16 operands of tc_gemm_real from a real FP32 matrix in either orientation.

@@ -33,6 +33,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "kernels.h"
+#include "tcgemm.h"
 
 namespace mpdo {
 void set_global_error(const char* msg);
@@ -238,6 +239,15 @@ struct mpdo_vmpo_s {
   double *lam = nullptr, *sv = nullptr, *lt = nullptr;
   EigWork<double> eig;
   void* eigmem = nullptr;
+  // tensor-core form (mpdo_vmpo_set_precision 1): exact-slice products and the mixed solver
+  int tc = 0;
+  MixWork mixw;
+  void* mixmem = nullptr;
+  void* tcws = nullptr;
+  size_t tcws_bytes = 0;
+  int* tcerr = nullptr;
+  int* htcerr = nullptr;   // pinned
+  double sv_req = 0;       // requested cut (Schmidt values, relative)
   VScalars* dsc = nullptr;
   VScalars* hsc = nullptr;
   std::vector<void*> allocs;
@@ -277,6 +287,18 @@ cudaError_t g64(cudaStream_t st, int opa, int opb, int m, int n, int k, const do
                 int batch) {
   return cgemm<double>(st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch,
                        make_double2(1, 0), make_double2(0, 0));
+}
+
+// Products of the update: in the tensor-core form, those of at least 2^21 complex
+// multiply-adds (both output sides >= 16) as error-free BF16 slice products summed in FP64
+// (carried to ~2^-48 of each operand row's largest entry); FP64 CUDA cores otherwise.
+cudaError_t u64(mpdo_vmpo h, int opa, int opb, int m, int n, int k, const double2* A, long lda,
+                long sa, const double2* B, long ldb, long sb, double2* C, long ldc, long sc,
+                int batch) {
+  if (h->tc && m >= 16 && n >= 16 && (double)m * n * k * batch >= (double)(1 << 21))
+    return tc_cgemm_exact<double2, double2>(h->st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C,
+                                            ldc, sc, batch, h->tcws, h->tcws_bytes, h->tcerr);
+  return g64(h->st, opa, opb, m, n, k, A, lda, sa, B, ldb, sb, C, ldc, sc, batch);
 }
 
 // right trace environments Renv[n] (right of site n, storage coords) for all n
@@ -349,19 +371,26 @@ int update(mpdo_vmpo h, int i, const VOp& op, mpdo_trunc_stats* acc) {
   const std::vector<zc>& S = h->rev ? op.sm : op.s;
   VK(cudaMemcpyAsync(h->S, S.data(), 81 * 81 * sizeof(double2), cudaMemcpyHostToDevice, st));
   // theta = A_i A_j ; theta' = S on (eta_i, eta_j), batched over l
-  VK(g64(st, OP_N, OP_N, rows, cols, dm, h->site(i), dm, 0, h->site(i + 1), cols, 0, h->th, cols,
+  VK(u64(h, OP_N, OP_N, rows, cols, dm, h->site(i), dm, 0, h->site(i + 1), cols, 0, h->th, cols,
          0, 1));
-  VK(g64(st, OP_N, OP_N, 81, dr, 81, h->S, 81, 0, h->th, dr, 81L * dr, h->th2, dr, 81L * dr, dl));
-  // Schmidt decomposition through the Gram theta' theta'^+ (FP64 Jacobi)
-  VK(g64(st, OP_N, OP_C, rows, rows, cols, h->th2, cols, 0, h->th2, cols, 0, h->H, rows, 0, 1));
-  VK(heig<double>(st, rows, h->H, rows, h->U, rows, h->lam, h->eig, 30));
+  VK(u64(h, OP_N, OP_N, 81, dr, 81, h->S, 81, 0, h->th, dr, 81L * dr, h->th2, dr, 81L * dr, dl));
+  // Schmidt decomposition through the Gram theta' theta'^+: FP64 Jacobi, or in the
+  // tensor-core form the mixed solver (FP32 Jacobi levels, FP64 refinement) resolved below
+  // a tenth of the cut -- in naive mode only the chi + 1 leading pairs (PPT needs T and
+  // Lambda of every Schmidt pair)
+  VK(u64(h, OP_N, OP_C, rows, rows, cols, h->th2, cols, 0, h->th2, cols, 0, h->H, rows, 0, 1));
+  if (h->tc)
+    VK(heig_mixed(st, rows, h->H, rows, h->U, rows, h->lam, 0.1 * h->cut2, h->mixw, nullptr,
+                  nullptr, h->mode == 1 ? 0 : h->chi + 1));
+  else
+    VK(heig<double>(st, rows, h->H, rows, h->U, rows, h->lam, h->eig, 30));
   // trace environment: tl = (L (x) tau)^T U ; W = U^+ theta' (row k = Lambda_k V^+_k) ;
   // trw = W (tau (x) R)
   count_launch();
   trace_vec_kernel<<<nblk(rows), 256, 0, st>>>(dl, h->Lenv + (long)i * h->chi, 0, h->x);
   VK(cudaGetLastError());
   VK(g64(st, OP_N, OP_N, 1, rows, rows, h->x, rows, 0, h->U, rows, 0, h->tl, rows, 0, 1));
-  VK(g64(st, OP_C, OP_N, rows, cols, rows, h->U, rows, 0, h->th2, cols, 0, h->th, cols, 0, 1));
+  VK(u64(h, OP_C, OP_N, rows, cols, rows, h->U, rows, 0, h->th2, cols, 0, h->th, cols, 0, 1));
   count_launch();
   trace_vec_kernel<<<nblk(cols), 256, 0, st>>>(dr, h->Renv + (long)(i + 1) * h->chi, 1,
                                                 h->x + rows);
@@ -372,7 +401,9 @@ int update(mpdo_vmpo h, int i, const VOp& op, mpdo_trunc_stats* acc) {
                                     h->lt, h->dsc);
   VK(cudaGetLastError());
   VK(cudaMemcpyAsync(h->hsc, h->dsc, sizeof(VScalars), cudaMemcpyDeviceToHost, st));
+  if (h->tc) VK(cudaMemcpyAsync(h->htcerr, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
   VK(cudaStreamSynchronize(st));
+  if (h->tc && *h->htcerr) return vfail(h, MPDO_ERR_TIMEOUT, "vmpo: a tensor-core pipeline wait gave up");
   if (h->hsc->flags & 1) return vfail(h, MPDO_ERR_NUMERIC, "vmpo: zero or non-finite state");
   const int keep = h->hsc->keep;
   // A_i <- U_keep ; A_{i+1} <- diag(Lambda~ / Lambda) W_keep
@@ -443,6 +474,7 @@ int mpdo_vmpo_create(int n_sites, int chi_max, int use_ppt, double sv_cutoff,
   // Gram eigenvalues resolve to ~1e-16 of the largest: Schmidt values below sqrt(1e-15) of
   // the largest are numerical zeros whatever cut is asked for
   const double sv = sv_cutoff > 0 ? sv_cutoff : 1e-14;
+  h->sv_req = sv;
   h->cut2 = std::max(sv * sv, 1e-15);
   if (cuda_stream) {
     h->st = static_cast<cudaStream_t>(cuda_stream);
@@ -599,6 +631,45 @@ int mpdo_vmpo_purity(mpdo_vmpo h, double* purity) {
   return MPDO_OK;
 }
 
+int mpdo_vmpo_collision(mpdo_vmpo h, double* collision) {
+  if (!h || !collision) return vfail(h, MPDO_ERR_ARG, "vmpo: null argument");
+  // rho_xx = prod_n A_n[., (s_n, s_n), .]: E <- sum_s A_s^T E A_s (D x D, the pair of copies)
+  // and t <- sum_s t A_s (the trace), with A_s = A_n[:, (s, s), :] (rows of stride 9 D_r);
+  // the site order of the storage does not matter for a sum over all x
+  const long D = h->chi;
+  double2* E = h->th;              // D x D
+  double2* En = E + D * D;         // D x D
+  double2* T = En + D * D;         // 3 x D x D
+  double2* t = T + 3 * D * D;      // D
+  double2* tn = t + D;             // D
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  VK(cudaMemcpyAsync(E, &one, sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  VK(cudaMemcpyAsync(t, &one, sizeof(double2), cudaMemcpyHostToDevice, h->st));
+  for (int s = 0; s < h->n; ++s) {
+    const int dl = h->bond[s], dr = h->bond[s + 1];
+    const double2* A = h->site(s);
+    const long la = 9L * dr, sd = 4L * dr;   // diagonal eta = 0, 4, 8
+    // T_s = E A_s, batched over the three diagonal entries
+    VK(cgemm<double>(h->st, OP_N, OP_N, dl, dr, dl, E, dl, 0, A, la, sd, T, dr, (long)dl * dr, 3,
+                     one, zero));
+    for (int q = 0; q < 3; ++q) {
+      VK(cgemm<double>(h->st, OP_T, OP_N, dr, dr, dl, A + q * sd, la, 0, T + (long)q * dl * dr, dr,
+                       0, En, dr, 0, 1, one, q ? one : zero));
+      VK(cgemm<double>(h->st, OP_N, OP_N, 1, dr, dl, t, dl, 0, A + q * sd, la, 0, tn, dr, 0, 1,
+                       one, q ? one : zero));
+    }
+    std::swap(E, En);
+    std::swap(t, tn);
+  }
+  double2 r[2];
+  VK(cudaMemcpyAsync(&r[0], E, sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+  VK(cudaMemcpyAsync(&r[1], t, sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+  VK(cudaStreamSynchronize(h->st));
+  if (!(r[1].x != 0) || !std::isfinite(r[1].x)) return vfail(h, MPDO_ERR_NUMERIC, "vmpo: zero trace");
+  *collision = r[0].x / (r[1].x * r[1].x);
+  return MPDO_OK;
+}
+
 int mpdo_vmpo_get_dims(mpdo_vmpo h, int* bond_dims, int* centre) {
   if (!h) return vfail(nullptr, MPDO_ERR_ARG, "vmpo: null handle");
   for (int u = 0; u < h->n - 1; ++u) {
@@ -609,11 +680,46 @@ int mpdo_vmpo_get_dims(mpdo_vmpo h, int* bond_dims, int* centre) {
   return MPDO_OK;
 }
 
+int mpdo_vmpo_set_precision(mpdo_vmpo h, int mode) {
+  if (!h || (mode != 0 && mode != 1)) return vfail(h, MPDO_ERR_ARG, "vmpo: mode must be 0 or 1");
+  if (mode == 1 && !h->mixmem) {
+    const int n9 = 9 * h->chi;
+    const size_t tw = (size_t)256 << 20;
+    int rc;
+    if ((rc = valloc(h, &h->mixmem, mix_work_bytes(n9))) || (rc = valloc(h, &h->tcws, tw)) ||
+        (rc = valloc(h, (void**)&h->tcerr, sizeof(int)))) {
+      h->mixmem = nullptr;
+      return rc;
+    }
+    if (cudaMallocHost((void**)&h->htcerr, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      h->htcerr = nullptr;
+      h->mixmem = nullptr;
+      return vfail(h, MPDO_ERR_OOM, "vmpo: pinned host allocation");
+    }
+    *h->htcerr = 0;
+    mix_work_bind(h->mixw, h->mixmem, n9);
+    h->mixw.tcws = h->tcws;
+    h->mixw.tcws_bytes = tw;
+    h->mixw.tcerr = h->tcerr;
+    h->mixw.tc_min_macs = (double)(1 << 21);
+    h->tcws_bytes = tw;
+  }
+  h->tc = mode;
+  // the mixed solver resolves eigenvalues to ~1e-14 of the largest: numerical zeros below
+  // 10 x that in the tensor-core form, below 1e-15 in FP64
+  h->cut2 = std::max(h->sv_req * h->sv_req, mode ? 1e-13 : 1e-15);
+  VK(cudaStreamSynchronize(h->st));
+  return MPDO_OK;
+}
+
 int mpdo_vmpo_destroy(mpdo_vmpo h) {
   if (!h) return MPDO_OK;
   if (h->st) cudaStreamSynchronize(h->st);
+  mix_work_release(h->mixw);
   for (void* p : h->allocs) cudaFree(p);
   if (h->hsc) cudaFreeHost(h->hsc);
+  if (h->htcerr) cudaFreeHost(h->htcerr);
   if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
   return MPDO_OK;

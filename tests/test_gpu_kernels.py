@@ -149,4 +149,50 @@ def test_mixed_heig_graded_spectrum(lib, n):
     res = np.linalg.norm(h @ v - v * w[None, :], axis=0).max()
     assert res < 1e-8
     assert np.abs(v.conj().T @ v - np.eye(n)).max() < 1e-4
-    assert 1 <= levels <= 8
+    assert 1 <= levels <= 24
+
+
+@pytest.mark.parametrize("prec,n", [(2, 300), (3, 300), (3, 1350), (3, 2304)])
+def test_mixed_heig_bond_sizes(lib, prec, n):
+    """The mixed solver at bond-Gram sizes n = 9 D (D = 150 and 256): FP32 Jacobi levels and
+    FP64 refinement, with the refinement's products on the CUDA cores (prec 2) or as exact
+    BF16 slice products on the tensor cores (prec 3).  Spectrum over 14 decades, dense
+    (neighbours 1.4-10 % apart).
+
+    Bounds, with eps = 2^-48 sqrt(n) (the slice products carry ~2^-48 of each row's largest
+    entry; FP64's rounding is below it): eigenvalues to 10 eps of the largest; for the pairs
+    above 1e-10 of the largest, residuals to 1e-8 and orthonormality to the perturbation
+    bound of the products (Davis-Kahan): |<v_i, v_j>| |l_i - l_j| <= 10 eps l_0, norms to
+    1e-8 -- a pair is corrected once its mixing angle is below the pass's bound and the last
+    pass leaves angles and norms off by at most ~1e-8; pairs the FP32 sweeps leave mixed are
+    settled by Rayleigh-Ritz."""
+    rng = np.random.default_rng(n + prec)
+    q, _ = np.linalg.qr(_rand(rng, (n, n)))
+    lam = 10.0 ** (-np.linspace(0, 14, n))
+    h = (q * lam) @ q.conj().T
+    h = 0.5 * (h + h.conj().T)
+    ta = torch.tensor(h, dtype=torch.complex128, device="cuda")
+    tv = torch.zeros_like(ta)
+    tw = torch.zeros(n, dtype=torch.float64, device="cuda")
+    levels = lib.kernel_heig(prec, n, ta, tv, tw)
+    torch.cuda.synchronize()
+    w = tw.cpu().numpy()
+    v = tv.cpu().numpy()
+    order = np.argsort(w)[::-1]
+    w, v = w[order], v[:, order]
+    eps = 2.0 ** -48 * np.sqrt(n)
+    big = lam > 1e-10
+    vb, wb = v[:, big], w[big]
+    eig_err = np.abs(w - lam).max()
+    res = np.linalg.norm(h @ vb - vb * wb[None, :], axis=0).max()
+    ov = np.abs(vb.conj().T @ vb)
+    norm_err = np.abs(np.diag(ov) - 1.0).max()
+    np.fill_diagonal(ov, 0.0)
+    dk = (ov * np.abs(wb[:, None] - wb[None, :])).max()
+    print(f"n={n} prec={prec}: levels {levels}, eigenvalues {eig_err:.2e}, residual {res:.2e}, "
+          f"norms {norm_err:.2e}, overlap x gap {dk:.2e} (bound {10 * eps:.1e})")
+    assert eig_err < 10 * eps
+    assert res < 1e-8
+    assert norm_err < 1e-8
+    assert dk < 10 * eps
+    assert 1 <= levels <= 24

@@ -415,11 +415,40 @@ def test_second_order_matches_oracle(lib, prec, case):
     g.close()
 
 
+U32 = 2.0 ** -24   # unit roundoff of the FP32-stored site tensors
+
+
+def _energy_norm(c):
+    """sum_k ||h_k|| of the TFIM terms: |J| per bond, |h| + |b J| per site (a bound on ||H||)."""
+    return (c.n_sites - 1) * abs(c.J) + c.n_sites * (abs(c.hx) + abs(c.bz * c.J))
+
+
+def test_batch512_circuit0_fp64_matches_oracle(lib):
+    """Circuit 0 of the batched workload (N = 99, p = 2, chi 64, K 8; its energy's two parts
+    cancel to a sixth of their scale) in FP64 at the same cut: 1e-9 relative on every output,
+    so what the mixed form shows on this circuit is its precision, not the method."""
+    c = synth.batch512()[0]
+    g, e, _ = _gpu(lib, c, "fp64", sv_cutoff=MIXED_FLOOR_CUT)
+    _, r = _oracle(c, sv_cutoff=MIXED_FLOOR_CUT)
+    for key in ("e_raw", "e_succ", "p_succ", "trace"):
+        assert abs(e[key] - r[key]) < 1e-9 * max(1.0, abs(r[key])), (key, e[key], r[key])
+    g.close()
+
+
 def test_batch512_first_32_circuits_match_oracle(lib):
     """The batched workload's first 32 circuits (N ~ U{20..100}, chi in {32,64,128}, K = 8,
     p in {1,2}, log-uniform rates) run concurrently through the executor in the mixed
     tensor-core form at reading A4's cut, every one against the oracle at the effective cut
-    (s > sqrt(1e-13) s_max): 1e-6 relative on every energy and probability."""
+    (s > sqrt(1e-13) s_max).
+
+    Bounds: 1e-6 relative on the success probability and the trace.  An energy is a sum of
+    local terms; the rounding of the FP32-stored site tensors (unit roundoff u = 2^-24) gives
+    each term's expectation an absolute error of order u ||h_k||, whatever its value, so the
+    energy's bound is absolute: |dE| <= 2 u sum_k ||h_k||.  Relative to |E| that is a
+    condition number of the sum: on circuits whose terms are small or cancel (circuit 30:
+    N = 71, |E| = 1.22 from 141 terms) it exceeds 1e-6; on chain100 (|E| = 30.9) it is
+    7.7e-7, below the 1e-6 relative bound that test keeps.
+    """
     circs = synth.batch512()[:32]
     pool = [lib.Mpdo(100, 128, 8, m_max=25, prec="tf32x3", gram_fp64=True, sv_cutoff=1e-7,
                      own_stream=True) for _ in range(16)]
@@ -430,15 +459,24 @@ def test_batch512_first_32_circuits_match_oracle(lib):
         descs.append(dict(n_sites=c.n_sites, chi_max=c.chi_max, k_max=c.k_max, layers=dls,
                           J=c.J, hx=c.hx, b=c.bz))
     out = lib.batch_run(pool, descs)
-    worst = {}
+    worst, fails = {}, []
     for i, c in enumerate(circs):
         _, r = _oracle(c, sv_cutoff=MIXED_FLOOR_CUT)
         for j, key in enumerate(("e_raw", "e_succ", "p_succ", "trace")):
-            err = _rel(out[i][j], r[key]) if key in ("p_succ", "trace") else \
-                abs(out[i][j] - r[key]) / abs(r[key])
+            if key in ("p_succ", "trace"):
+                err = _rel(out[i][j], r[key])
+                ok = err < CHAIN100_TOL[key]
+            else:
+                err = abs(out[i][j] - r[key]) / (2 * U32 * _energy_norm(c))
+                ok = err < 1.0
+                worst[key + "_rel_to_E"] = max(worst.get(key + "_rel_to_E", 0.0),
+                                               abs(out[i][j] - r[key]) / abs(r[key]))
             worst[key] = max(worst.get(key, 0.0), err)
-            assert err < CHAIN100_TOL[key], (i, key, out[i][j], r[key])
-    print("batch512[:32] worst relative errors", worst)
+            if not ok:
+                fails.append((i, key, out[i][j], r[key], err))
+    print("batch512[:32] worst errors (p_succ, trace: relative; energies: |dE| / (2 u sum||h||))",
+          worst)
+    assert not fails, fails
     for dls in uploaded:
         for dl in dls:
             pool[0].free_uploaded(dl)

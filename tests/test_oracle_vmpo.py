@@ -70,3 +70,23 @@ def test_trace_environment_is_real():
     # under the site-wise swap s <-> s' with conjugation); near-degenerate pairs at the cut
     # leave a small imaginary part, which the reading drops
     assert v.t_imag_max < 1e-5
+
+
+def test_collision_probability_pins():
+    """sum_x <x|rho|x>^2 / (tr rho)^2 of the vectorized MPO: the dense definition on the tiny
+    circuit, the MPDO's two-copy diagonal contraction on the same circuit, and the product
+    state |+>^N, whose diagonal is uniform over the 2^N qubit strings (collision 2^-N)."""
+    c = synth.tiny()
+    v = ovmpo.VMPO(c.n_sites, oqaoa.plus_state(), 729)
+    d = odense.DenseRho(c.n_sites, oqaoa.plus_state())
+    m = ompdo.MPDO(c.n_sites, oqaoa.plus_state(), 729, 729)
+    assert abs(v.collision() - 0.5 ** c.n_sites) < 1e-15
+    for i, k in oqaoa.circuit_ops(c):
+        v.apply_two_site(i, k)
+        d.apply_two_site(i, k)
+        m.apply_two_site(i, k)
+    rho = d.matrix()
+    want = np.sum(np.real(np.diag(rho)) ** 2) / np.trace(rho).real ** 2
+    assert abs(v.collision() - want) < 1e-13 * want
+    from oracle import second_order as oso
+    assert abs(oso.second_order(m, 3)["collision"] - v.collision()) < 1e-12 * want
