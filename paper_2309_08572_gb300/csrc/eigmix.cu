@@ -12,9 +12,9 @@
 //       S = Z^+ A Z, G = Z^+ Z, lam_i = S_ii / G_ii,
 //       E_ij = (S_ij - lam_j G_ij) / (lam_j - lam_i) for separated pairs with a
 //              resolved member, -G_ij / 2 otherwise;  E_ii = (1 - G_ii) / 2;  Z <- Z (I + E)
-//     pairs with lam > tau * lam_max(l) (a leading run) are final; the other columns of Z
-//     span the next level's basis, because FP32 sweeps resolve eigenvectors only down to
-//     ~n eps_32 lam_max(l)
+//     pairs with lam > tau * lam_max(l) (a leading run ending where a column is separated
+//     from the next) are final; the other columns of Z span the next level's basis,
+//     because FP32 sweeps resolve eigenvectors only down to ~n eps_32 lam_max(l)
 //   until the largest remaining lam falls below floor * lam_max(0) or nothing remains.
 #include <cuda_runtime.h>
 
@@ -44,10 +44,10 @@ namespace {
 // the sweeps is at 1e-4 after the first pass and at 1e-8 after the last, with norms and
 // angles off by at most ~1e-8.  Levels wider than kThreePassMin (whose FP32 vectors from
 // the block Jacobi carry angles up to ~m eps_32 lam_max / gap) take a third pass, the first
-// one accepting angles up to kNewtonWide.  Other pairs -- those the FP32 sweeps could not separate --
-// are orthonormalised only, and in the final pass short runs of them are settled by
-// Rayleigh-Ritz (ritz_cluster).  Resolved eigenvalues lie above kTau lam_max, two decades
-// per level, the range FP32 sweeps resolve relative to the level's largest.
+// one accepting angles up to kNewtonWide.  Other pairs -- those the FP32 sweeps could not
+// separate -- are orthonormalised only, and in the final pass short runs of them are
+// settled by Rayleigh-Ritz (ritz_cluster).  Resolved eigenvalues lie above kTau lam_max,
+// two decades per level, the range FP32 sweeps resolve relative to the level's largest.
 constexpr double kTau = 1e-2;
 constexpr double kNewtonMax = 1e-2;
 constexpr double kNewtonFinal = 1e-4;
@@ -284,27 +284,38 @@ __device__ void ritz_cluster(int m, const double2* SG, int c0, int c, double* la
 __device__ void fill_ie(int m, const double2* SG, const double* lam, double2* IE, int nl,
                         double fsep, double emax, const int* cid) {
   const long ld = 2L * m;
+  // one thread per pair i <= j: the pair's separation is decided once, from the entry above
+  // the diagonal, and both entries are written
   for (long e = threadIdx.x; e < (long)m * m; e += blockDim.x) {
     const int i = (int)(e / m), j = (int)(e % m);
+    if (j < i) continue;
     if (cid && cid[i] >= 0 && cid[i] == cid[j]) {
       IE[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      if (j != i) IE[(long)j * m + i] = make_double2(0.0, 0.0);
       continue;
     }
-    const double2 g = __ldcg(&SG[(long)i * ld + m + j]);
-    double2 r;
+    const double2 gij = __ldcg(&SG[(long)i * ld + m + j]);
     if (i == j) {
-      r = make_double2(1.0 + 0.5 * (1.0 - g.x), 0.0);
-    } else {
-      const bool resolved = (i < nl) || (j < nl);
-      if (resolved && pair_separated(SG, ld, m, lam, i, j, fsep, emax)) {
-        const double d = lam[j] - lam[i];
-        const double2 sv = __ldcg(&SG[(long)i * ld + j]);
-        r = make_double2((sv.x - lam[j] * g.x) / d, (sv.y - lam[j] * g.y) / d);
-      } else {
-        r = make_double2(-0.5 * g.x, -0.5 * g.y);
-      }
+      IE[e] = make_double2(1.0 + 0.5 * (1.0 - gij.x), 0.0);
+      continue;
     }
-    IE[e] = r;
+    const double2 gji = __ldcg(&SG[(long)j * ld + m + i]);
+    const double li = lam[i], lj = lam[j], d = lj - li;
+    bool newton = false;
+    double2 sij, sji;
+    if ((i < nl || j < nl) && fabs(d) > fsep) {
+      sij = __ldcg(&SG[(long)i * ld + j]);
+      const double ex = sij.x - lj * gij.x, ey = sij.y - lj * gij.y;
+      newton = sqrt(ex * ex + ey * ey) < emax * fabs(d);
+      if (newton) sji = __ldcg(&SG[(long)j * ld + i]);
+    }
+    if (newton) {
+      IE[e] = make_double2((sij.x - lj * gij.x) / d, (sij.y - lj * gij.y) / d);
+      IE[(long)j * m + i] = make_double2((sji.x - li * gji.x) / -d, (sji.y - li * gji.y) / -d);
+    } else {
+      IE[e] = make_double2(-0.5 * gij.x, -0.5 * gij.y);
+      IE[(long)j * m + i] = make_double2(-0.5 * gji.x, -0.5 * gji.y);
+    }
   }
 }
 
@@ -351,8 +362,14 @@ __device__ void refine_step(int m, int n, const double2* SG, int level0, int lev
     __shared__ int s_cl0[kMaxClusters], s_cln[kMaxClusters];
     __shared__ int s_ncl;
     unsigned char* sep = m <= kSepMax ? s_sep : sepg;
-    // neighbour separation, then the runs of unseparated neighbours: short ones become
-    // Ritz clusters (cid = first index), longer ones (or beyond kMaxClusters) cid = -2
+    // columns at or below kTau lam_max go to the next level whatever happens here
+    int f0 = m;
+    for (int i = tid; i < m; i += nt)
+      if (!(lam[i] > kTau * v)) f0 = min(f0, i);
+    f0 = block_min_int(f0, ired);
+    // neighbour separation, then the runs of unseparated neighbours that start above f0:
+    // short ones become Ritz clusters (cid = first index), longer ones (or beyond
+    // kMaxClusters) cid = -2
     for (int i = tid; i < m; i += nt) {
       sep[i] = (i + 1 < m) ? (pair_separated(SG, ld, m, lam, i, i + 1, fsep, kNewtonFinal) ? 1 : 0) : 1;
       cid[i] = -1;
@@ -360,7 +377,7 @@ __device__ void refine_step(int m, int n, const double2* SG, int level0, int lev
     __syncthreads();
     if (tid == 0) {
       int ncl = 0;
-      for (int i = 0; i < m;) {
+      for (int i = 0; i < f0;) {
         int j = i;
         while (j + 1 < m && !sep[j]) ++j;   // run [i, j]
         const int len = j - i + 1;
