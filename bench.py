@@ -751,9 +751,10 @@ def run_compare(args):
     one-qubit gates and noisy CZ brickwork, seed 5), for the vectorized MPO with naive and
     with purity-preserving truncation on the bond and for the MPDO, against the update time
     per two-layer period.  Errors are the mean over the last 5 periods of |Z - Z_ref| / Z_ref,
-    Z_ref from the vectorized MPO with PPT at chi = 128 (tensor-core form, bond cut
-    s > 1e-5 s_max); the MPDO at (chi 64, K 8) is reported beside it as a check of the
-    reference.  Points: FP64, bond cut s > 1e-7 s_max.  One line of JSON with every point."""
+    Z_ref from the MPDO at (chi 64, K 16), whose points converge fastest; the MPDO at
+    (chi 32, K 8) is reported beside it as a check of the reference.  Points: FP64, bond cut
+    s > 1e-7 s_max, except the vMPO at chi = 128 (tensor-core form, s > 1e-5 s_max).  One
+    line of JSON with every point and its collision probabilities."""
     import torch
     import paper_2309_08572_gb300 as lib
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -783,19 +784,24 @@ def run_compare(args):
         g.close()
         return np.array(zs), t / (depth / 2)
 
-    z_ref, t_ref = run("vmpo", 128, mode="ppt", tc=True)
-    z_chk, t_chk = run("mpdo", 64, 8)
+    z_ref, t_ref = run("mpdo", 64, 16)
+    z_chk, t_chk = run("mpdo", 32, 8)
     points = []
+
+    def add(engine, chi, k, z, t):
+        points.append({"engine": engine, "chi": chi, "K": k, "s_per_period": t,
+                       "collision_rel_err": float(np.mean(np.abs(z - z_ref) / z_ref)),
+                       "collision": [float(x) for x in z]})
+
     for mode in ("naive", "ppt"):
         for chi in (8, 16, 32, 64):
             z, t = run("vmpo", chi, mode=mode)
-            points.append({"engine": f"vmpo-{mode}", "chi": chi, "K": None,
-                           "s_per_period": t,
-                           "collision_rel_err": float(np.mean(np.abs(z - z_ref) / z_ref))})
-    for chi, k in ((8, 2), (16, 2), (16, 4), (32, 4), (32, 8)):
+            add(f"vmpo-{mode}", chi, None, z, t)
+    z, t = run("vmpo", 128, mode="ppt", tc=True)
+    add("vmpo-ppt (tensor-core form)", 128, None, z, t)
+    for chi, k in ((8, 2), (16, 2), (16, 4), (32, 4)):
         z, t = run("mpdo", chi, k)
-        points.append({"engine": "mpdo", "chi": chi, "K": k, "s_per_period": t,
-                       "collision_rel_err": float(np.mean(np.abs(z - z_ref) / z_ref))})
+        add("mpdo", chi, k, z, t)
     line = {"metric": "collision-probability error vs update time per two-layer period "
                       "(Fig. 7 comparison)",
             "value": None, "unit": "relative error / s", "n_gpus": 1, "higher_is_better": False,
@@ -803,10 +809,10 @@ def run_compare(args):
             "config": {"workload": "rcs8 gamma_diss=0.1: 8 sites (d=3), depth 40, Haar U(2) on "
                                    "the qubit levels + noisy CZ brickwork (G0), post-promotion "
                                    "0.01 rad, seed 5, |0>^8; bond cut s > 1e-7 s_max",
-                       "precision": "FP64 (the reference: exact-slice tensor-core products + "
-                                    "mixed eigensolver)",
-                       "reference": "vMPO PPT chi=128", "reference_s_per_period": t_ref,
-                       "check_mpdo_64x8_vs_reference": float(np.mean(np.abs(z_chk - z_ref) /
+                       "precision": "FP64 (the vMPO at chi=128: exact-slice tensor-core "
+                                    "products + mixed eigensolver)",
+                       "reference": "MPDO chi=64 K=16", "reference_s_per_period": t_ref,
+                       "check_mpdo_32x8_vs_reference": float(np.mean(np.abs(z_chk - z_ref) /
                                                                     z_ref)),
                        "check_s_per_period": t_chk,
                        "collision_reference": [float(x) for x in z_ref]},
@@ -851,8 +857,7 @@ def main():
                          "(default: the built-in size rules, faster under concurrency)")
     ap.add_argument("--gate-model", choices=["g0", "g1"], default="g0",
                     help="g0: ideal CZ with closed-form noise per block; g1: the Gaussian-pulse "
-                         "CZ channel integrated from the Lindbladian (chain workloads; no timed "
-                         "measurement of it exists yet)")
+                         "CZ channel integrated from the Lindbladian (chain workloads)")
     ap.add_argument("--batch", type=int, default=32,
                     help="circuits per step, run concurrently by the batch executor")
     ap.add_argument("--workload", choices=["chain100", "chain100deep", "chain40", "batch512",
