@@ -258,6 +258,22 @@ int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double beta, double 
                           double bd, double eta, int* sites, int* ms, double* out,
                           size_t cap);
 
+/* The same QAOA layer split by the coherent part of Rydberg dissipation (App. E): the
+ * dissipation gamma_diss (per pulse) damps the gate's two-atom coherences by
+ * alpha = e^{-0.012291 gamma_diss} and beta = e^{-0.0185454 gamma_diss}, which act on the
+ * Ising phase gate as the extra phases d1 = ((1-alpha)/(1+alpha))^2 on S^z_i + S^z_j and
+ * d2 = ((alpha-beta)/(alpha+beta))^2 on S^z_i S^z_j.  part 0: the coherent part alone -- every
+ * block without dissipation (the other noise kept), followed by the diagonal shift
+ * exp(-i J alpha (d2 z_i z_j + d1 (z_i + z_j))), z = (1, -1, 0) on (|0>, |1>, |r>); part 1:
+ * the incoherent part -- the full block followed by the inverse shift.  Outputs, capacity
+ * and the other arguments as for mpdo_build_qaoa_layer; MPDO_ERR_ARG for part not 0 or 1 or
+ * a negative or non-finite gamma_diss. */
+int mpdo_build_qaoa_layer_appe(int n_sites, int k, double alpha, double beta, double J,
+                               double bz, double gamma_diss, double gamma_deph,
+                               double xtalk_phase, double delta_pp, double b0, double b1,
+                               double bd, int part, double eta, int* sites, int* ms,
+                               double* out, size_t cap);
+
 /* Random-circuit layer k (0-based) of the paper's RCS workload (Sec. IV, Figs. 4 and 5 a-c):
  * a Haar one-qubit gate on every atom, then a noisy CZ on the bonds (i, i+1) with
  * i = k mod 2 (brickwork), written as one sweep of n_sites-1 two-site ops (left to right for

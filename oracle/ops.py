@@ -149,9 +149,27 @@ def zz_block_unitary(angle_zz: float) -> np.ndarray:
     return cnot @ rz @ cnot
 
 
+def app_e_phases(gamma_diss: float):
+    """App. E: coherence damping alpha = e^{-0.012291 gamma}, beta = e^{-0.0185454 gamma} of
+    a dissipative pulse, and the phases it adds to the Ising phase gate:
+    d1 = ((1 - alpha)/(1 + alpha))^2 on S^z_i + S^z_j, d2 = ((alpha - beta)/(alpha + beta))^2
+    on S^z_i S^z_j."""
+    alpha = np.exp(-0.012291 * gamma_diss)
+    beta = np.exp(-0.0185454 * gamma_diss)
+    return ((1 - alpha) / (1 + alpha)) ** 2, ((alpha - beta) / (alpha + beta)) ** 2
+
+
+def app_e_shift(angle_zz: float, d1: float, d2: float) -> np.ndarray:
+    """exp(-i a (d2 S^z (x) S^z + d1 (S^z (x) I + I (x) S^z))) on two atoms (S^z the Pauli
+    matrix on the qubit levels, zero on |r>): the App. E phases of a block of angle a."""
+    zz = np.kron(Z_Q, Z_Q)
+    z1 = np.kron(Z_Q, I3) + np.kron(I3, Z_Q)
+    return expm_h(angle_zz, d2 * zz + d1 * z1)
+
+
 def g0_block_channel(angle_zz: float, gamma_diss: float, gamma_deph: float,
                      xtalk_phase: float, delta_pp: float, b0: float, b1: float, bd: float,
-                     post_left=None, post_right=None):
+                     post_left=None, post_right=None, shift=None):
     """One noisy ZZ block on a bond in the G0 (gate-level) model, as a Kraus set.
 
     Order of action (reading): the crosstalk phase exp(-i phi n_r (x) n_r) on residual Rydberg population
@@ -172,6 +190,8 @@ def g0_block_channel(angle_zz: float, gamma_diss: float, gamma_deph: float,
     # reorder the (a_i a_j, a_i' a_j') product superoperator to two-site row-major vec
     s = s.reshape(3, 3, 3, 3, 3, 3, 3, 3).transpose(0, 2, 1, 3, 4, 6, 5, 7).reshape(81, 81)
     s = s @ superop([u])
+    if shift is not None:                              # a unitary after the noise unit
+        s = superop([shift]) @ s
     if post_left is not None or post_right is not None:
         v = np.kron(post_left if post_left is not None else I3,
                     post_right if post_right is not None else I3)

@@ -40,6 +40,27 @@ def layer_ops(c, k: int) -> List[Tuple[int, list]]:
     return [(i, both if i == 0 else mid) for i in range(n - 2, -1, -1)]
 
 
+def layer_ops_appe(c, k: int, part: int) -> List[Tuple[int, list]]:
+    """Layer k split by the coherent part of the dissipation (App. E): part 0 -- every
+    block without dissipation, followed by the phases app_e_phases(gamma_diss) adds to the
+    Ising phase gate (mimicking the dissipation's coherent part); part 1 -- the full block
+    followed by the inverse of those phases (its incoherent part)."""
+    n = c.n_sites
+    a, b = c.alpha[k], c.beta[k]
+    v = site_gate(a, b, c.J, c.bz)
+    d1, d2 = ops.app_e_phases(c.gamma_diss)
+    sh = ops.app_e_shift(c.J * a, d1, d2)
+    common = dict(angle_zz=c.J * a, gamma_diss=c.gamma_diss if part == 1 else 0.0,
+                  gamma_deph=c.gamma_deph, xtalk_phase=c.xtalk_phase, delta_pp=c.delta_pp,
+                  b0=c.b0, b1=c.b1, bd=c.bd, shift=sh if part == 0 else sh.conj().T)
+    both = ops.g0_block_channel(**common, post_left=v, post_right=v)
+    if k % 2 == 0:                                   # left -> right
+        mid = ops.g0_block_channel(**common, post_left=v)
+        return [(i, both if i == n - 2 else mid) for i in range(n - 1)]
+    mid = ops.g0_block_channel(**common, post_right=v)
+    return [(i, both if i == 0 else mid) for i in range(n - 2, -1, -1)]
+
+
 def layer_ops_cz(c, k: int, s_cz: np.ndarray) -> List[Tuple[int, list]]:
     """Layer k in gate model G1: every CZ of the ZZ blocks is the channel s_cz (81 x 81, e.g.
     the pulse CZ of oracle.pulse); crosstalk as in G0, no post-promotion and no separate
@@ -57,11 +78,15 @@ def layer_ops_cz(c, k: int, s_cz: np.ndarray) -> List[Tuple[int, list]]:
     return [(i, both if i == 0 else mid) for i in range(n - 2, -1, -1)]
 
 
-def circuit_ops(c, s_cz=None) -> List[Tuple[int, list]]:
-    """All ops of the circuit; gate model G0, or G1 with the CZ channel s_cz."""
+def circuit_ops(c, s_cz=None, appe_part=None) -> List[Tuple[int, list]]:
+    """All ops of the circuit; gate model G0, or G1 with the CZ channel s_cz, or G0 split
+    by App. E's coherent part (appe_part 0 / 1)."""
     out = []
     for k in range(c.p):
-        out.extend(layer_ops(c, k) if s_cz is None else layer_ops_cz(c, k, s_cz))
+        if appe_part is not None:
+            out.extend(layer_ops_appe(c, k, appe_part))
+        else:
+            out.extend(layer_ops(c, k) if s_cz is None else layer_ops_cz(c, k, s_cz))
     return out
 
 

@@ -123,6 +123,8 @@ def _load():
                                          C.c_size_t]),
         "mpdo_build_qaoa_layer": (I, [I, I, D, D, D, D, D, D, D, D, D, D, D, D, P(I), P(I),
                                       P(D), S]),
+        "mpdo_build_qaoa_layer_appe": (I, [I, I, D, D, D, D, D, D, D, D, D, D, D, I, D, P(I),
+                                           P(I), P(D), S]),
         "mpdo_build_rcs_layer": (I, [I, I, P(D), D, D, D, D, D, D, D, D, P(I), P(I), P(D), S]),
         "mpdo_kernel_launches": (C.c_longlong, []),
         "mpdo_profile": (I, [VP, I]),
@@ -206,17 +208,25 @@ def build_block_channel(angle_zz: float, gamma_diss: float, gamma_deph: float,
 def build_qaoa_layer(n_sites: int, k: int, alpha: float, beta: float, J: float = 1.0,
                      bz: float = 0.0, gamma_diss: float = 0.0, gamma_deph: float = 0.0,
                      xtalk_phase: float = 0.0, delta_pp: float = 0.0, b0: float = 1 / 16,
-                     b1: float = 1 / 16, bd: float = 7 / 8, eta: float = 1e-15):
-    """Ordered two-site ops [(site, Kraus (M,9,9))] of QAOA layer k (library builder)."""
+                     b1: float = 1 / 16, bd: float = 7 / 8, eta: float = 1e-15,
+                     appe_part: Optional[int] = None):
+    """Ordered two-site ops [(site, Kraus (M,9,9))] of QAOA layer k (library builder).
+    appe_part 0 / 1: the coherent / incoherent part of the dissipation (App. E)."""
     nops = n_sites - 1
     sites = np.zeros(nops, dtype=np.int32)
     ms = np.zeros(nops, dtype=np.int32)
     cap = nops * 81 * 81
     out = np.zeros((cap, 2))
-    rc = LIB.mpdo_build_qaoa_layer(n_sites, k, alpha, beta, J, bz, gamma_diss, gamma_deph,
-                                   xtalk_phase, delta_pp, b0, b1, bd, eta,
-                                   sites.ctypes.data_as(C.POINTER(C.c_int)),
-                                   ms.ctypes.data_as(C.POINTER(C.c_int)), _dptr(out), cap)
+    sp = sites.ctypes.data_as(C.POINTER(C.c_int))
+    mp_ = ms.ctypes.data_as(C.POINTER(C.c_int))
+    if appe_part is None:
+        rc = LIB.mpdo_build_qaoa_layer(n_sites, k, alpha, beta, J, bz, gamma_diss, gamma_deph,
+                                       xtalk_phase, delta_pp, b0, b1, bd, eta, sp, mp_,
+                                       _dptr(out), cap)
+    else:
+        rc = LIB.mpdo_build_qaoa_layer_appe(n_sites, k, alpha, beta, J, bz, gamma_diss,
+                                            gamma_deph, xtalk_phase, delta_pp, b0, b1, bd,
+                                            int(appe_part), eta, sp, mp_, _dptr(out), cap)
     _check(rc)
     flat = out.view(complex).reshape(-1)
     ops, off = [], 0
@@ -287,15 +297,17 @@ def build_rcs_layer(n_sites: int, k: int, haar, gamma_diss: float = 0.0,
     return ops
 
 
-def circuit_layers(c) -> List[list]:
+def circuit_layers(c, appe_part: Optional[int] = None) -> List[list]:
     """Library-built op lists for every layer of a workload description (synth.Circuit, or
-    synth.RcsCircuit for the random circuits)."""
+    synth.RcsCircuit for the random circuits).  appe_part (QAOA only): 0 / 1 builds the
+    coherent / incoherent part of the dissipation (App. E) instead of the full blocks."""
     if hasattr(c, "haar"):
         return [build_rcs_layer(c.n_sites, k, c.haar[k], c.gamma_diss, c.gamma_deph,
                                 c.xtalk_phase, c.delta_pp, c.b0, c.b1, c.bd)
                 for k in range(c.depth)]
     return [build_qaoa_layer(c.n_sites, k, c.alpha[k], c.beta[k], c.J, c.bz, c.gamma_diss,
-                             c.gamma_deph, c.xtalk_phase, c.delta_pp, c.b0, c.b1, c.bd)
+                             c.gamma_deph, c.xtalk_phase, c.delta_pp, c.b0, c.b1, c.bd,
+                             appe_part=appe_part)
             for k in range(c.p)]
 
 

@@ -215,7 +215,7 @@ Mat zz_block(double angle) {
 
 int block_channel(double angle_zz, double gd, double gp, double phi, double dpp, double b0,
                   double b1, double bd, const Mat* post_l, const Mat* post_r, double eta,
-                  std::vector<Mat>& kraus) {
+                  std::vector<Mat>& kraus, const Mat* shift = nullptr) {
   (void)bd;
   Mat u = zz_block(angle_zz);
   if (phi != 0.0) u = matmul(u, expmh(phi, kron(nr(), 3, nr(), 3), 9), 9);
@@ -225,11 +225,37 @@ int block_channel(double angle_zz, double gd, double gp, double phi, double dpp,
     u = matmul(kron(pp, 3, pp, 3), u, 9);
   }
   Mat s = matmul(two_site_product(noise_superop(gd, gp, b0, b1)), unitary_superop(u, 9), 81);
+  if (shift) s = matmul(unitary_superop(*shift, 9), s, 81);
   if (post_l || post_r) {
     Mat v = kron(post_l ? *post_l : eye(3), 3, post_r ? *post_r : eye(3), 3);
     s = matmul(unitary_superop(v, 9), s, 81);
   }
   return kraus_from_superop(s, 9, eta, kraus);
+}
+
+// ------------------------------------------------------------------ App. E coherent part
+// Rydberg dissipation gamma (per pulse) damps the pulse's two-atom coherences by
+// alpha = e^{-0.012291 gamma} (one atom through |r>) and beta = e^{-0.0185454 gamma} (both),
+// which shows up in the Ising phase gate as the extra phases
+//   d1 = ((1 - alpha) / (1 + alpha))^2 on S^z_i + S^z_j,  d2 = ((alpha - beta) / (alpha + beta))^2
+// on S^z_i S^z_j (App. E).  With S^z the Pauli matrix on the qubit levels and zero on |r>
+// (the workload's reading of S^z), the shift after a block of angle a is the diagonal
+// exp(-i sign a (d2 z_i z_j + d1 (z_i + z_j))), z = (1, -1, 0) on (|0>, |1>, |r>).
+void appe_shifts(double gamma, double* d1, double* d2) {
+  const double al = std::exp(-0.012291 * gamma), be = std::exp(-0.0185454 * gamma);
+  *d1 = ((1.0 - al) / (1.0 + al)) * ((1.0 - al) / (1.0 + al));
+  *d2 = ((al - be) / (al + be)) * ((al - be) / (al + be));
+}
+
+Mat appe_shift(double angle, double d1, double d2, double sign) {
+  const double z[3] = {1.0, -1.0, 0.0};
+  Mat u(81, zc(0, 0));
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      const double ph = -sign * angle * (d2 * z[a] * z[b] + d1 * (z[a] + z[b]));
+      u[(a * 3 + b) * 9 + (a * 3 + b)] = zc(std::cos(ph), std::sin(ph));
+    }
+  return u;
 }
 
 // ------------------------------------------------------------------ gate model G1
@@ -398,23 +424,34 @@ extern "C" int mpdo_build_block_channel(double angle_zz, double gamma_diss, doub
   return MPDO_OK;
 }
 
-extern "C" int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double beta, double J,
-                                     double bz, double gamma_diss, double gamma_deph,
-                                     double xtalk_phase, double delta_pp, double b0, double b1,
-                                     double bd, double eta, int* sites, int* ms, double* out,
-                                     size_t cap) {
-  if (n_sites < 2 || k < 0 || !sites || !ms || !out) return MPDO_ERR_ARG;
+// QAOA layer k in gate model G0; part = -1 the full block, 0 its App. E coherent part alone
+// (no dissipation, the shift of gamma_diss applied), 1 the block with that shift reversed.
+int qaoa_layer(int n_sites, int k, double alpha, double beta, double J, double bz,
+               double gamma_diss, double gamma_deph, double xtalk_phase, double delta_pp,
+               double b0, double b1, double bd, double eta, int part, int* sites, int* ms,
+               double* out, size_t cap) {
+  if (n_sites < 2 || k < 0 || !sites || !ms || !out || part < -1 || part > 1) return MPDO_ERR_ARG;
   if (!finite_all({alpha, beta, J, bz, eta})) return MPDO_ERR_NUMERIC;
   if (eta < 0) return MPDO_ERR_ARG;
+  if (part >= 0 && (!std::isfinite(gamma_diss) || gamma_diss < 0)) return MPDO_ERR_ARG;
   // one-site gate exp(-i beta S^x) exp(-i b J alpha S^z), folded after the last block
   Mat v = matmul(expmh(beta, xq(), 3), expmh(bz * J * alpha, zq(), 3), 3);
+  Mat shift;
+  double gd = gamma_diss;
+  if (part >= 0) {
+    double d1, d2;
+    appe_shifts(gamma_diss, &d1, &d2);
+    shift = appe_shift(J * alpha, d1, d2, part == 0 ? 1.0 : -1.0);
+    if (part == 0) gd = 0.0;
+  }
+  const Mat* sh = part >= 0 ? &shift : nullptr;
   std::vector<Mat> both, mid;
-  int rc = block_channel(J * alpha, gamma_diss, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd,
-                         &v, &v, eta, both);
+  int rc = block_channel(J * alpha, gd, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd, &v, &v,
+                         eta, both, sh);
   if (rc) return rc;
   const bool ltr = (k % 2 == 0);
-  rc = block_channel(J * alpha, gamma_diss, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd,
-                     ltr ? &v : nullptr, ltr ? nullptr : &v, eta, mid);
+  rc = block_channel(J * alpha, gd, gamma_deph, xtalk_phase, delta_pp, b0, b1, bd,
+                     ltr ? &v : nullptr, ltr ? nullptr : &v, eta, mid, sh);
   if (rc) return rc;
   size_t off = 0;
   for (int q = 0; q < n_sites - 1; ++q) {
@@ -432,6 +469,26 @@ extern "C" int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double be
       }
   }
   return MPDO_OK;
+}
+
+extern "C" int mpdo_build_qaoa_layer(int n_sites, int k, double alpha, double beta, double J,
+                                     double bz, double gamma_diss, double gamma_deph,
+                                     double xtalk_phase, double delta_pp, double b0, double b1,
+                                     double bd, double eta, int* sites, int* ms, double* out,
+                                     size_t cap) {
+  return qaoa_layer(n_sites, k, alpha, beta, J, bz, gamma_diss, gamma_deph, xtalk_phase,
+                    delta_pp, b0, b1, bd, eta, -1, sites, ms, out, cap);
+}
+
+extern "C" int mpdo_build_qaoa_layer_appe(int n_sites, int k, double alpha, double beta,
+                                          double J, double bz, double gamma_diss,
+                                          double gamma_deph, double xtalk_phase,
+                                          double delta_pp, double b0, double b1, double bd,
+                                          int part, double eta, int* sites, int* ms,
+                                          double* out, size_t cap) {
+  if (part != 0 && part != 1) return MPDO_ERR_ARG;
+  return qaoa_layer(n_sites, k, alpha, beta, J, bz, gamma_diss, gamma_deph, xtalk_phase,
+                    delta_pp, b0, b1, bd, eta, part, sites, ms, out, cap);
 }
 
 // Random-circuit layer (the paper's RCS workload, Sec. IV / Figs. 4-5): one sweep over the

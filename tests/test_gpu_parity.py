@@ -89,6 +89,27 @@ def test_tiny_exact_matches_dense(lib, prec):
     assert np.abs(rho - d.matrix()).max() < (1e-11 if prec == "fp64" else 5e-5)
 
 
+@pytest.mark.parametrize("part", [0, 1])
+def test_appe_parts_match_dense(lib, part):
+    """The tiny circuit with the App. E split of its dissipation (part 0: coherent phases
+    only; part 1: dissipation with those phases reversed), library-built layers through the
+    engine in FP64, against the dense rho of the oracle's split layers: energies and
+    probabilities at the FP64 tolerance, rho to 1e-11 (as the unsplit tiny circuit)."""
+    c = dataclasses.replace(synth.tiny(), k_max=40, gamma_diss=0.2)
+    g = lib.Mpdo(c.n_sites, c.chi_max, c.k_max, m_max=25, prec="fp64")
+    for layer in lib.circuit_layers(c, appe_part=part):
+        g.apply_layer(layer)
+    e = g.expect_energy(c.J, c.hx, c.bz)
+    d = odense.DenseRho(c.n_sites, oqaoa.plus_state())
+    for i, k in oqaoa.circuit_ops(c, appe_part=part):
+        d.apply_two_site(i, k)
+    r = d.expect(c.J, c.hx, c.bz)
+    for key in r:
+        assert _rel(e[key], r[key]) < TOL["fp64"], (key, e[key], r[key])
+    assert np.abs(_dense(g) - d.matrix()).max() < 1e-11
+    g.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "c64"])
 @pytest.mark.parametrize("n,chi,k", [(8, 6, 3), (12, 16, 4), (9, 64, 8)])
 def test_truncated_snake_circuit_matches_oracle(lib, prec, n, chi, k):
