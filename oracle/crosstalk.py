@@ -84,3 +84,38 @@ def apply_dense(rho: np.ndarray, n_sites: int, sites, u: np.ndarray) -> np.ndarr
     left, right = 3 ** lo, 3 ** (n_sites - lo - k)
     full = np.kron(np.kron(np.eye(left), u), np.eye(right))
     return full @ rho @ full.conj().T
+
+
+def apply_mpdo(m, sites, u: np.ndarray, sv_cutoff: float = 1e-14) -> None:
+    """U X on consecutive sites of an oracle MPDO m (oracle.mpdo.MPDO), U acting on the atom
+    levels only (the inner indices are untouched, so rho -> U rho U^+).  The centre must lie
+    in the block: the block's tensors are contracted into one, U applied, and the block
+    split back left to right by SVDs keeping every value above sv_cutoff * s_max (exact up
+    to that cut); the centre ends on the block's last site."""
+    first, k = sites[0], len(sites)
+    if not first <= m.centre < first + k:
+        raise ValueError("the centre must lie in the block")
+    th = m.A[first]                                   # [l, s, k, r]
+    for j in range(1, k):
+        th = np.tensordot(th, m.A[first + j], axes=([th.ndim - 1], [0]))
+    # axes: l, (s_1, k_1), ..., (s_k, k_k), r
+    inner = [th.shape[2 + 2 * j] for j in range(k)]
+    perm = [0] + [1 + 2 * j for j in range(k)] + [2 + 2 * j for j in range(k)] + [th.ndim - 1]
+    t = th.transpose(perm)                            # l, s_1..s_k, k_1..k_k, r
+    dl, dr = t.shape[0], t.shape[-1]
+    t = t.reshape(dl, 3 ** k, -1)
+    t = np.einsum("st,ltr->lsr", u, t)
+    t = t.reshape([dl] + [3] * k + inner + [dr])
+    back = [0]
+    for j in range(k):
+        back += [1 + j, 1 + k + j]
+    th = t.transpose(back + [2 * k + 1])              # l, (s_j, k_j)..., r
+    for j in range(k - 1):
+        rows = th.shape[0] * 3 * inner[j]
+        mat = th.reshape(rows, -1)
+        uu, s, vh = np.linalg.svd(mat, full_matrices=False)
+        keep = max(1, int(np.count_nonzero(s > sv_cutoff * s[0])))
+        m.A[first + j] = uu[:, :keep].reshape(th.shape[0], 3, inner[j], keep)
+        th = (s[:keep, None] * vh[:keep]).reshape([keep] + list(th.shape[3:]))
+    m.A[first + k - 1] = th.reshape(th.shape[0], 3, inner[k - 1], dr)
+    m.centre = first + k - 1

@@ -71,3 +71,37 @@ def test_chain_ends_drop_the_missing_neighbours(n, i, sites):
     if n == 2:
         _, c = pulse.phase_correction(pulse.pulse_unitary(STEPS))
         assert np.abs(u - np.kron(c, c) @ pulse.pulse_unitary(STEPS)).max() < 1e-13
+
+
+def _sweep(n, v, b_x=None):
+    from oracle import mpdo
+    m = mpdo.MPDO(n, v, 3 ** n, 3 ** n)
+    rho = np.ones((1, 1), dtype=complex)
+    for _ in range(n):
+        rho = np.kron(rho, np.outer(v, v.conj()))
+    for i in range(n - 1):
+        sites, u = xt.gate_on_chain(n, i, STEPS, b_x=b_x)
+        xt.apply_mpdo(m, sites, u)
+        rho = xt.apply_dense(rho, n, sites, u)
+    return m, rho
+
+
+def test_mpdo_sweep_of_crosstalk_gates_equals_the_dense_rho():
+    """A left-to-right sweep of crosstalk CZs over a 5-site chain with Rydberg population on
+    every atom: the oracle MPDO's multi-site update, untruncated, equals the dense rho; the
+    neighbours' Rydberg populations enter (B = 0 gives a different state) and the gates
+    leave the population of a non-active neighbour unchanged."""
+    n = 5
+    v = np.array([1.0, 1.0, 0.4], dtype=complex)
+    v /= np.linalg.norm(v)
+    m, rho = _sweep(n, v)
+    assert np.abs(m.to_dense() - rho).max() < 1e-13
+    _, rho0 = _sweep(n, v, b_x=0.0)
+    assert np.abs(rho - rho0).max() > 1e-3
+    # one gate on (1, 2): site 0 and site 3 are controls, their |r> population is kept
+    sites, u = xt.gate_on_chain(n, 1, STEPS)
+    nr = lambda s: np.kron(np.kron(np.eye(3 ** s), np.diag([0.0, 0.0, 1.0])),
+                           np.eye(3 ** (n - s - 1)))
+    after = xt.apply_dense(rho, n, sites, u)
+    for s in (0, 3):
+        assert abs(np.trace(nr(s) @ after) - np.trace(nr(s) @ rho)) < 1e-13
