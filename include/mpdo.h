@@ -308,6 +308,16 @@ int mpdo_build_cz_pulse(const mpdo_pulse* pulse, double gamma_diss, double gamma
                         double b0, double b1, int n_steps, double* superop, double* phi1,
                         double* infidelity);
 
+/* Crosstalk CZ (Sec. III.B, noiseless): a Rydberg atom next to an active atom shifts that
+ * atom's detuning by the neighbour blockade b_x, so the gate on (i, i+1) with its non-active
+ * neighbours i-1 and i+2 is  sum_{a,b} P_a (x) C(delta + a b_x, delta + b b_x) (x) P_b,
+ * P_1 = |r><r|, P_0 = 1 - P_1, C the pulse of `pulse` with those detunings followed by the
+ * one-atom phase correction of the unshifted pulse (as mpdo_build_cz_pulse).  out: host
+ * complex128 [81][81], index ((s_{i-1} 3 + s_i) 3 + s_{i+1}) 3 + s_{i+2}.  n_steps midpoint
+ * exponentials.  A four-site unitary: the two-site update of the engine does not apply it
+ * (it serves the host and the tests). */
+int mpdo_build_crosstalk_cz(const mpdo_pulse* pulse, double b_x, int n_steps, double* out);
+
 /* The QAOA layer of mpdo_build_qaoa_layer with every CZ of the ZZ blocks replaced by the
  * channel cz_superop (host complex128 [81][81], e.g. from mpdo_build_cz_pulse): block =
  * (I(x)Had) CZ (I(x)Had Rz(J alpha) Had) CZ (I(x)Had) as superoperators, the crosstalk phase

@@ -119,6 +119,7 @@ def _load():
         "mpdo_last_error": (C.c_char_p, [VP]),
         "mpdo_build_block_channel": (I, [D, D, D, D, D, D, D, D, P(D), P(D), D, P(D), I, P(I)]),
         "mpdo_build_cz_pulse": (I, [P(Pulse), D, D, D, D, I, P(D), P(D), P(D)]),
+        "mpdo_build_crosstalk_cz": (I, [P(Pulse), D, I, P(D)]),
         "mpdo_build_qaoa_layer_cz": (I, [I, I, D, D, D, D, P(D), D, D, P(I), P(I), P(D),
                                          C.c_size_t]),
         "mpdo_build_qaoa_layer": (I, [I, I, D, D, D, D, D, D, D, D, D, D, D, D, P(I), P(I),
@@ -247,6 +248,18 @@ def build_cz_pulse(gamma_diss: float = 0.0, gamma_deph: float = 0.0, b0: float =
     _check(LIB.mpdo_build_cz_pulse(C.byref(p), gamma_diss, gamma_deph, b0, b1, n_steps,
                                    _dptr(out), C.byref(phi1), C.byref(infid)))
     return out.view(complex).reshape(81, 81).copy(), phi1.value, infid.value
+
+
+def build_crosstalk_cz(b_x: Optional[float] = None, n_steps: int = 2000,
+                       pulse: Optional[dict] = None):
+    """Four-site crosstalk CZ (81 x 81 unitary on (i-1, i, i+1, i+2), Sec. III.B, host
+    builder): the pulse CZ on (i, i+1) with each active atom's detuning shifted by b_x when
+    its non-active neighbour is in |r> (default b_x: the pulse's blockade)."""
+    p = Pulse(**(pulse or GAUSSIAN_CZ))
+    out = np.zeros((81 * 81, 2))
+    _check(LIB.mpdo_build_crosstalk_cz(C.byref(p), p.blockade if b_x is None else b_x, n_steps,
+                                       _dptr(out)))
+    return out.view(complex).reshape(81, 81).copy()
 
 
 def build_qaoa_layer_cz(n_sites: int, k: int, alpha: float, beta: float, cz_superop,

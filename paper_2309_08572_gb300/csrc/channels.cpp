@@ -579,6 +579,55 @@ extern "C" int mpdo_build_cz_pulse(const mpdo_pulse* pulse, double gamma_diss,
   return MPDO_OK;
 }
 
+// Crosstalk CZ (Sec. III.B): the noiseless pulse with the atoms' detunings shifted by
+// s1, s2 (a Rydberg neighbour next to an active atom shifts its detuning by the neighbour
+// blockade), then the controlled combination over the non-active neighbours' Rydberg
+// projectors.  The phase correction is the unshifted pulse's.
+Mat pulse_unitary_shifted(const mpdo_pulse& p, int n_steps, double s1, double s2) {
+  const double tau = p.T / n_steps;
+  Mat u = eye(9);
+  for (int k = 0; k < n_steps; ++k) {
+    const double om = gaussian_omega((k + 0.5) * tau, p);
+    Mat h1 = op3({0, 0, 0, 0, 0, 0.5 * om, 0, 0.5 * om, p.delta + s1});
+    Mat h2 = op3({0, 0, 0, 0, 0, 0.5 * om, 0, 0.5 * om, p.delta + s2});
+    Mat h = kron(h1, 3, eye(3), 3);
+    Mat hb = kron(eye(3), 3, h2, 3);
+    for (int i = 0; i < 81; ++i) h[i] += hb[i];
+    h[8 * 9 + 8] += p.blockade;   // |rr><rr|
+    u = matmul(expmh(tau, h, 9), u, 9);
+  }
+  return u;
+}
+
+extern "C" int mpdo_build_crosstalk_cz(const mpdo_pulse* pulse, double b_x, int n_steps,
+                                       double* out) {
+  if (!pulse || !out || n_steps < 1 || n_steps > 1000000) return MPDO_ERR_ARG;
+  if (!finite_all({pulse->T, pulse->omega_max, pulse->delta, pulse->blockade, pulse->width,
+                   b_x}))
+    return MPDO_ERR_NUMERIC;
+  if (!(pulse->T > 0) || !(pulse->width > 0)) return MPDO_ERR_ARG;
+  const Mat u0 = pulse_unitary_shifted(*pulse, n_steps, 0.0, 0.0);
+  const double phi1 = std::arg(u0[1 * 9 + 1]) - std::arg(u0[0]);
+  const Mat c1 = op3({1, 0, 0, 0, std::exp(zc(0, -phi1)), 0, 0, 0, 1});
+  const Mat cc = kron(c1, 3, c1, 3);
+  const Mat pr = op3({0, 0, 0, 0, 0, 0, 0, 0, 1});
+  const Mat pn = op3({1, 0, 0, 0, 1, 0, 0, 0, 0});
+  Mat acc(81 * 81, zc(0, 0));
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const Mat ua = (a == 0 && b == 0) ? u0
+                                        : pulse_unitary_shifted(*pulse, n_steps, a * b_x, b * b_x);
+      const Mat g = matmul(cc, ua, 9);
+      const Mat term = kron(kron(a ? pr : pn, 3, g, 9), 27, b ? pr : pn, 3);
+      for (int i = 0; i < 81 * 81; ++i) acc[i] += term[i];
+    }
+  for (int i = 0; i < 81 * 81; ++i) {
+    out[2 * i] = acc[i].real();
+    out[2 * i + 1] = acc[i].imag();
+  }
+  return MPDO_OK;
+}
+
 extern "C" int mpdo_build_qaoa_layer_cz(int n_sites, int k, double alpha, double beta, double J,
                                         double bz, const double* cz_superop, double xtalk_phase,
                                         double eta, int* sites, int* ms, double* out,

@@ -105,3 +105,19 @@ def test_mpdo_sweep_of_crosstalk_gates_equals_the_dense_rho():
     after = xt.apply_dense(rho, n, sites, u)
     for s in (0, 3):
         assert abs(np.trace(nr(s) @ after) - np.trace(nr(s) @ rho)) < 1e-13
+
+
+@pytest.mark.parametrize("b_x", [None, 0.0, 2 * np.pi * 1e3])
+def test_library_builder_matches_oracle(b_x):
+    """mpdo_build_crosstalk_cz (host C++) against the oracle, gate by gate.  Bound: the two
+    sides exponentiate each of the n steps independently, so their phases differ by rounding
+    of order n eps tau |H| (tau |H| up to ~37 rad at the largest shift): 10 n eps max(1, tau |H|)."""
+    import __graft_entry__ as g
+    g.build()
+    import paper_2309_08572_gb300 as lib
+    p = pulse.GAUSSIAN
+    a = lib.build_crosstalk_cz(b_x=b_x, n_steps=STEPS)
+    b = xt.crosstalk_cz(STEPS, b_x=b_x)
+    bx = p["blockade"] if b_x is None else b_x
+    th = p["T"] / STEPS * (abs(p["delta"]) + abs(bx) + p["blockade"] + p["omega_max"])
+    assert np.abs(a - b).max() < 10 * STEPS * 2.2e-16 * max(1.0, th)
